@@ -1,0 +1,290 @@
+"""FP64 CPU oracle for the semiclassical lattice Boltzmann method (arXiv 1710.09472).
+
+TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package; the product path never
+does.  It is a thin ctypes wrapper around ``lbm_oracle.c`` (plain C, double
+precision), which restates the paper step by step and shares no code with the
+CUDA library.
+
+Functions and the passages they follow:
+  weight_integrals   Sec. 3, Eq. i2n-cont2 (I_2N of the weight omega)
+  coefficients       Sec. 3 (c_K, cbar_K, c'_K, Delta_2K, J_2K); Sec. 9.1 (thetabar)
+  Model              Sec. 8 + Table lattices-tab (lattices), Sec. 9.1 (EDF, step)
+  Model.equilibrium  Sec. 9.1, Eq. feq-reduced-applied-electrons-in-metals-eq
+  Model.force_term   Sec. 7, Eq. forcing-term-integrals-eq
+  Model.step         Sec. 9.1 discrete Boltzmann equation (collide, then stream)
+  Model.adjoint      reverse sweep of Model.step (chain rule of the above)
+
+Every function is pinned in tests/ against something other than itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "liblbm_oracle.so")
+
+STAT = {"fd": 0, "be": 1, "mb": 2}
+VEL = {"D1V3": 0, "D2V9": 1, "D3V15": 2, "D3V19": 3, "D3V27": 4}
+FORCE = {"shift": 0, "term": 1}
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB_PATH)
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    vp = ctypes.c_void_p
+    lib.or_weight_integrals.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_int, dp]
+    lib.or_coefficients.argtypes = [ctypes.c_int, dp, dp]
+    lib.or_lattice.argtypes = [ctypes.c_int, dp, ip, dp, ip, dp]
+    lib.or_model_size.restype = ctypes.c_int
+    lib.or_model_init.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, dp, dp, ctypes.c_int]
+    lib.or_model_constants.argtypes = [vp, dp]
+    lib.or_model_velocities.argtypes = [vp, ip, ip]
+    lib.or_equilibrium.argtypes = [vp, ctypes.c_double, dp, dp]
+    lib.or_force_term.argtypes = [vp, ctypes.c_double, dp, dp, dp]
+    lib.or_collide_cell.argtypes = [vp, dp, dp, dp]
+    lib.or_init_equilibrium.argtypes = [vp, i64p, u8p, dp, dp, dp]
+    lib.or_step.argtypes = [vp, i64p, u8p, dp, dp, dp, ctypes.c_int64]
+    lib.or_moments.argtypes = [vp, i64p, u8p, dp, dp, dp, dp]
+    lib.or_collide_cell_adjoint.argtypes = [vp, dp, dp, dp, dp, dp, dp, dp]
+    lib.or_adjoint.argtypes = [vp, i64p, u8p, dp, dp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp,
+                               dp, dp, dp]
+    lib.or_num_threads.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _dp(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _u8p(a):
+    if a is None:
+        return None
+    assert a.dtype == np.uint8 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+
+
+def num_threads() -> int:
+    return int(_load().or_num_threads())
+
+
+def weight_integrals(D: int, stat: str = "fd", theta: float = 1.0 / 270.0, mu: float = 1.0,
+                     nmax: int = 4) -> np.ndarray:
+    """I_0, I_2, ..., I_{2 nmax} of the weight (Sec. 3, Eq. i2n-cont2)."""
+    out = np.zeros(nmax + 1)
+    rc = _load().or_weight_integrals(D, STAT[stat], theta, mu, nmax, _dp(out))
+    if rc != 0:
+        raise ValueError("bad weight-integral arguments")
+    return out
+
+
+def coefficients(D: int, I: np.ndarray) -> dict:
+    """Second-order polynomial coefficients and thetabar (Sec. 3; Sec. 9.1)."""
+    I = np.ascontiguousarray(I[:3], dtype=np.float64)
+    out = np.zeros(8)
+    _load().or_coefficients(D, _dp(I), _dp(out))
+    keys = ["c0", "c1", "c2", "cbar2", "cprime2", "thetabar", "J2", "Delta2"]
+    return dict(zip(keys, out.tolist()))
+
+
+def lattice(vel: str, I: np.ndarray):
+    """(e[Q,3], w[Q], opp[Q], c_s) of a lattice from Table lattices-tab; raises
+    ValueError('unstable') when a weight or c_s is not positive (Sec. 8)."""
+    I4 = np.zeros(5)
+    I4[: len(I)] = I
+    e = np.zeros(3 * 27, dtype=np.int32)
+    w = np.zeros(27)
+    opp = np.zeros(27, dtype=np.int32)
+    cs = ctypes.c_double(0.0)
+    q = _load().or_lattice(VEL[vel], _dp(I4), e.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(w),
+                           opp.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(cs))
+    if q == -2:
+        raise ValueError("unstable")
+    if q < 0:
+        raise ValueError("bad lattice")
+    return e[: 3 * q].reshape(q, 3).copy(), w[:q].copy(), opp[:q].copy(), cs.value
+
+
+class Model:
+    """A configured model: lattice + weight + tau + uniform E, B + force mode."""
+
+    def __init__(self, vel: str = "D2V9", stat: str = "fd", theta: float = 1.0 / 270.0, mu: float = 1.0,
+                 tau: float = 0.8, E=(0.0, 0.0, 0.0), B=(0.0, 0.0, 0.0), force: str = "term"):
+        lib = _load()
+        self._buf = ctypes.create_string_buffer(lib.or_model_size())
+        E3 = np.zeros(3)
+        E3[: len(E)] = E
+        B3 = np.zeros(3)
+        B3[: len(B)] = B
+        rc = lib.or_model_init(self._buf, VEL[vel], STAT[stat], theta, mu, tau, _dp(E3), _dp(B3),
+                               FORCE[force])
+        if rc == -2:
+            raise ValueError("unstable lattice (a weight or c_s is not positive)")
+        if rc != 0:
+            raise ValueError("bad model arguments")
+        self.vel, self.stat, self.force, self.tau = vel, stat, force, tau
+        self.D = {"D1V3": 1, "D2V9": 2}.get(vel, 3)
+        self.E = E3.copy()
+        self.B = B3.copy()
+        if self.D < 3:  # the model keeps only the in-plane E and B_z in 2D
+            self.E[2] = 0.0
+            self.B[0] = self.B[1] = 0.0
+        out = np.zeros(12 + 27)
+        self.Q = lib.or_model_constants(self._buf, _dp(out))
+        keys = ["I0", "I2", "I4", "c0", "c1", "c2", "cbar2", "cprime2", "thetabar", "J2", "Delta2", "cs"]
+        self.const = dict(zip(keys, out[:12].tolist()))
+        self.w = out[12: 12 + self.Q].copy()
+        e = np.zeros(3 * 27, dtype=np.int32)
+        opp = np.zeros(27, dtype=np.int32)
+        lib.or_model_velocities(self._buf, e.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                opp.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        self.e = e[: 3 * self.Q].reshape(self.Q, 3).copy()
+        self.opp = opp[: self.Q].copy()
+        self.xi = self.e / self.const["cs"]
+
+    # --- single-cell pieces -------------------------------------------------
+    def equilibrium(self, rho: float, u) -> np.ndarray:
+        u3 = np.zeros(3)
+        u3[: len(u)] = u
+        out = np.zeros(self.Q)
+        _load().or_equilibrium(self._buf, float(rho), _dp(u3), _dp(out))
+        return out
+
+    def force_term(self, rho: float, u, E) -> np.ndarray:
+        u3 = np.zeros(3)
+        u3[: len(u)] = u
+        E3 = np.zeros(3)
+        E3[: len(E)] = E
+        out = np.zeros(self.Q)
+        _load().or_force_term(self._buf, float(rho), _dp(u3), _dp(E3), _dp(out))
+        return out
+
+    def collide_cell(self, fc: np.ndarray, E=None) -> np.ndarray:
+        fc = np.ascontiguousarray(fc, dtype=np.float64)
+        E3 = np.zeros(3)
+        if E is None:
+            E3[:] = self._uniform_E()
+        else:
+            E3[: len(E)] = E
+        out = np.zeros(self.Q)
+        _load().or_collide_cell(self._buf, _dp(fc), _dp(E3), _dp(out))
+        return out
+
+    def _uniform_E(self):
+        return self.E
+
+    # --- grids ---------------------------------------------------------------
+    @staticmethod
+    def _dims(shape):
+        n = list(shape)[::-1]  # shape is (nz, ny, nx) / (ny, nx) -> n = (nx, ny, nz)
+        while len(n) < 3:
+            n.append(1)
+        return np.array(n, dtype=np.int64)
+
+    def init_equilibrium(self, shape, solid, rho, u=None) -> np.ndarray:
+        """f(x, 0) = f^eq(rho(x), u(x)); arrays in C order over `shape`."""
+        n = self._dims(shape)
+        N = int(np.prod(n))
+        solid_a = None if solid is None else np.ascontiguousarray(solid, dtype=np.uint8).reshape(N)
+        rho_a = np.ascontiguousarray(np.broadcast_to(rho, shape), dtype=np.float64).reshape(N)
+        u_a = None
+        if u is not None:
+            u_a = np.ascontiguousarray(u, dtype=np.float64).reshape(self.D * N)
+        f = np.zeros(self.Q * N)
+        _load().or_init_equilibrium(self._buf, n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                    _u8p(solid_a), _dp(rho_a), _dp(u_a), _dp(f))
+        return f
+
+    def step(self, shape, solid, f: np.ndarray, nsteps: int, Efield=None) -> np.ndarray:
+        """Advance f (Q*N, float64) in place by nsteps collide-and-stream steps."""
+        n = self._dims(shape)
+        N = int(np.prod(n))
+        assert f.shape == (self.Q * N,)
+        solid_a = None if solid is None else np.ascontiguousarray(solid, dtype=np.uint8).reshape(N)
+        E_a = None if Efield is None else np.ascontiguousarray(Efield, dtype=np.float64).reshape(self.D * N)
+        tmp = np.empty_like(f)
+        _load().or_step(self._buf, n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _u8p(solid_a),
+                        _dp(E_a), _dp(f), _dp(tmp), int(nsteps))
+        return f
+
+    def moments(self, shape, solid, f: np.ndarray):
+        """(rho[shape], j[D, *shape], totals[4] = (sum rho, sum j_x, sum j_y, sum j_z))."""
+        n = self._dims(shape)
+        N = int(np.prod(n))
+        solid_a = None if solid is None else np.ascontiguousarray(solid, dtype=np.uint8).reshape(N)
+        rho = np.zeros(N)
+        j = np.zeros(self.D * N)
+        tot = np.zeros(4)
+        _load().or_moments(self._buf, n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _u8p(solid_a),
+                           _dp(np.ascontiguousarray(f)), _dp(rho), _dp(j), _dp(tot))
+        return rho.reshape(shape), j.reshape((self.D,) + tuple(shape)), tot
+
+    def trajectory(self, shape, solid, f0: np.ndarray, nsteps: int, Efield=None) -> np.ndarray:
+        """States f_0..f_T stacked as (T+1, Q*N)."""
+        out = np.empty((nsteps + 1, f0.size))
+        out[0] = f0
+        f = f0.copy()
+        for t in range(nsteps):
+            self.step(shape, solid, f, 1, Efield)
+            out[t + 1] = f
+        return out
+
+    def adjoint(self, shape, solid, states: np.ndarray, t_begin: int, t_end: int, wr=None, wj=None,
+                Efield=None):
+        """Reverse sweep over a stored trajectory (states[t] = f_t, t = 0..t_end).
+
+        Loss L = sum_{t_begin < t <= t_end} sum_x wr(x) rho_t(x) + wj(x).j_t(x).
+        Returns dict(loss, lam0[Q*N], gE[D, *shape], gB[3], gtau)."""
+        n = self._dims(shape)
+        N = int(np.prod(n))
+        assert states.shape[0] >= t_end + 1
+        solid_a = None if solid is None else np.ascontiguousarray(solid, dtype=np.uint8).reshape(N)
+        E_a = None if Efield is None else np.ascontiguousarray(Efield, dtype=np.float64).reshape(self.D * N)
+        wr_a = None if wr is None else np.ascontiguousarray(wr, dtype=np.float64).reshape(N)
+        wj_a = None if wj is None else np.ascontiguousarray(wj, dtype=np.float64).reshape(self.D * N)
+        st = np.ascontiguousarray(states[: t_end + 1], dtype=np.float64)
+        lam0 = np.zeros(self.Q * N)
+        gE = np.zeros(self.D * N)
+        gB = np.zeros(3)
+        gtau = np.zeros(1)
+        loss = np.zeros(1)
+        _load().or_adjoint(self._buf, n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _u8p(solid_a),
+                           _dp(E_a), _dp(st), int(t_begin), int(t_end), _dp(wr_a), _dp(wj_a), _dp(lam0),
+                           _dp(gE), _dp(gB), _dp(gtau), _dp(loss))
+        return {"loss": float(loss[0]), "lam0": lam0, "gE": gE.reshape((self.D,) + tuple(shape)),
+                "gB": gB, "gtau": float(gtau[0])}
