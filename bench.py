@@ -1,0 +1,360 @@
+"""Throughput benchmark of the fused semiclassical-LBM step on one GB300.
+
+Workload: 3D porous medium 256^3 on the D3V19 lattice (Boolean spheres of
+radius 6, porosity 0.7, seed 1), Fermi-Dirac weight (theta = 1/270, mu = 1),
+tau = 0.8, E_x = 1e-6, B_z = 1e-3, explicit Lorentz forcing term; populations
+stored as FP16 deviations (FP32 collision).  A step is one fused
+stream-collide-force pass over the whole box; the state (1.2 GB) is larger
+than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the same metric instead (a deliberately slow baseline).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(n=256, radius=6.0, porosity=0.7, seed=1, Ex=1e-6, Bz=1e-3, tau=0.8)
+WORKLOAD_NAME = ("porous-3d-256^3 D3V19 FD(theta=1/270,mu=1) spheres r=6 porosity=0.7 seed=1, "
+                 "tau=0.8 E_x=1e-6 B_z=1e-3 force=term")
+
+# DRAM traffic per launch of the step kernel from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by storage, with the
+# hash of the kernel source it was taken on; reported as null once the
+# source has changed.
+NCU_TRAFFIC = {}
+
+FALLBACK_HBM_GBS = 6800.0
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("lbm_kernels.cu", "lbm_internal.h"):
+        with open(os.path.join(ROOT, "paper_1710_09472_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.samples = []
+        if self.proc is None:
+            return
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        for line in (out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def summary(self):
+        if not getattr(self, "samples", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        smax = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, name in enumerate(names):
+                if s[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def make_geometry():
+    from paper_1710_09472_gb300 import workloads as wl
+
+    n = WORKLOAD["n"]
+    mask, count = wl.boolean_obstacles((n, n, n), WORKLOAD["radius"], WORKLOAD["porosity"], WORKLOAD["seed"])
+    return mask, count
+
+
+def run_gpu(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_1710_09472_gb300.build import build
+    from paper_1710_09472_gb300.lbm import LBM
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        build()
+    dev = torch.device("cuda", local)
+    mask, count = make_geometry()
+    n = WORKLOAD["n"]
+    dims = (n, n, n)
+    E = (WORKLOAD["Ex"], 0.0, 0.0)
+    B = (0.0, 0.0, WORKLOAD["Bz"])
+    mask_d = torch.from_numpy(mask.reshape(-1)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed_forward(storage):
+        sim = LBM("D3V19", dims, WORKLOAD["tau"], E=E, B=B, storage=storage, force="term", stream=stream)
+        sim.set_geometry(mask_d)
+        sim.init_equilibrium()
+        sim.step(args.warmup)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        l0 = sim.launch_count()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            ev0.record(stream)
+            sim.step(args.steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        launches = sim.launch_count() - l0
+        info = sim.info()
+        rho = torch.empty(sim.N, device=dev)
+        j = torch.empty(3 * sim.N, device=dev)
+        tot = sim.moments(rho, j)
+        return sim, ms, launches, info, clk.summary(), (rho, j, tot)
+
+    # primary: FP16-deviation storage
+    sim16, ms16, launches16, info, clocks, m16 = timed_forward("f16")
+    sim16.close()
+    sim32, ms32, launches32, info32, clocks32, m32 = timed_forward("f32")
+    sim32.close()
+
+    # whole-job through the public API with pinned host buffers
+    N = n * n * n
+    mask_h = torch.from_numpy(mask.reshape(-1)).pin_memory()
+    rho_h = torch.ones(N, dtype=torch.float32).pin_memory()
+    u_h = torch.zeros(3 * N, dtype=torch.float32).pin_memory()
+    rho_out = torch.empty(N, dtype=torch.float32).pin_memory()
+    j_out = torch.empty(3 * N, dtype=torch.float32).pin_memory()
+    sim = LBM("D3V19", dims, WORKLOAD["tau"], E=E, B=B, storage="f16", force="term", stream=stream)
+    sim.set_geometry(mask_h)
+    sim.init_equilibrium(rho_h, u_h)
+    sim.step(args.warmup)
+    sim.moments(rho_out, j_out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.set_geometry(mask_h)
+    sim.init_equilibrium(rho_h, u_h)
+    sim.step(args.steps)
+    sim.moments(rho_out, j_out)  # synchronises
+    e2e_s = time.perf_counter() - t0
+    sim.close()
+
+    def rel(a, b):
+        den = float(torch.max(torch.abs(b)))
+        return float(torch.max(torch.abs(a - b))) / den if den > 0 else 0.0
+
+    err_rho = rel(m16[0], m32[0])
+    err_j = rel(m16[1], m32[1])
+
+    # max over ranks
+    times = [ms16, ms32, e2e_s]
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor(times, dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        times = t.tolist()
+    ms16, ms32, e2e_s = times
+    n_fluid = info["n_fluid"]
+    Q = 19
+    peak, peak_kind = hbm_peak()
+
+    def mlups(ms):
+        return world * N * args.steps / (ms * 1e-3) / 1e6
+
+    def roof(ms, b):
+        per_launch_ms = ms / args.steps
+        alg = 2 * Q * b * n_fluid
+        achieved = alg / (per_launch_ms * 1e-3) / 1e9
+        return achieved, alg
+
+    ach16, alg16 = roof(ms16, 2)
+    ach32, alg32 = roof(ms32, 4)
+    src_hash = kernel_source_hash()
+    tr = NCU_TRAFFIC.get("f16")
+    traffic = tr[0] if tr and tr[1] == src_hash else None
+    result = {
+        "metric": "MLUPS",
+        "value": round(mlups(ms16), 1),
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms16 / args.steps, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "storage": "f16-deviation (2^12 scale), FP32 collision",
+                   "cells": N, "fluid_cells": n_fluid, "spheres": count, "parallelism": f"replicas x{world}",
+                   "l2": "state 1.2 GB > 129 MB L2; no flush needed"},
+        "mflups": round(world * n_fluid * args.steps / (ms16 * 1e-3) / 1e6, 1),
+        "roofline": {"bound": "hbm", "achieved": round(ach16, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(ach16 / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "k_step<D3V19,f16,term>", "alg_bytes_per_launch": alg16},
+        "fp32": {"value": round(mlups(ms32), 1), "unit": "MLUPS", "ms_per_step": round(ms32 / args.steps, 5),
+                 "roofline": {"bound": "hbm", "achieved": round(ach32, 1), "peak": peak, "unit": "GB/s",
+                              "frac": round(ach32 / peak, 4), "alg_bytes_per_launch": alg32}},
+        "fp16_vs_fp32": {"rho_rel_linf": err_rho, "j_rel_linf": err_j, "after_steps": args.warmup + args.steps},
+        "e2e": {"value": round(world * N * args.steps / e2e_s / 1e6, 1), "unit": "MLUPS",
+                "h2d_bytes_per_step": int((N + 4 * N + 12 * N) / args.steps),
+                "d2h_bytes_per_step": int((4 * N + 12 * N) / args.steps),
+                "what": "set_geometry + init_equilibrium from pinned host buffers, K steps, moments to pinned host"},
+        "gpu_launches": int(launches16),
+        "clocks": clocks,
+        "kernel_source": src_hash,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(mask)
+    return result
+
+
+def _oracle_sample(mask, box: int):
+    """A box^3 sub-block of the same geometry, periodic, at rest."""
+    import numpy as np
+
+    sub = np.ascontiguousarray(mask[:box, :box, :box])
+    return sub
+
+
+def cpu_baseline(mask, target_s: float = 12.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload."""
+    import numpy as np
+
+    import oracle
+
+    box = 96
+    sub = _oracle_sample(mask, box)
+    shape = sub.shape
+    m = oracle.Model("D3V19", "fd", 1.0 / 270.0, 1.0, tau=WORKLOAD["tau"], E=(WORKLOAD["Ex"], 0, 0),
+                     B=(0, 0, WORKLOAD["Bz"]), force="term")
+    f = m.init_equilibrium(shape, sub, np.ones(shape))
+    t0 = time.perf_counter()
+    m.step(shape, sub, f, 1)
+    one = time.perf_counter() - t0
+    steps = max(1, min(200, int(target_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    m.step(shape, sub, f, steps)
+    dt = time.perf_counter() - t0
+    cells = box ** 3
+    return {"value": round(cells * steps / dt / 1e6, 3), "unit": "MLUPS", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{box}^3 sub-box of the same sphere packing (periodic), {steps} steps, FP64 C with OpenMP"}
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host cores as the reference arm: each step is one
+    oracle time step over a 64^3 sub-box of the same workload."""
+    import numpy as np
+
+    import oracle
+
+    if rank != 0:
+        return None
+    mask, count = make_geometry()
+    box = 64
+    sub = _oracle_sample(mask, box)
+    shape = sub.shape
+    m = oracle.Model("D3V19", "fd", 1.0 / 270.0, 1.0, tau=WORKLOAD["tau"], E=(WORKLOAD["Ex"], 0, 0),
+                     B=(0, 0, WORKLOAD["Bz"]), force="term")
+    f = m.init_equilibrium(shape, sub, np.ones(shape))
+    m.step(shape, sub, f, args.warmup)
+    t0 = time.perf_counter()
+    m.step(shape, sub, f, args.steps)
+    dt = time.perf_counter() - t0
+    v = round(box ** 3 * args.steps / dt / 1e6, 3)
+    sample = f"{box}^3 sub-box of the same sphere packing (periodic), FP64 C oracle with OpenMP"
+    return {"metric": "MLUPS", "value": v, "unit": "MLUPS", "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    res = run_gpu(args, rank, world)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

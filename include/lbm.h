@@ -1,0 +1,187 @@
+/*
+ * lbm.h - C ABI of the GB300 semiclassical lattice Boltzmann library.
+ *
+ * The library advances the isothermal semiclassical (Fermi-Dirac,
+ * Bose-Einstein or Maxwell-Boltzmann weight) lattice Boltzmann model of
+ * Coelho & Doria, "Lattice Boltzmann method for semiclassical fluids",
+ * arXiv 1710.09472, Sec. 9.1, on one CUDA device:
+ *
+ *   f_a(x + e_a, t + 1) = f_a(x, t) - (f_a(x, t) - f^eq_a(x, t)) / tau [+ S_a]
+ *
+ * with the second-order equilibrium of Sec. 9.1 (equivalently Sec. 5.1),
+ * the Lorentz forcing of Sec. 7 (velocity shift or explicit term), halfway
+ * bounce-back on links into solid cells, and a hand-written adjoint.
+ *
+ * Conventions shared by every call:
+ *   - dims = {nx, ny, nz}; 2D lattices take nz = 1.  Cells are numbered
+ *     cell = (z * ny + y) * nx + x (x fastest); N = nx * ny * nz.
+ *   - The box is periodic in every direction; walls and obstacles come
+ *     only from the solid mask.
+ *   - Velocity-set order (rest vector first, then opposite pairs; a odd
+ *     has opposite a + 1):
+ *       D2V9 : 0 (0,0) 1 (1,0) 2 (-1,0) 3 (0,1) 4 (0,-1) 5 (1,1) 6 (-1,-1)
+ *              7 (1,-1) 8 (-1,1)
+ *       D3V19: 0 (0,0,0) 1 (1,0,0) 2 (-1,0,0) 3 (0,1,0) 4 (0,-1,0)
+ *              5 (0,0,1) 6 (0,0,-1) 7 (1,1,0) 8 (-1,-1,0) 9 (1,-1,0)
+ *              10 (-1,1,0) 11 (1,0,1) 12 (-1,0,-1) 13 (1,0,-1) 14 (-1,0,1)
+ *              15 (0,1,1) 16 (0,-1,-1) 17 (0,1,-1) 18 (0,-1,1)
+ *   - Velocities u, currents j = rho u, fields E and B are in the paper's
+ *     xi units (velocity / reference speed c_s, Sec. 8; Sec. 9.3 takes the
+ *     acceleration a = E).  A lattice-unit velocity is c_s * u.
+ *   - Per-cell vector fields are laid out component-major: v[d * N + cell].
+ *   - "State at time t": after t calls' worth of steps, f(x, t) is the
+ *     post-stream (pre-collision) population field.  Moments are those of
+ *     f(x, t): rho = sum_a f_a, rho u = sum_a f_a e_a / c_s (the reading of
+ *     Sec. 9.1 Eq. mac-fields-model-sec-eq without the stray w_a).
+ *   - Pointer arguments marked "host or device" may point to either; the
+ *     library inspects them.  Device pointers must belong to the context's
+ *     device.  Caller buffers are only borrowed for the duration of a call.
+ *   - Calls are asynchronous on the context's stream unless they return
+ *     host values, in which case they synchronise that stream first.
+ *   - Every call returns an lbm_status and never aborts; on error the
+ *     context keeps a message readable with lbm_last_error().
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = 1,      /* a bad size, pointer, enum or parameter */
+    LBM_ERR_UNSTABLE_LATTICE = 2, /* a weight w_a or c_s is not positive (Sec. 8) */
+    LBM_ERR_CUDA = 3,             /* a CUDA runtime call failed; see lbm_last_error */
+    LBM_ERR_OOM = 4,              /* device or host allocation failed */
+    LBM_ERR_NONFINITE = 5,        /* a NaN/Inf appeared in a reduction */
+    LBM_ERR_TIMEOUT = 6,          /* reserved: no call waits on the device without a bound */
+    LBM_ERR_STATE = 7             /* call out of order (e.g. step before init) */
+} lbm_status;
+
+typedef enum { LBM_D2V9 = 0, LBM_D3V19 = 1 } lbm_velset;          /* Sec. 8.2; Table lattices-tab */
+typedef enum { LBM_FD = 0, LBM_BE = 1, LBM_MB = 2 } lbm_stat;      /* Sec. 2, Eq. be-fd-dist-eq */
+typedef enum { LBM_F32 = 0, LBM_F16_DEV = 1, LBM_BF16_DEV = 2 } lbm_dtype;
+typedef enum { LBM_FORCE_SHIFT = 0, LBM_FORCE_TERM = 1 } lbm_force; /* Sec. 7 */
+
+/* Model description.
+ *   vel   : lbm_velset
+ *   stat  : weight omega(xi) (Sec. 2, 9.1): FD 1/(exp((xi^2-mu)/theta)+1),
+ *           BE 1/(exp((xi^2-mu)/theta)-1) with mu < 0,
+ *           MB (2 pi theta)^(-D/2) exp(-xi^2 / 2 theta) (theta = 1: Hermite).
+ *   theta, mu : weight parameters (the paper's electrons: 1/270 and 1).
+ *   force : LBM_FORCE_SHIFT - f^eq evaluated at u + tau (E + u x B)
+ *           (Sec. 7, Eq. u-update-force-term-eq);
+ *           LBM_FORCE_TERM  - explicit source S_a = a_a . grad_u f^eq_a with
+ *           a_a = E + xi_a x B (Sec. 7, Eq. forcing-term-integrals-eq).
+ *   rho0  : reference density of the stored deviations (see lbm_create). */
+typedef struct {
+    int vel;
+    int stat;
+    double theta;
+    double mu;
+    int force;
+    double rho0;
+} lbm_lattice;
+
+/* Create a context and allocate its device buffers.
+ *   dims   : {nx, ny, nz}, each >= 1 (nz == 1 for D2V9); N < 2^31 * 16.
+ *   tau    : BGK relaxation time, > 1/2.
+ *   E, B   : uniform field (3 components each, may be NULL = 0).  In 2D only
+ *            E_x, E_y and B_z act.
+ *   storage: population storage.  Every storage keeps the deviation
+ *            h_a = f_a - rho0 w_a / I_0 from the rest equilibrium at rho0;
+ *            LBM_F32 stores h in FP32, LBM_F16_DEV stores 2^12 h in FP16,
+ *            LBM_BF16_DEV stores h in BF16.  Collision arithmetic is FP32.
+ *   cuda_stream: cudaStream_t to run on (NULL = the legacy default stream).
+ * Host-side set-up derives I_0..I_4 (Sec. 3, Eq. i2n-cont2), the EDF
+ * coefficients (Sec. 5.1) and the lattice weights and c_s (Sec. 8) in FP64.
+ * The new context has no geometry (all fluid) and no state: call
+ * lbm_init_equilibrium before lbm_step.  *out receives the handle; the
+ * caller releases it with lbm_destroy.
+ * Errors: INVALID_ARG, UNSTABLE_LATTICE (a weight or c_s <= 0), OOM, CUDA. */
+lbm_status lbm_create(lbm_ctx** out, const lbm_lattice* lat, const int64_t dims[3], double tau,
+                      const double E[3], const double B[3], int storage, void* cuda_stream);
+
+/* Release every buffer of the context (synchronises its stream).  NULL is a no-op. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Copy the host-side constants into out[0..n-1] (FP64):
+ *   I0 I2 I4 c0 c1 c2 cbar2 cprime2 thetabar J2 Delta2 cs w[0..Q-1]
+ * (Sec. 3 coefficients, Sec. 9.1 thetabar = I2/I0, Sec. 8 weights).
+ * n must be >= 12 + Q.  Errors: INVALID_ARG. */
+lbm_status lbm_constants(const lbm_ctx* ctx, double* out, int n);
+
+/* Read back sizes: out = {D, Q, nx, ny, nz, N, n_fluid, steps_done,
+ * bytes_per_population}.  n must be >= 9.  n_fluid is exact once the
+ * geometry is set (synchronises).  Errors: INVALID_ARG. */
+lbm_status lbm_info(const lbm_ctx* ctx, int64_t* out, int n);
+
+/* Solid geometry (Sec. 9.3 walls, Sec. 9.4 obstacles): solid_mask[N] bytes,
+ * nonzero = solid, host or device.  Links from a fluid cell into a solid cell
+ * bounce back halfway.  Resets the state (call lbm_init_equilibrium again).
+ * Errors: INVALID_ARG, CUDA. */
+lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* solid_mask);
+
+/* Per-cell electric field E(x) (the acceleration of Sec. 7, a_E = E):
+ * E[D * N] FP32, component-major, host or device; copied into the context.
+ * NULL switches back to the uniform E of lbm_create / lbm_set_params.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+lbm_status lbm_set_E_field(lbm_ctx* ctx, const float* E);
+
+/* Change tau, the uniform E and B between steps without reallocating.
+ * E or B may be NULL (unchanged).  Errors: INVALID_ARG (tau <= 1/2). */
+lbm_status lbm_set_params(lbm_ctx* ctx, double tau, const double E[3], const double B[3]);
+
+/* Start state f(x, 0) = f^eq(rho(x), u(x)) on fluid cells (Sec. 9.1 EDF, no
+ * force shift).  rho[N] FP32 (NULL = rho0 everywhere) and u[D * N] FP32 in
+ * xi units (NULL = 0), host or device.  Sets the step counter to 0.
+ * Errors: INVALID_ARG, CUDA. */
+lbm_status lbm_init_equilibrium(lbm_ctx* ctx, const float* rho, const float* u);
+
+/* Advance n >= 0 time steps (collide, then stream; one fused kernel per
+ * step).  Asynchronous.  Errors: STATE (no init), CUDA. */
+lbm_status lbm_step(lbm_ctx* ctx, int64_t n);
+
+/* Moments of the current state f(x, t): rho[N] and j[D * N] (FP32, host or
+ * device, either may be NULL; solid cells get 0), and the FP64 totals over
+ * fluid cells total_rho = sum rho, total_j[3] = sum j (host, either may be
+ * NULL; requesting a total or a host output synchronises).  Totals are
+ * reduced deterministically (fixed tree order).
+ * Errors: STATE, CUDA, NONFINITE (a total is NaN/Inf). */
+lbm_status lbm_moments(lbm_ctx* ctx, float* rho, float* j, double* total_rho, double total_j[3]);
+
+/* Populations of the current state as FP32, f[Q * N] (population-major:
+ * f[a * N + cell]), host or device; solid cells get 0.  deviation == 0 gives
+ * f_a(x, t); deviation != 0 gives the stored deviation h_a = f_a - rho0 w_a / I_0
+ * exactly as the kernels see it (decoded from the storage format).
+ * Errors: STATE, CUDA. */
+lbm_status lbm_get_populations(lbm_ctx* ctx, float* f, int deviation);
+
+/* Serialise / restore the state (raw stored populations plus a header with
+ * lattice, dims, storage, step count and a checksum) to / from host memory.
+ * lbm_save_state with host_buf == NULL only reports the size in *used.
+ * lbm_load_state checks the header against the context.
+ * Errors: INVALID_ARG (short buffer, header mismatch, bad checksum), CUDA. */
+lbm_status lbm_save_state(lbm_ctx* ctx, void* host_buf, size_t cap, size_t* used);
+lbm_status lbm_load_state(lbm_ctx* ctx, const void* host_buf, size_t len);
+
+/* Message of the last failed call on this context ("" if none). */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Static text of a status code. */
+const char* lbm_status_string(lbm_status s);
+
+/* Number of kernels this context has launched so far (host-side counter). */
+int64_t lbm_launch_count(const lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,83 @@
+"""ctypes binding of the C ABI in include/lbm.h (argument marshalling only).
+
+The shared library is ``paper_1710_09472_gb300/_build/liblbm.so``, built in
+tree by ``paper_1710_09472_gb300.build.build()``.  There is no fallback: if
+the library is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "liblbm.so")
+
+LBM_OK = 0
+STATUS = {0: "LBM_OK", 1: "LBM_ERR_INVALID_ARG", 2: "LBM_ERR_UNSTABLE_LATTICE", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_OOM",
+          5: "LBM_ERR_NONFINITE", 6: "LBM_ERR_TIMEOUT", 7: "LBM_ERR_STATE"}
+VEL = {"D2V9": 0, "D3V19": 1}
+STAT = {"fd": 0, "be": 1, "mb": 2}
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+FORCE = {"shift": 0, "term": 1}
+
+# Every symbol include/lbm.h declares, with (restype, argtypes).
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_d = ctypes.c_double
+_i = ctypes.c_int
+SIGNATURES = {
+    "lbm_create": (_i, [ctypes.POINTER(_vp), _vp, _vp, _d, _vp, _vp, _i, _vp]),
+    "lbm_destroy": (None, [_vp]),
+    "lbm_constants": (_i, [_vp, _vp, _i]),
+    "lbm_info": (_i, [_vp, _vp, _i]),
+    "lbm_set_geometry": (_i, [_vp, _vp]),
+    "lbm_set_E_field": (_i, [_vp, _vp]),
+    "lbm_set_params": (_i, [_vp, _d, _vp, _vp]),
+    "lbm_init_equilibrium": (_i, [_vp, _vp, _vp]),
+    "lbm_step": (_i, [_vp, _i64]),
+    "lbm_moments": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "lbm_get_populations": (_i, [_vp, _vp, _i]),
+    "lbm_save_state": (_i, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "lbm_load_state": (_i, [_vp, _vp, ctypes.c_size_t]),
+    "lbm_last_error": (ctypes.c_char_p, [_vp]),
+    "lbm_status_string": (ctypes.c_char_p, [_i]),
+    "lbm_launch_count": (_i64, [_vp]),
+}
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class lbm_lattice(ctypes.Structure):
+    _fields_ = [("vel", ctypes.c_int), ("stat", ctypes.c_int), ("theta", ctypes.c_double),
+                ("mu", ctypes.c_double), ("force", ctypes.c_int), ("rho0", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Load liblbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"liblbm.so is not built ({LIB_PATH}); run paper_1710_09472_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status: int, ctx=None, what: str = ""):
+    if status != LBM_OK:
+        msg = ""
+        if ctx:
+            msg = (load().lbm_last_error(ctx) or b"").decode()
+        raise LBMError(status, f"{what}: {msg}" if what else msg)

@@ -1,0 +1,580 @@
+// Host side of the C ABI declared in include/lbm.h: context lifetime, FP64
+// derivation of the model constants (weight integrals, EDF coefficients,
+// lattice weights), argument marshalling and kernel launches.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "lbm_internal.h"
+
+using lbm::KParams;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Weight integrals I_2N = pi^{D/2} / (2^{N-1} Gamma(N + D/2)) int_0^inf omega
+// xi^{2N+D-1} dxi (Sec. 3, Eq. i2n-cont2), by adaptive Simpson quadrature
+// with Richardson correction, split at the Fermi edge xi = sqrt(mu).
+// ---------------------------------------------------------------------------
+struct Weight {
+    int stat, D, power;
+    double theta, mu;
+    double operator()(double xi) const {
+        double om;
+        if (stat == LBM_MB) {
+            om = std::pow(2.0 * M_PI * theta, -0.5 * D) * std::exp(-0.5 * xi * xi / theta);
+        } else {
+            const double x = (xi * xi - mu) / theta;
+            if (stat == LBM_FD)
+                om = x > 0 ? std::exp(-x) / (1.0 + std::exp(-x)) : 1.0 / (std::exp(x) + 1.0);
+            else
+                om = 1.0 / std::expm1(x);
+        }
+        double pw = 1.0;
+        for (int k = 0; k < power; ++k) pw *= xi;
+        return om * pw;
+    }
+};
+
+bool simpson(const Weight& f, double a, double b, double* result) {
+    struct Seg {
+        double a, b, fa, fm, fb, whole;
+        int depth;
+    };
+    // size estimate on a fixed grid sets the absolute tolerance
+    double est = 0.0;
+    const int n0 = 256;
+    for (int i = 0; i <= n0; ++i) est += std::fabs(f(a + (b - a) * i / n0)) * (b - a) / n0;
+    if (est == 0.0) {
+        *result = 0.0;
+        return true;
+    }
+    const double tol = 1e-17 * est;
+    std::vector<Seg> stack;
+    const double fa = f(a), fb = f(b), fm = f(0.5 * (a + b));
+    stack.push_back({a, b, fa, fm, fb, (b - a) / 6.0 * (fa + 4 * fm + fb), 0});
+    double total = 0.0;
+    long evals = 3;
+    while (!stack.empty()) {
+        Seg s = stack.back();
+        stack.pop_back();
+        const double m = 0.5 * (s.a + s.b);
+        const double lm = 0.5 * (s.a + m), rm = 0.5 * (m + s.b);
+        const double flm = f(lm), frm = f(rm);
+        evals += 2;
+        const double left = (m - s.a) / 6.0 * (s.fa + 4 * flm + s.fm);
+        const double right = (s.b - m) / 6.0 * (s.fm + 4 * frm + s.fb);
+        const double diff = left + right - s.whole;
+        if (std::fabs(diff) <= 15.0 * tol || s.depth >= 48) {
+            total += left + right + diff / 15.0;
+        } else {
+            stack.push_back({s.a, m, s.fa, flm, s.fm, left, s.depth + 1});
+            stack.push_back({m, s.b, s.fm, frm, s.fb, right, s.depth + 1});
+        }
+        if (evals > 50000000L) return false;
+    }
+    *result = total;
+    return true;
+}
+
+bool weight_integrals(int D, int stat, double theta, double mu, double* I /* [5] */) {
+    Weight f{stat, D, 0, theta, mu};
+    double edge, top;
+    if (stat == LBM_MB) {
+        edge = std::sqrt(theta);
+        top = std::sqrt(1600.0 * theta);
+    } else {
+        edge = mu > 0 ? std::sqrt(mu) : std::sqrt(theta);
+        top = std::sqrt((mu > 0 ? mu : 0.0) + 800.0 * theta);
+    }
+    for (int N = 0; N <= 4; ++N) {
+        f.power = 2 * N + D - 1;
+        double s1, s2;
+        if (!simpson(f, 0.0, edge, &s1) || !simpson(f, edge, top, &s2)) return false;
+        const double pref = std::pow(M_PI, 0.5 * D) / (std::pow(2.0, N - 1.0) * std::tgamma(N + 0.5 * D));
+        I[N] = pref * (s1 + s2);
+    }
+    return true;
+}
+
+lbm_status fail(lbm_ctx* c, lbm_status st, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return st;
+}
+
+lbm_status cuda_check(lbm_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return LBM_OK;
+    return fail(c, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(ctx, call)                                   \
+    do {                                                      \
+        lbm_status _st = cuda_check((ctx), (call), #call);    \
+        if (_st != LBM_OK) return _st;                        \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t pop_elem_bytes(int storage) { return storage == LBM_F32 ? 4 : 2; }
+
+KParams make_params(const lbm_ctx* c) {
+    KParams p;
+    std::memset(&p, 0, sizeof p);
+    p.nx = (int)c->nx;
+    p.ny = (int)c->ny;
+    p.nz = (int)c->nz;
+    p.N = c->N;
+    p.omega = (float)(1.0 / c->tau);
+    p.tau = (float)c->tau;
+    p.rho0 = (float)c->lat.rho0;
+    p.A = (float)c->A;
+    p.Bp = (float)(c->Bc / c->cs);
+    p.Cp = (float)(c->Cc / (c->cs * c->cs));
+    p.Gp = (float)(c->G / (c->cs * c->cs));
+    p.H = (float)c->H;
+    p.cs_inv = (float)(1.0 / c->cs);
+    for (int a = 0; a < c->Q; ++a) {
+        p.w[a] = (float)c->w[a];
+        p.f0[a] = (float)(c->lat.rho0 * c->w[a] * c->A);
+    }
+    for (int d = 0; d < 3; ++d) {
+        p.E[d] = (float)c->E[d];
+        p.B[d] = (float)c->B[d];
+    }
+    p.scale = (float)c->scale;
+    p.inv_scale = (float)(1.0 / c->scale);
+    return p;
+}
+
+void sanitize_fields(lbm_ctx* c) {
+    if (c->D == 2) {  // only in-plane E and B_z act in 2D
+        c->E[2] = 0.0;
+        c->B[0] = c->B[1] = 0.0;
+    }
+}
+
+// Device staging for a host-pointer argument of `bytes` bytes.
+lbm_status stage(lbm_ctx* c, size_t bytes) {
+    if (c->stage_bytes >= bytes) return LBM_OK;
+    if (c->stage) cudaFree(c->stage);
+    c->stage = nullptr;
+    c->stage_bytes = 0;
+    LBM_CUDA(c, cudaMalloc((void**)&c->stage, bytes));
+    c->stage_bytes = bytes;
+    return LBM_OK;
+}
+
+lbm_status after_launch(lbm_ctx* c, int n) {
+    c->launches += n;
+    return cuda_check(c, cudaGetLastError(), "kernel launch");
+}
+
+uint32_t checksum(const unsigned char* p, size_t n) {  // FNV-1a
+    uint32_t h = 2166136261u;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 16777619u;
+    }
+    return h;
+}
+
+struct StateHeader {
+    char magic[8];
+    int32_t vel, storage;
+    int64_t nx, ny, nz;
+    int64_t steps;
+    uint64_t payload;
+    uint32_t crc;
+    uint32_t pad;
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_status_string(lbm_status s) {
+    switch (s) {
+        case LBM_OK: return "ok";
+        case LBM_ERR_INVALID_ARG: return "invalid argument";
+        case LBM_ERR_UNSTABLE_LATTICE: return "unstable lattice (a weight or c_s is not positive)";
+        case LBM_ERR_CUDA: return "CUDA error";
+        case LBM_ERR_OOM: return "out of memory";
+        case LBM_ERR_NONFINITE: return "non-finite value";
+        case LBM_ERR_TIMEOUT: return "timeout";
+        case LBM_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int64_t lbm_launch_count(const lbm_ctx* c) { return c ? c->launches : 0; }
+
+lbm_status lbm_create(lbm_ctx** out, const lbm_lattice* lat, const int64_t dims[3], double tau, const double E[3],
+                      const double B[3], int storage, void* cuda_stream) {
+    if (!out || !lat || !dims) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (lat->vel != LBM_D2V9 && lat->vel != LBM_D3V19) return LBM_ERR_INVALID_ARG;
+    if (lat->stat < LBM_FD || lat->stat > LBM_MB) return LBM_ERR_INVALID_ARG;
+    if (lat->force != LBM_FORCE_SHIFT && lat->force != LBM_FORCE_TERM) return LBM_ERR_INVALID_ARG;
+    if (storage < LBM_F32 || storage > LBM_BF16_DEV) return LBM_ERR_INVALID_ARG;
+    if (!(lat->theta > 0.0) || !(tau > 0.5) || !std::isfinite(tau) || !(lat->rho0 > 0.0)) return LBM_ERR_INVALID_ARG;
+    if (lat->stat == LBM_BE && !(lat->mu < 0.0)) return LBM_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (dims[d] < 1 || dims[d] > (1 << 20)) return LBM_ERR_INVALID_ARG;
+    if (lat->vel == LBM_D2V9 && dims[2] != 1) return LBM_ERR_INVALID_ARG;
+    if (dims[1] * dims[2] > 0x7fffffffLL || dims[0] > 0x7fffffffLL) return LBM_ERR_INVALID_ARG;
+
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_ERR_OOM;
+    c->lat = *lat;
+    c->D = lat->vel == LBM_D2V9 ? 2 : 3;
+    c->Q = lat->vel == LBM_D2V9 ? 9 : 19;
+    c->nx = dims[0];
+    c->ny = dims[1];
+    c->nz = dims[2];
+    c->N = dims[0] * dims[1] * dims[2];
+    c->n_fluid = c->N;
+    c->storage = storage;
+    c->tau = tau;
+    c->stream = (cudaStream_t)cuda_stream;
+    for (int d = 0; d < 3; ++d) {
+        c->E[d] = E ? E[d] : 0.0;
+        c->B[d] = B ? B[d] : 0.0;
+    }
+    sanitize_fields(c);
+    c->scale = storage == LBM_F16_DEV ? 4096.0 : 1.0;
+
+    // --- constants (Sec. 3, 5.1, 8, 9.1) ---
+    if (!weight_integrals(c->D, lat->stat, lat->theta, lat->mu, c->I)) {
+        lbm_destroy(c);
+        return LBM_ERR_INVALID_ARG;
+    }
+    const double I0 = c->I[0], I2 = c->I[1], I4 = c->I[2];
+    const int D = c->D;
+    c->J2 = I2 * I2 / (I4 * I0);
+    const double Delta2sq = 2.0 / ((D + 2.0) - c->J2 * D);
+    if (!(Delta2sq > 0.0)) {
+        lbm_destroy(c);
+        return LBM_ERR_UNSTABLE_LATTICE;
+    }
+    c->Delta2 = std::sqrt(Delta2sq);
+    c->c0 = 1.0 / std::sqrt(I0);
+    c->c1 = 1.0 / std::sqrt(I2);
+    c->c2 = 1.0 / std::sqrt(I4);
+    c->cbar2 = c->c2 * (c->Delta2 - 1.0) / D;
+    c->cprime2 = -c->c2 * (I2 / I0) * c->Delta2;
+    c->thetabar = I2 / I0;
+    // direct N = 2 EDF (Sec. 5.1): rho w [1/I0 + xi.u/I2 + (xi.u)^2/(2 I4)
+    //   + u^2 xi^2 (Delta2^2 - 1)/(2 D I4) - u^2 I2 Delta2^2/(2 I0 I4)]
+    c->A = 1.0 / I0;
+    c->Bc = 1.0 / I2;
+    c->Cc = 1.0 / (2.0 * I4);
+    c->G = (Delta2sq - 1.0) / (2.0 * D * I4);
+    c->H = -I2 * Delta2sq / (2.0 * I0 * I4);
+    // lattice (Sec. 8.2 D2V9; Table lattices-tab D3V19); c_s = sqrt(I2/(3 I4))
+    c->cs = std::sqrt(I2 / (3.0 * I4));
+    if (lat->vel == LBM_D2V9) {
+        c->w[0] = I0 * (1.0 - 5.0 * c->J2 / 9.0);
+        for (int a = 1; a <= 4; ++a) c->w[a] = I0 * c->J2 / 9.0;
+        for (int a = 5; a <= 8; ++a) c->w[a] = I0 * c->J2 / 36.0;
+    } else {
+        c->w[0] = I0 * (1.0 - 2.0 * c->J2 / 3.0);
+        for (int a = 1; a <= 6; ++a) c->w[a] = I0 * c->J2 / 18.0;
+        for (int a = 7; a <= 18; ++a) c->w[a] = I0 * c->J2 / 36.0;
+    }
+    bool stable = c->cs > 0.0;
+    for (int a = 0; a < c->Q; ++a) stable = stable && c->w[a] > 0.0;
+    if (!stable) {
+        lbm_destroy(c);
+        return LBM_ERR_UNSTABLE_LATTICE;
+    }
+
+    // --- device buffers ---
+    lbm_status st = LBM_OK;
+    cudaGetDevice(&c->device);
+    const size_t pop_bytes = (size_t)c->Q * (size_t)c->N * pop_elem_bytes(storage);
+    KParams p = make_params(c);
+    c->partials_cap = lbm::moments_partial_count(p);
+    if ((st = cuda_check(c, cudaMalloc(&c->pop[0], pop_bytes), "cudaMalloc populations")) != LBM_OK ||
+        (st = cuda_check(c, cudaMalloc(&c->pop[1], pop_bytes), "cudaMalloc populations")) != LBM_OK ||
+        (st = cuda_check(c, cudaMalloc((void**)&c->nbr, sizeof(uint32_t) * c->N), "cudaMalloc neighbours")) !=
+            LBM_OK ||
+        (st = cuda_check(c, cudaMalloc((void**)&c->mask_dev, c->N), "cudaMalloc mask")) != LBM_OK ||
+        (st = cuda_check(c, cudaMalloc((void**)&c->partials, sizeof(double) * 4 * c->partials_cap),
+                         "cudaMalloc partials")) != LBM_OK ||
+        (st = cuda_check(c, cudaMalloc((void**)&c->totals_dev, sizeof(double) * 4), "cudaMalloc totals")) !=
+            LBM_OK ||
+        (st = cuda_check(c, cudaMalloc((void**)&c->count_dev, sizeof(unsigned long long)), "cudaMalloc count")) !=
+            LBM_OK ||
+        (st = cuda_check(c, cudaMallocHost((void**)&c->totals_host, sizeof(double) * 4), "cudaMallocHost")) !=
+            LBM_OK) {
+        lbm_destroy(c);
+        return st;
+    }
+    // default geometry: all fluid
+    if ((st = cuda_check(c, cudaMemsetAsync(c->mask_dev, 0, c->N, c->stream), "memset mask")) != LBM_OK) {
+        lbm_destroy(c);
+        return st;
+    }
+    cudaMemsetAsync(c->count_dev, 0, sizeof(unsigned long long), c->stream);
+    c->launches += lbm::launch_build_neighbors(c->lat.vel, c->mask_dev, c->nbr, c->count_dev, p, c->stream);
+    if ((st = cuda_check(c, cudaGetLastError(), "neighbour kernel")) != LBM_OK) {
+        lbm_destroy(c);
+        return st;
+    }
+    c->geometry_counted = false;
+    *out = c;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->pop[0]);
+    cudaFree(c->pop[1]);
+    cudaFree(c->nbr);
+    cudaFree(c->mask_dev);
+    cudaFree(c->Efield);
+    cudaFree(c->partials);
+    cudaFree(c->totals_dev);
+    cudaFree(c->count_dev);
+    cudaFree(c->stage);
+    if (c->totals_host) cudaFreeHost(c->totals_host);
+    delete c;
+}
+
+lbm_status lbm_constants(const lbm_ctx* c, double* out, int n) {
+    if (!c || !out || n < 12 + c->Q) return LBM_ERR_INVALID_ARG;
+    const double v[12] = {c->I[0], c->I[1], c->I[2], c->c0, c->c1, c->c2, c->cbar2, c->cprime2,
+                          c->thetabar, c->J2, c->Delta2, c->cs};
+    for (int k = 0; k < 12; ++k) out[k] = v[k];
+    for (int a = 0; a < c->Q; ++a) out[12 + a] = c->w[a];
+    return LBM_OK;
+}
+
+lbm_status lbm_info(const lbm_ctx* cc, int64_t* out, int n) {
+    lbm_ctx* c = const_cast<lbm_ctx*>(cc);
+    if (!c || !out || n < 9) return LBM_ERR_INVALID_ARG;
+    if (!c->geometry_counted) {
+        unsigned long long cnt = 0;
+        LBM_CUDA(c, cudaMemcpyAsync(&cnt, c->count_dev, sizeof cnt, cudaMemcpyDeviceToHost, c->stream));
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->n_fluid = (int64_t)cnt;
+        c->geometry_counted = true;
+    }
+    const int64_t v[9] = {c->D, c->Q, c->nx, c->ny, c->nz, c->N, c->n_fluid, c->steps,
+                          (int64_t)pop_elem_bytes(c->storage)};
+    for (int k = 0; k < 9; ++k) out[k] = v[k];
+    return LBM_OK;
+}
+
+lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* mask) {
+    if (!c || !mask) return fail(c, LBM_ERR_INVALID_ARG, "lbm_set_geometry: null argument");
+    const cudaMemcpyKind kind = is_device_ptr(mask) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    LBM_CUDA(c, cudaMemcpyAsync(c->mask_dev, mask, c->N, kind, c->stream));
+    LBM_CUDA(c, cudaMemsetAsync(c->count_dev, 0, sizeof(unsigned long long), c->stream));
+    KParams p = make_params(c);
+    lbm_status st = after_launch(c, lbm::launch_build_neighbors(c->lat.vel, c->mask_dev, c->nbr, c->count_dev, p,
+                                                                 c->stream));
+    c->geometry_counted = false;
+    c->has_state = false;
+    return st;
+}
+
+lbm_status lbm_set_E_field(lbm_ctx* c, const float* E) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (!E) {
+        c->use_Efield = false;
+        return LBM_OK;
+    }
+    const size_t bytes = sizeof(float) * (size_t)c->D * (size_t)c->N;
+    if (!c->Efield) LBM_CUDA(c, cudaMalloc((void**)&c->Efield, bytes));
+    const cudaMemcpyKind kind = is_device_ptr(E) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    LBM_CUDA(c, cudaMemcpyAsync(c->Efield, E, bytes, kind, c->stream));
+    c->use_Efield = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_params(lbm_ctx* c, double tau, const double E[3], const double B[3]) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (!(tau > 0.5) || !std::isfinite(tau)) return fail(c, LBM_ERR_INVALID_ARG, "tau must be > 1/2");
+    c->tau = tau;
+    for (int d = 0; d < 3; ++d) {
+        if (E) c->E[d] = E[d];
+        if (B) c->B[d] = B[d];
+    }
+    sanitize_fields(c);
+    return LBM_OK;
+}
+
+lbm_status lbm_init_equilibrium(lbm_ctx* c, const float* rho, const float* u) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    const size_t nN = (size_t)c->N;
+    const float* rho_d = rho;
+    const float* u_d = u;
+    const bool rho_host = rho && !is_device_ptr(rho);
+    const bool u_host = u && !is_device_ptr(u);
+    if (rho_host || u_host) {
+        lbm_status st = stage(c, sizeof(float) * nN * (1 + c->D));
+        if (st != LBM_OK) return st;
+        if (rho_host) {
+            LBM_CUDA(c, cudaMemcpyAsync(c->stage, rho, sizeof(float) * nN, cudaMemcpyHostToDevice, c->stream));
+            rho_d = c->stage;
+        }
+        if (u_host) {
+            LBM_CUDA(c, cudaMemcpyAsync(c->stage + nN, u, sizeof(float) * nN * c->D, cudaMemcpyHostToDevice,
+                                        c->stream));
+            u_d = c->stage + nN;
+        }
+    }
+    KParams p = make_params(c);
+    c->cur = 0;
+    lbm_status st = after_launch(c, lbm::launch_init(c->lat.vel, c->storage, c->pop[0], c->nbr, rho_d, u_d, p,
+                                                      c->stream));
+    if (st != LBM_OK) return st;
+    c->has_state = true;
+    c->steps = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int64_t n) {
+    if (!c || n < 0) return fail(c, LBM_ERR_INVALID_ARG, "lbm_step: bad argument");
+    if (!c->has_state) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init_equilibrium");
+    KParams p = make_params(c);
+    const bool ef = c->use_Efield;
+    for (int64_t t = 0; t < n; ++t) {
+        c->launches += lbm::launch_step(c->lat.vel, c->storage, c->lat.force, ef, c->pop[c->cur], c->pop[c->cur ^ 1],
+                                        c->nbr, c->Efield, p, c->stream);
+        c->cur ^= 1;
+    }
+    c->steps += n;
+    return cuda_check(c, cudaGetLastError(), "lbm_step launch");
+}
+
+lbm_status lbm_moments(lbm_ctx* c, float* rho, float* j, double* total_rho, double total_j[3]) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (!c->has_state) return fail(c, LBM_ERR_STATE, "lbm_moments before lbm_init_equilibrium");
+    const size_t nN = (size_t)c->N;
+    const bool rho_host = rho && !is_device_ptr(rho);
+    const bool j_host = j && !is_device_ptr(j);
+    float* rho_d = rho;
+    float* j_d = j;
+    if (rho_host || j_host) {
+        lbm_status st = stage(c, sizeof(float) * nN * (1 + c->D));
+        if (st != LBM_OK) return st;
+        if (rho_host) rho_d = c->stage;
+        if (j_host) j_d = c->stage + nN;
+    }
+    const bool want_totals = total_rho || total_j;
+    KParams p = make_params(c);
+    int64_t np = 0;
+    lbm_status st = after_launch(c, lbm::launch_moments(c->lat.vel, c->storage, c->pop[c->cur], c->nbr, rho_d, j_d,
+                                                         want_totals ? c->partials : nullptr, &np, p, c->stream));
+    if (st != LBM_OK) return st;
+    if (want_totals) {
+        st = after_launch(c, lbm::launch_reduce_partials(c->partials, np, c->totals_dev, c->stream));
+        if (st != LBM_OK) return st;
+        LBM_CUDA(c, cudaMemcpyAsync(c->totals_host, c->totals_dev, sizeof(double) * 4, cudaMemcpyDeviceToHost,
+                                    c->stream));
+    }
+    if (rho_host)
+        LBM_CUDA(c, cudaMemcpyAsync(rho, rho_d, sizeof(float) * nN, cudaMemcpyDeviceToHost, c->stream));
+    if (j_host)
+        LBM_CUDA(c, cudaMemcpyAsync(j, j_d, sizeof(float) * nN * c->D, cudaMemcpyDeviceToHost, c->stream));
+    if (want_totals || rho_host || j_host) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (want_totals) {
+        for (int k = 0; k < 4; ++k)
+            if (!std::isfinite(c->totals_host[k])) return fail(c, LBM_ERR_NONFINITE, "non-finite total moment");
+        if (total_rho) *total_rho = c->totals_host[0];
+        if (total_j)
+            for (int d = 0; d < 3; ++d) total_j[d] = c->totals_host[1 + d];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx* c, float* f, int deviation) {
+    if (!c || !f) return fail(c, LBM_ERR_INVALID_ARG, "lbm_get_populations: null argument");
+    if (!c->has_state) return fail(c, LBM_ERR_STATE, "lbm_get_populations before lbm_init_equilibrium");
+    const size_t bytes = sizeof(float) * (size_t)c->Q * (size_t)c->N;
+    const bool host = !is_device_ptr(f);
+    float* fd = f;
+    if (host) {
+        lbm_status st = stage(c, bytes);
+        if (st != LBM_OK) return st;
+        fd = c->stage;
+    }
+    KParams p = make_params(c);
+    lbm_status st = after_launch(c, lbm::launch_populations(c->lat.vel, c->storage, c->pop[c->cur], c->nbr, fd,
+                                                             deviation != 0, p, c->stream));
+    if (st != LBM_OK) return st;
+    if (host) {
+        LBM_CUDA(c, cudaMemcpyAsync(f, fd, bytes, cudaMemcpyDeviceToHost, c->stream));
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_save_state(lbm_ctx* c, void* host_buf, size_t cap, size_t* used) {
+    if (!c || !used) return LBM_ERR_INVALID_ARG;
+    const size_t payload = (size_t)c->Q * (size_t)c->N * pop_elem_bytes(c->storage);
+    const size_t total = sizeof(StateHeader) + payload;
+    *used = total;
+    if (!host_buf) return LBM_OK;
+    if (cap < total) return fail(c, LBM_ERR_INVALID_ARG, "lbm_save_state: buffer too small");
+    if (!c->has_state) return fail(c, LBM_ERR_STATE, "lbm_save_state without a state");
+    StateHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, "LBMSTAT", 8);
+    h.vel = c->lat.vel;
+    h.storage = c->storage;
+    h.nx = c->nx;
+    h.ny = c->ny;
+    h.nz = c->nz;
+    h.steps = c->steps;
+    h.payload = payload;
+    unsigned char* dst = (unsigned char*)host_buf + sizeof(StateHeader);
+    LBM_CUDA(c, cudaMemcpyAsync(dst, c->pop[c->cur], payload, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    h.crc = checksum(dst, payload);
+    std::memcpy(host_buf, &h, sizeof h);
+    return LBM_OK;
+}
+
+lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t len) {
+    if (!c || !host_buf) return LBM_ERR_INVALID_ARG;
+    if (len < sizeof(StateHeader)) return fail(c, LBM_ERR_INVALID_ARG, "lbm_load_state: short buffer");
+    StateHeader h;
+    std::memcpy(&h, host_buf, sizeof h);
+    const size_t payload = (size_t)c->Q * (size_t)c->N * pop_elem_bytes(c->storage);
+    if (std::memcmp(h.magic, "LBMSTAT", 8) != 0 || h.vel != c->lat.vel || h.storage != c->storage || h.nx != c->nx ||
+        h.ny != c->ny || h.nz != c->nz || h.payload != payload)
+        return fail(c, LBM_ERR_INVALID_ARG, "lbm_load_state: header does not match this context");
+    if (len < sizeof(StateHeader) + payload) return fail(c, LBM_ERR_INVALID_ARG, "lbm_load_state: short buffer");
+    const unsigned char* src = (const unsigned char*)host_buf + sizeof(StateHeader);
+    if (checksum(src, payload) != h.crc) return fail(c, LBM_ERR_INVALID_ARG, "lbm_load_state: checksum mismatch");
+    LBM_CUDA(c, cudaMemcpyAsync(c->pop[c->cur], src, payload, cudaMemcpyHostToDevice, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->steps = h.steps;
+    c->has_state = true;
+    return LBM_OK;
+}
+
+}  // extern "C"

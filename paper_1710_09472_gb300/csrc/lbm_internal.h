@@ -1,0 +1,157 @@
+// Internal declarations of the GB300 semiclassical LBM library: context,
+// lattice and storage traits, kernel parameter block and launchers.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "lbm.h"
+
+namespace lbm {
+
+constexpr int kMaxQ = 19;
+constexpr uint32_t kSolidBit = 0x80000000u;
+
+// ---------------------------------------------------------------------------
+// Lattices (Sec. 8.2 and Table lattices-tab).  Order: rest vector, then
+// opposite pairs (a odd, a + 1 = -e_a), as documented in lbm.h.
+// ---------------------------------------------------------------------------
+struct LatD2V9 {
+    static constexpr int D = 2;
+    static constexpr int Q = 9;
+    __host__ __device__ static constexpr int c(int a, int d) {
+        constexpr signed char t[9][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
+                                         {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
+        return t[a][d];
+    }
+};
+
+struct LatD3V19 {
+    static constexpr int D = 3;
+    static constexpr int Q = 19;
+    __host__ __device__ static constexpr int c(int a, int d) {
+        constexpr signed char t[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                                          {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                          {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                          {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+        return t[a][d];
+    }
+};
+
+__host__ __device__ constexpr int opposite(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
+
+// ---------------------------------------------------------------------------
+// Storage of the deviation h_a = f_a - rho0 w_a / I_0 (scaled by `scale`).
+// ---------------------------------------------------------------------------
+struct StoreF32 {
+    using T = float;
+    static constexpr bool kScaled = false;
+    __device__ __forceinline__ static float load(const T* __restrict__ p, int64_t i, float) { return __ldg(p + i); }
+    __device__ __forceinline__ static void store(T* __restrict__ p, int64_t i, float v, float) { p[i] = v; }
+};
+
+struct StoreF16 {
+    using T = __half;
+    static constexpr bool kScaled = true;
+    __device__ __forceinline__ static float load(const T* __restrict__ p, int64_t i, float inv_scale) {
+        return __half2float(__ldg(p + i)) * inv_scale;
+    }
+    __device__ __forceinline__ static void store(T* __restrict__ p, int64_t i, float v, float scale) {
+        p[i] = __float2half_rn(v * scale);
+    }
+};
+
+struct StoreBF16 {
+    using T = __nv_bfloat16;
+    static constexpr bool kScaled = true;
+    __device__ __forceinline__ static float load(const T* __restrict__ p, int64_t i, float inv_scale) {
+        return __bfloat162float(__ldg(p + i)) * inv_scale;
+    }
+    __device__ __forceinline__ static void store(T* __restrict__ p, int64_t i, float v, float scale) {
+        p[i] = __float2bfloat16_rn(v * scale);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Kernel parameter block (passed by value).  The equilibrium is evaluated in
+// the direct N = 2 form of Sec. 5.1 (Eq. feq-reduce-general-method-without-
+// pol-eq), with xi_a = e_a / c_s folded into the constants:
+//   f^eq_a = rho w_a [A + Bp (e_a.u) + Cp (e_a.u)^2 + (Gp e_a^2 + H) u^2]
+//   A = 1/I0, Bp = 1/(I2 c_s), Cp = 1/(2 I4 c_s^2),
+//   Gp = (Delta2^2 - 1)/(2 D I4 c_s^2), H = -I2 Delta2^2/(2 I0 I4).
+// ---------------------------------------------------------------------------
+struct KParams {
+    int nx, ny, nz;
+    int64_t N;
+    float omega;  // 1 / tau
+    float tau;
+    float rho0;
+    float A, Bp, Cp, Gp, H;
+    float cs_inv;
+    float w[kMaxQ];
+    float f0[kMaxQ];  // rho0 w_a A: the rest equilibrium at rho0
+    float E[3], B[3];
+    float scale, inv_scale;
+};
+
+struct Launch {
+    dim3 grid, block;
+};
+
+// Launchers (lbm_kernels.cu).  Each returns the number of kernels launched.
+int launch_build_neighbors(int vel, const uint8_t* mask, uint32_t* nbr, unsigned long long* fluid_count,
+                           const KParams& p, cudaStream_t s);
+int launch_init(int vel, int storage, void* pop, const uint32_t* nbr, const float* rho, const float* u,
+                const KParams& p, cudaStream_t s);
+int launch_step(int vel, int storage, int force, bool efield, const void* fin, void* fout, const uint32_t* nbr,
+                const float* Ef, const KParams& p, cudaStream_t s);
+int launch_moments(int vel, int storage, const void* pop, const uint32_t* nbr, float* rho, float* j,
+                   double* partials, int64_t* n_partials, const KParams& p, cudaStream_t s);
+int launch_reduce_partials(const double* partials, int64_t n_partials, double* out4, cudaStream_t s);
+int launch_populations(int vel, int storage, const void* pop, const uint32_t* nbr, float* f, bool deviation,
+                       const KParams& p, cudaStream_t s);
+int64_t moments_partial_count(const KParams& p);
+
+}  // namespace lbm
+
+// The context (opaque to C callers).
+struct lbm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    lbm_lattice lat{};
+    int D = 0, Q = 0;
+    int64_t nx = 1, ny = 1, nz = 1, N = 0;
+    int64_t n_fluid = 0;
+    int storage = 0;
+    double tau = 1.0;
+    double E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+    // host-side constants (FP64)
+    double I[5] = {0, 0, 0, 0, 0};
+    double c0 = 0, c1 = 0, c2 = 0, cbar2 = 0, cprime2 = 0, thetabar = 0, J2 = 0, Delta2 = 0, cs = 0;
+    double w[lbm::kMaxQ] = {};
+    double A = 0, Bc = 0, Cc = 0, G = 0, H = 0;
+    double scale = 1.0;
+    // device buffers
+    void* pop[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint32_t* nbr = nullptr;
+    uint8_t* mask_dev = nullptr;
+    float* Efield = nullptr;
+    bool use_Efield = false;
+    double* partials = nullptr;
+    int64_t partials_cap = 0;
+    double* totals_dev = nullptr;
+    double* totals_host = nullptr;  // pinned, 4 doubles
+    unsigned long long* count_dev = nullptr;
+    float* stage = nullptr;  // device staging for host-pointer arguments
+    size_t stage_bytes = 0;
+    bool geometry_counted = false;
+    bool has_state = false;
+    int64_t steps = 0;
+    int64_t launches = 0;
+    std::string err;
+};

@@ -1,0 +1,175 @@
+"""Thin Python front end of liblbm (one context = one simulation box).
+
+Only argument marshalling happens here: arrays are checked for dtype, size
+and contiguity and handed to the C ABI as raw pointers; every step of the
+method runs in the library's CUDA kernels.  Device arrays are torch tensors
+(PyTorch provides device memory and the stream); host arrays may be numpy
+arrays or CPU tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+try:
+    import torch
+except ImportError:  # pragma: no cover - torch is part of the supported stack
+    torch = None
+
+
+def _ptr(a, dtype, count: int, name: str):
+    """Raw pointer of a contiguous array with `count` elements of `dtype`."""
+    if a is None:
+        return None
+    if torch is not None and isinstance(a, torch.Tensor):
+        tdt = {np.float32: torch.float32, np.uint8: torch.uint8, np.float64: torch.float64}[dtype]
+        if a.dtype != tdt:
+            raise TypeError(f"{name}: expected {tdt}, got {a.dtype}")
+        if not a.is_contiguous():
+            raise ValueError(f"{name}: tensor must be contiguous")
+        if a.numel() != count:
+            raise ValueError(f"{name}: expected {count} elements, got {a.numel()}")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype:
+            raise TypeError(f"{name}: expected {np.dtype(dtype)}, got {a.dtype}")
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{name}: array must be C-contiguous")
+        if a.size != count:
+            raise ValueError(f"{name}: expected {count} elements, got {a.size}")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError(f"{name}: unsupported array type {type(a)}")
+
+
+def _vec3(v):
+    if v is None:
+        return None
+    out = (ctypes.c_double * 3)()
+    for i, x in enumerate(list(v)[:3]):
+        out[i] = float(x)
+    return out
+
+
+class LBM:
+    """A semiclassical LBM box on the current CUDA device.
+
+    vel: "D2V9" | "D3V19"; dims: (nx, ny) or (nx, ny, nz); storage: "f32" |
+    "f16" | "bf16" (deviations from the rest equilibrium, collision in FP32);
+    force: "term" (explicit Lorentz term) | "shift" (velocity shift);
+    stat: "fd" | "be" | "mb" weight with (theta, mu)."""
+
+    def __init__(self, vel: str, dims, tau: float, E=(0.0, 0.0, 0.0), B=(0.0, 0.0, 0.0), storage: str = "f32",
+                 force: str = "term", stat: str = "fd", theta: float = 1.0 / 270.0, mu: float = 1.0,
+                 rho0: float = 1.0, stream=None):
+        lib = _lib.load()
+        d = list(dims) + [1] * (3 - len(dims))
+        self.dims = tuple(int(x) for x in d)
+        self.vel, self.storage, self.force = vel, storage, force
+        lat = _lib.lbm_lattice(_lib.VEL[vel], _lib.STAT[stat], float(theta), float(mu), _lib.FORCE[force],
+                               float(rho0))
+        dims_c = (ctypes.c_int64 * 3)(*self.dims)
+        if stream is None and torch is not None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream
+        self._h = ctypes.c_void_p()
+        st = lib.lbm_create(ctypes.byref(self._h), ctypes.byref(lat), dims_c, float(tau), _vec3(E), _vec3(B),
+                            _lib.STORAGE[storage], ctypes.c_void_p(handle or 0))
+        _lib.check(st, None, "lbm_create")
+        info = self.info()
+        self.D, self.Q, self.N = info["D"], info["Q"], info["N"]
+        self.shape = tuple(reversed(self.dims[: self.D]))  # C-order array shape (.., ny, nx)
+
+    # -- lifetime ---------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.load().lbm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- queries ------------------------------------------------------------------
+    def constants(self) -> dict:
+        out = (ctypes.c_double * 40)()
+        _lib.check(_lib.load().lbm_constants(self._h, out, 40), self._h, "lbm_constants")
+        keys = ["I0", "I2", "I4", "c0", "c1", "c2", "cbar2", "cprime2", "thetabar", "J2", "Delta2", "cs"]
+        c = dict(zip(keys, list(out)[:12]))
+        q = 9 if self.vel == "D2V9" else 19
+        c["w"] = np.array(list(out)[12: 12 + q])
+        return c
+
+    def info(self) -> dict:
+        out = (ctypes.c_int64 * 9)()
+        _lib.check(_lib.load().lbm_info(self._h, out, 9), self._h, "lbm_info")
+        keys = ["D", "Q", "nx", "ny", "nz", "N", "n_fluid", "steps", "bytes_per_population"]
+        return dict(zip(keys, list(out)))
+
+    def launch_count(self) -> int:
+        return int(_lib.load().lbm_launch_count(self._h))
+
+    # -- set-up -------------------------------------------------------------------
+    def set_geometry(self, mask):
+        _lib.check(_lib.load().lbm_set_geometry(self._h, _ptr(mask, np.uint8, self.N, "mask")), self._h,
+                   "lbm_set_geometry")
+
+    def set_E_field(self, E):
+        p = None if E is None else _ptr(E, np.float32, self.D * self.N, "E")
+        _lib.check(_lib.load().lbm_set_E_field(self._h, p), self._h, "lbm_set_E_field")
+
+    def set_params(self, tau: float, E=None, B=None):
+        _lib.check(_lib.load().lbm_set_params(self._h, float(tau), _vec3(E), _vec3(B)), self._h, "lbm_set_params")
+
+    def init_equilibrium(self, rho=None, u=None):
+        _lib.check(_lib.load().lbm_init_equilibrium(self._h, _ptr(rho, np.float32, self.N, "rho"),
+                                                    _ptr(u, np.float32, self.D * self.N, "u")), self._h,
+                   "lbm_init_equilibrium")
+
+    # -- the hot path -------------------------------------------------------------
+    def step(self, n: int = 1):
+        _lib.check(_lib.load().lbm_step(self._h, int(n)), self._h, "lbm_step")
+
+    def moments(self, rho=None, j=None, totals: bool = True):
+        """Fill rho[N] / j[D*N] (either may be None) and return
+        (total_rho, total_j[3]) in FP64, or None when totals is False."""
+        tr = ctypes.c_double(0.0) if totals else None
+        tj = (ctypes.c_double * 3)() if totals else None
+        st = _lib.load().lbm_moments(self._h, _ptr(rho, np.float32, self.N, "rho"),
+                                     _ptr(j, np.float32, self.D * self.N, "j"),
+                                     ctypes.byref(tr) if totals else None, tj)
+        _lib.check(st, self._h, "lbm_moments")
+        if totals:
+            return tr.value, np.array(list(tj))
+        return None
+
+    def populations(self, out=None, deviation: bool = False):
+        """f_a(x, t) (or the stored deviations h_a when deviation=True), Q*N FP32."""
+        if out is None:
+            out = np.empty(self.Q * self.N, dtype=np.float32)
+        _lib.check(_lib.load().lbm_get_populations(self._h, _ptr(out, np.float32, self.Q * self.N, "f"),
+                                                   int(bool(deviation))), self._h, "lbm_get_populations")
+        return out
+
+    def save_state(self) -> bytes:
+        used = ctypes.c_size_t(0)
+        lib = _lib.load()
+        _lib.check(lib.lbm_save_state(self._h, None, 0, ctypes.byref(used)), self._h, "lbm_save_state")
+        buf = ctypes.create_string_buffer(used.value)
+        _lib.check(lib.lbm_save_state(self._h, buf, used.value, ctypes.byref(used)), self._h, "lbm_save_state")
+        return buf.raw
+
+    def load_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _lib.check(_lib.load().lbm_load_state(self._h, buf, len(blob)), self._h, "lbm_load_state")

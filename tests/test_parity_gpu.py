@@ -1,0 +1,328 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative L-inf on rho and j after the run): FP32 storage 1e-5,
+FP16/BF16 deviation storage 2e-3."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1710_09472_gb300 import workloads as wl
+from tests.conftest import load_golden
+from tests.helpers import TOL, THETA, gpu_run, oracle_run, rel_linf
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_09472_gb300.build import build
+
+    build()
+
+
+def _fields(shape, D, seed, amp_u=0.01, amp_rho=0.02):
+    N = int(np.prod(shape))
+    rho = (1.0 + amp_rho * (wl.uniform01(seed, N) - 0.5)).reshape(shape).astype(np.float32)
+    u = (amp_u * wl.normal(seed + 1, D * N)).reshape((D,) + tuple(shape)).astype(np.float32)
+    return rho, u
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("vel,fname", [("D2V9", "constants_2d.txt"), ("D3V19", "constants_3d.txt")])
+def test_library_constants_match_printed_tables(vel, fname):
+    from paper_1710_09472_gb300.lbm import LBM
+
+    g = load_golden(fname)
+    dims = (4, 4) if vel == "D2V9" else (4, 4, 4)
+    sim = LBM(vel, dims, 0.8)
+    c = sim.constants()
+    for k in ["c0", "c1", "c2", "cbar2", "cprime2", "thetabar", "cs"]:
+        assert abs(c[k] / g[k] - 1) < 1e-12, k
+    assert abs(c["w"][0] / g["w0"] - 1) < 1e-12
+    assert abs(c["w"][1] / g["ws"] - 1) < 1e-12
+    assert abs(c["w"][-1] / g["wl"] - 1) < 1e-12
+    sim.close()
+
+
+CASES_2D = [(s, f, e) for s in ("f32", "f16", "bf16") for f in ("term", "shift") for e in (False, True)]
+
+
+@pytest.mark.parametrize("storage,force,efield", CASES_2D)
+def test_parity_2d_ragged(storage, force, efield):
+    """D2V9 on 37 x 150 (x: one full 128-wide tile plus a ragged 22-cell tail),
+    disks, B_z != 0, 60 steps."""
+    shape = (37, 150)
+    solid, _ = wl.boolean_obstacles(shape, 3.0, 0.8, seed=41)
+    rho, u = _fields(shape, 2, 42)
+    E = (2e-4, -5e-5, 0.0)
+    B = (0.0, 0.0, 3e-3)
+    Ef = None
+    if efield:
+        Ef = np.stack([2e-4 + 2e-5 * wl.normal(43, solid.size).reshape(shape),
+                       -5e-5 + 1e-5 * wl.normal(44, solid.size).reshape(shape)]).astype(np.float32)
+    T = 60
+    rg, jg, totg, sim = gpu_run("D2V9", shape, solid, 0.7, T, storage, force, E, B, rho, u, Ef)
+    ro, jo, toto, _, _ = oracle_run("D2V9", shape, solid, 0.7, T, force, E, B, rho, u, Ef)
+    er, ej = rel_linf(rg, ro), rel_linf(jg, jo)
+    assert er <= TOL[storage] and ej <= TOL[storage], (er, ej)
+    assert abs(totg[0] / toto[0] - 1) < 1e-6
+    sim.close()
+
+
+CASES_3D = [(s, f, e) for s in ("f32", "f16", "bf16") for f in ("term", "shift") for e in (False, True)]
+
+
+@pytest.mark.parametrize("storage,force,efield", CASES_3D)
+def test_parity_3d_ragged(storage, force, efield):
+    """D3V19 on 9 x 10 x 133 (ragged x tail), spheres, B oblique, 40 steps."""
+    shape = (9, 10, 133)
+    solid, _ = wl.boolean_obstacles(shape, 2.5, 0.75, seed=51)
+    rho, u = _fields(shape, 3, 52)
+    E = (1e-4, 3e-5, -2e-5)
+    B = (1e-3, -2e-3, 3e-3)
+    Ef = None
+    if efield:
+        Ef = (np.array(E)[:, None, None, None] * (1 + 0.1 * wl.normal(53, 3 * solid.size).reshape((3,) + shape))
+              ).astype(np.float32)
+    T = 40
+    rg, jg, totg, sim = gpu_run("D3V19", shape, solid, 0.8, T, storage, force, E, B, rho, u, Ef)
+    ro, jo, toto, _, _ = oracle_run("D3V19", shape, solid, 0.8, T, force, E, B, rho, u, Ef)
+    er, ej = rel_linf(rg, ro), rel_linf(jg, jo)
+    assert er <= TOL[storage] and ej <= TOL[storage], (er, ej)
+    sim.close()
+
+
+@pytest.mark.parametrize("vel", ["D2V9", "D3V19"])
+def test_populations_elementwise(vel):
+    """Every population of every cell after a few steps (FP32 storage)."""
+    shape = (13, 70) if vel == "D2V9" else (6, 7, 40)
+    D = len(shape)
+    solid, _ = wl.boolean_obstacles(shape, 2.0, 0.8, seed=61)
+    rho, u = _fields(shape, D, 62)
+    E = (1e-4, 2e-5, 1e-5)
+    B = (0.0, 0.0, 1e-3) if D == 2 else (1e-3, 1e-3, 1e-3)
+    rg, jg, totg, sim = gpu_run(vel, shape, solid, 0.75, 9, "f32", "term", E, B, rho, u)
+    fg = sim.populations().astype(np.float64).reshape(sim.Q, -1)
+    _, _, _, m, fo = oracle_run(vel, shape, solid, 0.75, 9, "term", E, B, rho, u)
+    fo = fo.reshape(m.Q, -1)
+    assert np.max(np.abs(fg - fo)) <= 2e-7 * np.max(np.abs(fo))
+    sim.close()
+
+
+def test_config_poiseuille_32x64():
+    """Config: Poiseuille 32 x 64, E_x = 1e-6, tau = 0.8, 5000 steps (shift
+    forcing, as in Sec. 9.3)."""
+    w = wl.poiseuille_32x64()
+    ro, jo, toto, _, _ = oracle_run("D2V9", w["shape"], w["solid"], w["tau"], w["steps"], "shift", w["E"])
+    for storage in ("f32", "f16", "bf16"):
+        rg, jg, totg, sim = gpu_run("D2V9", w["shape"], w["solid"], w["tau"], w["steps"], storage, "shift", w["E"])
+        er, ej = rel_linf(rg, ro), rel_linf(jg, jo)
+        print(f"poiseuille {storage}: rho {er:.3e} j {ej:.3e}")
+        if storage != "bf16":
+            assert er <= TOL[storage] and ej <= TOL[storage], (storage, er, ej)
+        sim.close()
+
+
+def test_config_riemann_4096x8():
+    """Config: Riemann 4096 x 8, rho 1.05 | 1.0, tau = 0.6, 2000 steps."""
+    w = wl.riemann_4096x8()
+    rho = w["rho"].astype(np.float32)
+    ro, jo, toto, _, _ = oracle_run("D2V9", w["shape"], w["solid"], w["tau"], w["steps"], "term", rho=rho)
+    for storage in ("f32", "f16", "bf16"):
+        rg, jg, totg, sim = gpu_run("D2V9", w["shape"], w["solid"], w["tau"], w["steps"], storage, "term", rho=rho)
+        er, ej = rel_linf(rg, ro), rel_linf(jg, jo)
+        print(f"riemann {storage}: rho {er:.3e} j {ej:.3e}")
+        if storage != "bf16":
+            assert er <= TOL[storage] and ej <= TOL[storage], (storage, er, ej)
+        sim.close()
+
+
+# ---------------------------------------------------------------------------
+# Full bench size: sampled one-step checks and conservation properties.
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def porous256():
+    return wl.porous_3d(256, Ex=1e-6, Bz=1e-3, steps=0)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_porous256_sampled_one_step(porous256, storage):
+    """At 256^3 (the benchmark launch configuration): take the stored state after
+    30 steps, let the oracle collide-and-stream it at 4000 sampled fluid cells
+    and compare with the GPU's next state there."""
+    from paper_1710_09472_gb300.lbm import LBM
+
+    w = porous256
+    shape = w["shape"]
+    dev = torch.device("cuda")
+    sim = LBM("D3V19", tuple(reversed(shape)), w["tau"], E=w["E"], B=w["B"], storage=storage, force="term")
+    sim.set_geometry(torch.from_numpy(w["solid"].reshape(-1)).to(dev))
+    sim.init_equilibrium()
+    sim.step(30)
+    Q, N = sim.Q, sim.N
+    h_t = torch.empty(Q * N, dtype=torch.float32, device=dev)
+    sim.populations(h_t, deviation=True)
+    sim.step(1)
+    h_t1 = torch.empty(Q * N, dtype=torch.float32, device=dev)
+    sim.populations(h_t1, deviation=True)
+    torch.cuda.synchronize()
+    m = oracle.Model("D3V19", "fd", THETA, 1.0, tau=w["tau"], E=w["E"], B=w["B"], force="term")
+    f0 = 1.0 * m.w / m.const["I0"]
+    solid = w["solid"].reshape(-1)
+    fluid_idx = np.flatnonzero(solid == 0)
+    rng = np.random.default_rng(7)
+    sample = rng.choice(fluid_idx, 4000, replace=False)
+    nx, ny, nz = sim.dims
+    ht = h_t.view(Q, N).cpu().numpy()
+    ht1 = h_t1.view(Q, N).cpu().numpy()
+    err = 0.0
+    scale = 0.0
+    for cell in sample:
+        x, y, z = cell % nx, (cell // nx) % ny, cell // (nx * ny)
+        expect = np.empty(Q)
+        # f_{t+1,a}(x) = C(f_t)(x - e_a)_a, or C(f_t)(x)_abar if x - e_a is solid
+        cache = {}
+        for a in range(Q):
+            ex, ey, ez = m.e[a]
+            src = (((z - ez) % nz) * ny + (y - ey) % ny) * nx + (x - ex) % nx
+            if solid[src]:
+                src_cell, comp = cell, m.opp[a]
+            else:
+                src_cell, comp = src, a
+            if src_cell not in cache:
+                fc = ht[:, src_cell].astype(np.float64) + f0
+                cache[src_cell] = m.collide_cell(fc) - f0
+            expect[a] = cache[src_cell][comp]
+        err = max(err, float(np.max(np.abs(ht1[:, cell] - expect))))
+        scale = max(scale, float(np.max(np.abs(expect))))
+    # FP32: a few ulps of the deviations; FP16: the storage rounding (2^-11 relative)
+    tol = 1e-5 * scale if storage == "f32" else 2.0 ** -10 * scale
+    assert err <= tol, (err, scale)
+    sim.close()
+
+
+def test_porous256_mass_conserved(porous256):
+    """sum rho over fluid cells is conserved (bounce-back + BGK), FP64 totals."""
+    from paper_1710_09472_gb300.lbm import LBM
+
+    w = porous256
+    for storage in ("f32", "f16"):
+        sim = LBM("D3V19", tuple(reversed(w["shape"])), w["tau"], E=(1e-5, 0, 0), B=(0, 0, 1e-3), storage=storage)
+        sim.set_geometry(torch.from_numpy(w["solid"].reshape(-1)).cuda())
+        sim.init_equilibrium()
+        m0, _ = sim.moments()
+        sim.step(100)
+        m1, j1 = sim.moments()
+        assert abs(m1 / m0 - 1) < 1e-9, (storage, m0, m1)
+        assert sim.info()["n_fluid"] == int((w["solid"] == 0).sum())
+        sim.close()
+
+
+@pytest.mark.parametrize("force", ["term", "shift"])
+def test_periodic_momentum_growth(force):
+    """Periodic box without obstacles: sum j grows by sum rho E each step."""
+    from paper_1710_09472_gb300.lbm import LBM
+
+    E = (2e-5, -1e-5, 5e-6)
+    sim = LBM("D3V19", (64, 48, 40), 0.8, E=E, force=force)
+    sim.init_equilibrium()
+    m0, j0 = sim.moments()
+    sim.step(50)
+    m1, j1 = sim.moments()
+    for d in range(3):
+        assert abs(j1[d] - j0[d] - 50 * m0 * E[d]) < 1e-4 * abs(50 * m0 * E[d]) + 1e-9
+    sim.close()
+
+
+# ---------------------------------------------------------------------------
+# Edge cases and the C-ABI contract.
+# ---------------------------------------------------------------------------
+def test_degenerate_domains():
+    from paper_1710_09472_gb300.lbm import LBM
+
+    # one periodic cell (every neighbour is the cell itself), uniform force
+    for vel, dims in (("D2V9", (1, 1)), ("D3V19", (1, 1, 1))):
+        shape = tuple(reversed(dims))
+        rg, jg, tot, sim = gpu_run(vel, shape, None, 0.8, 10, "f32", "term", (1e-4, 0, 0))
+        ro, jo, toto, _, _ = oracle_run(vel, shape, None, 0.8, 10, "term", (1e-4, 0, 0))
+        assert rel_linf(rg, ro) < 1e-6 and rel_linf(jg, jo) < 1e-5
+        sim.close()
+    # a fully solid box: nothing moves, totals are zero
+    sim = LBM("D2V9", (16, 8), 0.8)
+    sim.set_geometry(np.ones(128, dtype=np.uint8))
+    sim.init_equilibrium()
+    sim.step(3)
+    m, j = sim.moments()
+    assert m == 0.0 and np.all(j == 0.0)
+    assert sim.info()["n_fluid"] == 0
+    sim.close()
+    # channel one cell wide in x, zero steps
+    sim = LBM("D2V9", (1, 64), 0.8, E=(1e-6, 0))
+    sim.set_geometry(wl.channel_mask((64, 1)).reshape(-1))
+    sim.init_equilibrium()
+    m0, _ = sim.moments()
+    sim.step(0)
+    m1, _ = sim.moments()
+    assert m0 == m1 == 62.0
+    sim.close()
+
+
+def test_host_and_device_pointers_agree():
+    from paper_1710_09472_gb300.lbm import LBM
+
+    shape = (20, 36)
+    solid, _ = wl.boolean_obstacles(shape, 2.0, 0.85, seed=71)
+    rho, u = _fields(shape, 2, 72)
+    outs = []
+    for where in ("host", "device"):
+        sim = LBM("D2V9", (36, 20), 0.7, E=(1e-4, 0))
+        conv = (lambda a: a.reshape(-1)) if where == "host" else (lambda a: torch.from_numpy(a.reshape(-1)).cuda())
+        sim.set_geometry(conv(solid))
+        sim.init_equilibrium(conv(rho), conv(u))
+        sim.step(7)
+        if where == "host":
+            r = np.empty(sim.N, np.float32)
+            j = np.empty(2 * sim.N, np.float32)
+            tot = sim.moments(r, j)
+        else:
+            r_d = torch.empty(sim.N, device="cuda")
+            j_d = torch.empty(2 * sim.N, device="cuda")
+            tot = sim.moments(r_d, j_d)
+            r, j = r_d.cpu().numpy(), j_d.cpu().numpy()
+        outs.append((r, j, tot))
+        sim.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2][0] == outs[1][2][0]
+
+
+def test_save_load_roundtrip_and_errors():
+    from paper_1710_09472_gb300._lib import LBMError
+    from paper_1710_09472_gb300.lbm import LBM
+
+    sim = LBM("D3V19", (10, 9, 8), 0.8, E=(1e-4, 0, 0), storage="f16")
+    with pytest.raises(LBMError):
+        sim.step(1)  # before init: LBM_ERR_STATE
+    sim.init_equilibrium()
+    sim.step(5)
+    blob = sim.save_state()
+    sim.step(5)
+    a = sim.populations()
+    sim.load_state(blob)
+    assert sim.info()["steps"] == 5
+    sim.step(5)
+    b = sim.populations()
+    assert np.array_equal(a, b)
+    bad = bytearray(blob)
+    bad[-1] ^= 0xFF
+    with pytest.raises(LBMError):
+        sim.load_state(bytes(bad))
+    with pytest.raises(LBMError):
+        sim.set_params(0.5)
+    sim.close()
+    with pytest.raises(LBMError):
+        LBM("D2V9", (8, 8, 2), 0.8)  # a 2D lattice needs nz = 1
+    with pytest.raises(LBMError):
+        LBM("D2V9", (8, 8), 0.4)
