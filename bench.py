@@ -170,6 +170,30 @@ def run_gpu(args, rank, world):
     sim32, ms32, launches32, info32, clocks32, m32 = timed_forward("f32")
     sim32.close()
 
+    # forward + adjoint: lbm_adjoint over T steps (loss = mean x-current after
+    # the last step), checkpoints every K steps, per-cell dL/dE in FP64
+    T_adj, K_adj = args.adjoint_steps, args.adjoint_checkpoint
+    sim = LBM("D3V19", dims, WORKLOAD["tau"], E=E, B=B, storage="f16", force="term", stream=stream)
+    sim.set_geometry(mask_d)
+    sim.init_equilibrium()
+    n_fluid_a = sim.info()["n_fluid"]
+    wj = torch.zeros(3 * sim.N, dtype=torch.float32, device=dev)
+    wj[: sim.N] = 1.0 / n_fluid_a
+    dE = torch.empty(3 * sim.N, dtype=torch.float64, device=dev)
+    sim.adjoint(T_adj - 1, T_adj, None, wj, K_adj, dL_dE=dE)  # warm-up (allocations, clocks)
+    sim.init_equilibrium()
+    torch.cuda.synchronize()
+    l0 = sim.launch_count()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    adj = sim.adjoint(T_adj - 1, T_adj, None, wj, K_adj, dL_dE=dE)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms_adj = a0.elapsed_time(a1)
+    adj_launches = sim.launch_count() - l0
+    sim.close()
+
     # whole-job through the public API with pinned host buffers
     N = n * n * n
     mask_h = torch.from_numpy(mask.reshape(-1)).pin_memory()
@@ -199,14 +223,14 @@ def run_gpu(args, rank, world):
     err_j = rel(m16[1], m32[1])
 
     # max over ranks
-    times = [ms16, ms32, e2e_s]
+    times = [ms16, ms32, e2e_s, ms_adj]
     if world > 1:
         import torch.distributed as dist
 
         t = torch.tensor(times, dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         times = t.tolist()
-    ms16, ms32, e2e_s = times
+    ms16, ms32, e2e_s, ms_adj = times
     n_fluid = info["n_fluid"]
     Q = 19
     peak, peak_kind = hbm_peak()
@@ -248,6 +272,14 @@ def run_gpu(args, rank, world):
         "fp32": {"value": round(mlups(ms32), 1), "unit": "MLUPS", "ms_per_step": round(ms32 / args.steps, 5),
                  "roofline": {"bound": "hbm", "achieved": round(ach32, 1), "peak": peak, "unit": "GB/s",
                               "frac": round(ach32 / peak, 4), "alg_bytes_per_launch": alg32}},
+        "fwd_adjoint": {
+            "value": round(world * N * T_adj / (ms_adj * 1e-3) / 1e6, 1), "unit": "MLUPS",
+            "steps": T_adj, "checkpoint_every": K_adj, "ms_per_step": round(ms_adj / T_adj, 5),
+            "cost_vs_forward_step": round((ms_adj / T_adj) / (ms16 / args.steps), 3),
+            "what": ("one lbm_adjoint call: T forward steps with checkpoints, segment replay storing every "
+                     "state, T reverse steps (FP64 per-cell dL/dE, dL/dB, dL/dtau); loss = mean x-current "
+                     "after the last step; storage f16-deviation"),
+            "launches": int(adj_launches), "dL_dtau": adj["dL_dtau"], "dL_dBz": float(adj["dL_dB"][2])},
         "fp16_vs_fp32": {"rho_rel_linf": err_rho, "j_rel_linf": err_j, "after_steps": args.warmup + args.steps},
         "e2e": {"value": round(world * N * args.steps / e2e_s / 1e6, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": int((N + 4 * N + 12 * N) / args.steps),
@@ -333,6 +365,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--adjoint-checkpoint", type=int, default=14)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

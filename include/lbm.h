@@ -163,6 +163,44 @@ lbm_status lbm_moments(lbm_ctx* ctx, float* rho, float* j, double* total_rho, do
  * Errors: STATE, CUDA. */
 lbm_status lbm_get_populations(lbm_ctx* ctx, float* f, int deviation);
 
+/* Advance t_end steps from the current state and return the window sums of
+ * the FP64 fluid totals over the states after steps t_begin+1 .. t_end:
+ *   out = {sum_t sum_x rho, sum_t sum_x j_x, sum_t sum_x j_y, sum_t sum_x j_z}.
+ * t_begin = -1 includes the start state.  Requires -1 <= t_begin <= t_end.
+ * Synchronises.  Errors: INVALID_ARG, STATE, CUDA, NONFINITE. */
+lbm_status lbm_window_totals(lbm_ctx* ctx, int64_t t_begin, int64_t t_end, double out[4]);
+
+/* Reverse-mode gradient of a linear functional of the trajectory that starts
+ * at the current state f_0 (this is an addition to the paper's method: a
+ * hand-written adjoint of the Sec. 9.1 step, with the Sec. 7 forcing):
+ *   L = sum_{t_begin < t <= t_end} sum_x [w_rho(x) rho_t(x) + w_j(x) . j_t(x)],
+ * where rho_t, j_t are the moments after t steps (lbm_moments convention).
+ * The call runs t_end forward steps (leaving the context at step t_end, as
+ * lbm_step would), keeping a copy of the state every checkpoint_every steps
+ * (0 = about sqrt(t_end)), then sweeps backwards segment by segment: each
+ * segment is replayed forward from its checkpoint storing every state, and
+ * the reverse step kernel maps lam_{t+1} = dL/df_{t+1} to lam_t.
+ *   w_rho[N], w_j[D * N] : FP32 loss weights, host or device, NULL = 0.
+ *   t_begin, t_end       : -1 <= t_begin < t_end, t_end >= 1.
+ *   dL_dE   : [D * N] FP64 device, per-cell dL/dE(x) (overwritten), or NULL.
+ *             With a uniform E, sum_x dL/dE(x) is the uniform-field gradient.
+ *   dL_dB   : 3 host doubles, dL/dB (2D: only the z component), or NULL.
+ *   dL_dtau : host double, or NULL.   loss : host double (L itself), or NULL.
+ *   dL_df0  : [Q * N] FP32 device, dL/df_0 (population layout), or NULL.
+ * Device memory: (ceil(t_end / K) + K - 1) copies of the stored populations
+ * plus two FP32 adjoint fields, allocated for the call and released before it
+ * returns.  Gradients accumulate in FP64; the sweep is deterministic.
+ * Synchronises.  Errors: INVALID_ARG, STATE, OOM (with the size needed), CUDA,
+ * NONFINITE. */
+lbm_status lbm_adjoint(lbm_ctx* ctx, const float* w_rho, const float* w_j, int64_t t_begin, int64_t t_end,
+                       int64_t checkpoint_every, double* dL_dE, double dL_dB[3], double* dL_dtau, double* loss,
+                       float* dL_df0);
+
+/* FP64 weight integrals I_0, I_2, ..., I_8 of the weight omega (Sec. 3, Eq.
+ * i2n-cont2) in dimension D, for stat / theta / mu as in lbm_lattice.
+ * Host only; needs no device.  Errors: INVALID_ARG. */
+lbm_status lbm_weight_integrals(int D, int stat, double theta, double mu, double I[5]);
+
 /* Serialise / restore the state (raw stored populations plus a header with
  * lattice, dims, storage, step count and a checksum) to / from host memory.
  * lbm_save_state with host_buf == NULL only reports the size in *used.

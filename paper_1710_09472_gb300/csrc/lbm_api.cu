@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -51,11 +52,11 @@ bool simpson(const Weight& f, double a, double b, double* result) {
         *result = 0.0;
         return true;
     }
-    const double tol = 1e-17 * est;
+    const double tol = 2e-18 * est;
     std::vector<Seg> stack;
     const double fa = f(a), fb = f(b), fm = f(0.5 * (a + b));
     stack.push_back({a, b, fa, fm, fb, (b - a) / 6.0 * (fa + 4 * fm + fb), 0});
-    double total = 0.0;
+    double total = 0.0, comp = 0.0;  // Kahan-compensated sum of accepted panels
     long evals = 3;
     while (!stack.empty()) {
         Seg s = stack.back();
@@ -68,7 +69,10 @@ bool simpson(const Weight& f, double a, double b, double* result) {
         const double right = (s.b - m) / 6.0 * (s.fm + 4 * frm + s.fb);
         const double diff = left + right - s.whole;
         if (std::fabs(diff) <= 15.0 * tol || s.depth >= 48) {
-            total += left + right + diff / 15.0;
+            const double y = (left + right + diff / 15.0) - comp;
+            const double t = total + y;
+            comp = (t - total) - y;
+            total = t;
         } else {
             stack.push_back({s.a, m, s.fa, flm, s.fm, left, s.depth + 1});
             stack.push_back({m, s.b, s.fm, frm, s.fb, right, s.depth + 1});
@@ -149,9 +153,16 @@ KParams make_params(const lbm_ctx* c) {
     p.Cp = (float)(c->Cc / (c->cs * c->cs));
     p.Gp = (float)(c->G / (c->cs * c->cs));
     p.H = (float)c->H;
+    p.cs = (float)c->cs;
     p.cs_inv = (float)(1.0 / c->cs);
     for (int a = 0; a < c->Q; ++a) {
+        const int e2 = (a == 0) ? 0 : (c->Q == 9 ? (a <= 4 ? 1 : 2) : (a <= 6 ? 1 : 2));
         p.w[a] = (float)c->w[a];
+        p.k2[a] = (float)(c->G * e2 / (c->cs * c->cs) + c->H);
+        // W1_a = w_a Bp / c_s = w_a / (I2 c_s^2) as a double-float pair
+        const double W1 = c->w[a] * c->Bc / (c->cs * c->cs);
+        p.W1hi[a] = (float)W1;
+        p.W1lo[a] = (float)(W1 - (double)p.W1hi[a]);
         p.f0[a] = (float)(c->lat.rho0 * c->w[a] * c->A);
     }
     for (int d = 0; d < 3; ++d) {
@@ -221,6 +232,12 @@ const char* lbm_status_string(lbm_status s) {
         case LBM_ERR_STATE: return "call out of order";
     }
     return "unknown status";
+}
+
+lbm_status lbm_weight_integrals(int D, int stat, double theta, double mu, double I[5]) {
+    if (!I || D < 1 || D > 3 || stat < LBM_FD || stat > LBM_MB || !(theta > 0.0)) return LBM_ERR_INVALID_ARG;
+    if (stat == LBM_BE && !(mu < 0.0)) return LBM_ERR_INVALID_ARG;
+    return weight_integrals(D, stat, theta, mu, I) ? LBM_OK : LBM_ERR_INVALID_ARG;
 }
 
 const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -447,7 +464,7 @@ lbm_status lbm_init_equilibrium(lbm_ctx* c, const float* rho, const float* u) {
     }
     KParams p = make_params(c);
     c->cur = 0;
-    lbm_status st = after_launch(c, lbm::launch_init(c->lat.vel, c->storage, c->pop[0], c->nbr, rho_d, u_d, p,
+    lbm_status st = after_launch(c, lbm::launch_init(c->lat.vel, c->storage, c->pop[0], c->mask_dev, rho_d, u_d, p,
                                                       c->stream));
     if (st != LBM_OK) return st;
     c->has_state = true;
@@ -574,6 +591,172 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t len) {
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->steps = h.steps;
     c->has_state = true;
+    return LBM_OK;
+}
+
+
+lbm_status lbm_window_totals(lbm_ctx* c, int64_t t_begin, int64_t t_end, double out[4]) {
+    if (!c || !out) return fail(c, LBM_ERR_INVALID_ARG, "lbm_window_totals: null argument");
+    if (!c->has_state) return fail(c, LBM_ERR_STATE, "lbm_window_totals before lbm_init_equilibrium");
+    if (t_end < 0 || t_begin < -1 || t_begin > t_end)
+        return fail(c, LBM_ERR_INVALID_ARG, "lbm_window_totals: need -1 <= t_begin <= t_end");
+    KParams p = make_params(c);
+    LBM_CUDA(c, cudaMemsetAsync(c->totals_dev, 0, sizeof(double) * 4, c->stream));
+    int64_t np = 0;
+    if (t_begin < 0) {  // the start state itself is in the window
+        c->launches += lbm::launch_moments(c->lat.vel, c->storage, c->pop[c->cur], c->nbr, nullptr, nullptr,
+                                           c->partials, &np, p, c->stream);
+        c->launches += lbm::launch_accumulate_totals(c->partials, np, c->totals_dev, c->stream);
+    }
+    for (int64_t t = 1; t <= t_end; ++t) {
+        c->launches += lbm::launch_step(c->lat.vel, c->storage, c->lat.force, c->use_Efield, c->pop[c->cur],
+                                        c->pop[c->cur ^ 1], c->nbr, c->Efield, p, c->stream);
+        c->cur ^= 1;
+        if (t > t_begin) {
+            c->launches += lbm::launch_moments(c->lat.vel, c->storage, c->pop[c->cur], c->nbr, nullptr, nullptr,
+                                               c->partials, &np, p, c->stream);
+            c->launches += lbm::launch_accumulate_totals(c->partials, np, c->totals_dev, c->stream);
+        }
+    }
+    c->steps += t_end;
+    LBM_CUDA(c, cudaGetLastError());
+    LBM_CUDA(c, cudaMemcpyAsync(c->totals_host, c->totals_dev, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 4; ++k) {
+        if (!std::isfinite(c->totals_host[k])) return fail(c, LBM_ERR_NONFINITE, "non-finite window total");
+        out[k] = c->totals_host[k];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t t_begin, int64_t t_end,
+                       int64_t checkpoint_every, double* dL_dE, double dL_dB[3], double* dL_dtau, double* loss,
+                       float* dL_df0) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (!c->has_state) return fail(c, LBM_ERR_STATE, "lbm_adjoint before lbm_init_equilibrium");
+    if (t_end < 1 || t_begin < -1 || t_begin >= t_end)
+        return fail(c, LBM_ERR_INVALID_ARG, "lbm_adjoint: need -1 <= t_begin < t_end and t_end >= 1");
+    if (checkpoint_every < 0) return fail(c, LBM_ERR_INVALID_ARG, "lbm_adjoint: checkpoint_every < 0");
+    if ((dL_dE && !is_device_ptr(dL_dE)) || (dL_df0 && !is_device_ptr(dL_df0)))
+        return fail(c, LBM_ERR_INVALID_ARG, "lbm_adjoint: dL_dE and dL_df0 must be device pointers");
+    const int64_t T = t_end;
+    int64_t K = checkpoint_every;
+    if (K == 0) {
+        K = 1;
+        while (K * K < T) ++K;
+    }
+    if (K > T) K = T;
+    const int64_t nseg = (T + K - 1) / K;
+    const size_t pop_bytes = (size_t)c->Q * (size_t)c->N * pop_elem_bytes(c->storage);
+    const size_t lam_bytes = sizeof(float) * (size_t)c->Q * (size_t)c->N;
+    KParams p = make_params(c);
+    const int64_t nslot = lbm::adjoint_slot_count(p);
+
+    // --- memory: nseg checkpoints + (K - 1) replay slots + 2 adjoint fields ---
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const size_t need = (size_t)(nseg + K - 1) * pop_bytes + 2 * lam_bytes + sizeof(double) * (nslot + 8) +
+                        sizeof(float) * (size_t)c->N * (1 + c->D);
+    if (need > free_b)
+        return fail(c, LBM_ERR_OOM, "lbm_adjoint: needs %.2f GB of device memory, %.2f GB free; choose "
+                    "checkpoint_every near sqrt(t_end)", need / 1e9, free_b / 1e9);
+    std::vector<void*> ckpt(nseg, nullptr), seg(K, nullptr);
+    float* lam[2] = {nullptr, nullptr};
+    double* slots = nullptr;
+    double* red = nullptr;
+    float* wstage = nullptr;
+    lbm_status st = LBM_OK;
+    auto release = [&]() {
+        cudaStreamSynchronize(c->stream);
+        for (void* q : ckpt) cudaFree(q);
+        for (size_t k = 1; k < seg.size(); ++k) cudaFree(seg[k]);
+        cudaFree(lam[0]);
+        cudaFree(lam[1]);
+        cudaFree(slots);
+        cudaFree(red);
+        cudaFree(wstage);
+    };
+#define ADJ_CHECK(call)                                        \
+    do {                                                       \
+        st = cuda_check(c, (call), #call);                     \
+        if (st != LBM_OK) {                                    \
+            release();                                         \
+            return st;                                         \
+        }                                                      \
+    } while (0)
+    for (int64_t s = 0; s < nseg; ++s) ADJ_CHECK(cudaMalloc(&ckpt[s], pop_bytes));
+    for (int64_t k = 1; k < K; ++k) ADJ_CHECK(cudaMalloc(&seg[k], pop_bytes));
+    ADJ_CHECK(cudaMalloc((void**)&lam[0], lam_bytes));
+    ADJ_CHECK(cudaMalloc((void**)&lam[1], lam_bytes));
+    ADJ_CHECK(cudaMalloc((void**)&slots, sizeof(double) * nslot));
+    ADJ_CHECK(cudaMalloc((void**)&red, sizeof(double) * 8));
+    ADJ_CHECK(cudaMemsetAsync(slots, 0, sizeof(double) * nslot, c->stream));
+    // loss weights: device, or staged from the host
+    const float* wr_d = w_rho;
+    const float* wj_d = w_j;
+    if ((w_rho && !is_device_ptr(w_rho)) || (w_j && !is_device_ptr(w_j))) {
+        ADJ_CHECK(cudaMalloc((void**)&wstage, sizeof(float) * (size_t)c->N * (1 + c->D)));
+        if (w_rho && !is_device_ptr(w_rho)) {
+            ADJ_CHECK(cudaMemcpyAsync(wstage, w_rho, sizeof(float) * c->N, cudaMemcpyHostToDevice, c->stream));
+            wr_d = wstage;
+        }
+        if (w_j && !is_device_ptr(w_j)) {
+            ADJ_CHECK(cudaMemcpyAsync(wstage + c->N, w_j, sizeof(float) * c->N * c->D, cudaMemcpyHostToDevice,
+                                      c->stream));
+            wj_d = wstage + c->N;
+        }
+    }
+    if (dL_dE) ADJ_CHECK(cudaMemsetAsync(dL_dE, 0, sizeof(double) * (size_t)c->D * c->N, c->stream));
+
+    const int vel = c->lat.vel, sto = c->storage, force = c->lat.force;
+    const bool ef = c->use_Efield;
+    // --- forward with checkpoints every K steps ---
+    for (int64_t t = 0; t < T; ++t) {
+        if (t % K == 0)
+            ADJ_CHECK(cudaMemcpyAsync(ckpt[t / K], c->pop[c->cur], pop_bytes, cudaMemcpyDeviceToDevice, c->stream));
+        c->launches += lbm::launch_step(vel, sto, force, ef, c->pop[c->cur], c->pop[c->cur ^ 1], c->nbr, c->Efield,
+                                        p, c->stream);
+        c->cur ^= 1;
+    }
+    ADJ_CHECK(cudaGetLastError());
+    // --- seed lam_T at the final state ---
+    int li = 0;
+    c->launches += lbm::launch_adjoint_seed(vel, sto, c->pop[c->cur], c->nbr, wr_d, wj_d, lam[li], slots,
+                                            T > t_begin && T <= t_end, p, c->stream);
+    // --- reverse sweep, one segment at a time ---
+    for (int64_t s = nseg - 1; s >= 0; --s) {
+        const int64_t t0 = s * K, t1 = std::min(t0 + K, T);
+        seg[0] = ckpt[s];
+        for (int64_t t = t0; t < t1 - 1; ++t)
+            c->launches += lbm::launch_step(vel, sto, force, ef, seg[t - t0], seg[t - t0 + 1], c->nbr, c->Efield, p,
+                                            c->stream);
+        for (int64_t t = t1 - 1; t >= t0; --t) {
+            const bool win = t > t_begin && t <= t_end;
+            c->launches += lbm::launch_adjoint_step(vel, sto, force, ef, win, seg[t - t0], lam[li], lam[li ^ 1],
+                                                    c->nbr, c->Efield, wr_d, wj_d, dL_dE, slots, p, c->stream);
+            li ^= 1;
+        }
+        ADJ_CHECK(cudaGetLastError());
+    }
+    seg[0] = nullptr;
+    if (dL_df0) ADJ_CHECK(cudaMemcpyAsync(dL_df0, lam[li], lam_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    c->launches += lbm::launch_reduce_slots(slots, nslot / 5, 5, red, c->stream);
+    double host[5];
+    ADJ_CHECK(cudaMemcpyAsync(host, red, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->stream));
+    ADJ_CHECK(cudaStreamSynchronize(c->stream));
+    release();
+#undef ADJ_CHECK
+    c->steps += T;
+    for (int k = 0; k < 5; ++k)
+        if (!std::isfinite(host[k])) return fail(c, LBM_ERR_NONFINITE, "lbm_adjoint: non-finite gradient or loss");
+    if (dL_dB) {
+        dL_dB[0] = host[0];
+        dL_dB[1] = host[1];
+        dL_dB[2] = host[2];
+        if (c->D == 2) dL_dB[0] = dL_dB[1] = 0.0;
+    }
+    if (dL_dtau) *dL_dtau = host[3];
+    if (loss) *loss = host[4];
     return LBM_OK;
 }
 

@@ -14,6 +14,8 @@
 namespace lbm {
 
 constexpr int kMaxQ = 19;
+// Per-cell link mask: bit a set when x + e_a is solid (a >= 1); kSolidBit
+// when x itself is solid.
 constexpr uint32_t kSolidBit = 0x80000000u;
 
 // ---------------------------------------------------------------------------
@@ -45,44 +47,40 @@ struct LatD3V19 {
 __host__ __device__ constexpr int opposite(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
 
 // ---------------------------------------------------------------------------
-// Storage of the deviation h_a = f_a - rho0 w_a / I_0 (scaled by `scale`).
+// Storage of the deviation h_a = f_a - rho0 w_a / I_0.  The kernels work in
+// the storage's scaled units h~ = scale * h (scale = 2^12 for FP16, 1
+// otherwise): raw() decodes to FP32 without unscaling, put() rounds to
+// nearest even.
 // ---------------------------------------------------------------------------
 struct StoreF32 {
     using T = float;
-    static constexpr bool kScaled = false;
-    __device__ __forceinline__ static float load(const T* __restrict__ p, int64_t i, float) { return __ldg(p + i); }
-    __device__ __forceinline__ static void store(T* __restrict__ p, int64_t i, float v, float) { p[i] = v; }
+    __device__ __forceinline__ static float raw(const T* p) { return __ldg(p); }
+    __device__ __forceinline__ static void put(T* p, float v) { *p = v; }
 };
 
 struct StoreF16 {
     using T = __half;
-    static constexpr bool kScaled = true;
-    __device__ __forceinline__ static float load(const T* __restrict__ p, int64_t i, float inv_scale) {
-        return __half2float(__ldg(p + i)) * inv_scale;
-    }
-    __device__ __forceinline__ static void store(T* __restrict__ p, int64_t i, float v, float scale) {
-        p[i] = __float2half_rn(v * scale);
-    }
+    __device__ __forceinline__ static float raw(const T* p) { return __half2float(__ldg(p)); }
+    __device__ __forceinline__ static void put(T* p, float v) { *p = __float2half_rn(v); }
 };
 
 struct StoreBF16 {
     using T = __nv_bfloat16;
-    static constexpr bool kScaled = true;
-    __device__ __forceinline__ static float load(const T* __restrict__ p, int64_t i, float inv_scale) {
-        return __bfloat162float(__ldg(p + i)) * inv_scale;
-    }
-    __device__ __forceinline__ static void store(T* __restrict__ p, int64_t i, float v, float scale) {
-        p[i] = __float2bfloat16_rn(v * scale);
-    }
+    __device__ __forceinline__ static float raw(const T* p) { return __bfloat162float(__ldg(p)); }
+    __device__ __forceinline__ static void put(T* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
 // ---------------------------------------------------------------------------
-// Kernel parameter block (passed by value).  The equilibrium is evaluated in
-// the direct N = 2 form of Sec. 5.1 (Eq. feq-reduce-general-method-without-
-// pol-eq), with xi_a = e_a / c_s folded into the constants:
-//   f^eq_a = rho w_a [A + Bp (e_a.u) + Cp (e_a.u)^2 + (Gp e_a^2 + H) u^2]
+// Kernel parameter block (passed by value).  The equilibrium is the direct
+// N = 2 form of Sec. 5.1 (Eq. feq-reduce-general-method-without-pol-eq) with
+// xi_a = e_a / c_s folded into the constants:
+//   f^eq_a = rho w_a [A + Bp (e_a.u) + Cp (e_a.u)^2 + k2_a u^2],
 //   A = 1/I0, Bp = 1/(I2 c_s), Cp = 1/(2 I4 c_s^2),
-//   Gp = (Delta2^2 - 1)/(2 D I4 c_s^2), H = -I2 Delta2^2/(2 I0 I4).
+//   k2_a = (Delta2^2 - 1) e_a^2 / (2 D I4 c_s^2) - I2 Delta2^2 / (2 I0 I4).
+// The odd (momentum-carrying) coefficient W1_a = w_a Bp / c_s is kept as a
+// double-float pair W1hi + W1lo so that sum_a W1_a e_a e_a = identity to
+// ~1e-15: an FP32-rounded W1 would leak a fixed fraction ~1e-7 of the
+// momentum in every collision, which compounds over thousands of steps.
 // ---------------------------------------------------------------------------
 struct KParams {
     int nx, ny, nz;
@@ -91,9 +89,11 @@ struct KParams {
     float tau;
     float rho0;
     float A, Bp, Cp, Gp, H;
-    float cs_inv;
+    float cs, cs_inv;
     float w[kMaxQ];
-    float f0[kMaxQ];  // rho0 w_a A: the rest equilibrium at rho0
+    float k2[kMaxQ];
+    float W1hi[kMaxQ], W1lo[kMaxQ];
+    float f0[kMaxQ];  // rho0 w_a A: the rest equilibrium at rho0 (unscaled)
     float E[3], B[3];
     float scale, inv_scale;
 };
@@ -105,7 +105,7 @@ struct Launch {
 // Launchers (lbm_kernels.cu).  Each returns the number of kernels launched.
 int launch_build_neighbors(int vel, const uint8_t* mask, uint32_t* nbr, unsigned long long* fluid_count,
                            const KParams& p, cudaStream_t s);
-int launch_init(int vel, int storage, void* pop, const uint32_t* nbr, const float* rho, const float* u,
+int launch_init(int vel, int storage, void* pop, const uint8_t* mask, const float* rho, const float* u,
                 const KParams& p, cudaStream_t s);
 int launch_step(int vel, int storage, int force, bool efield, const void* fin, void* fout, const uint32_t* nbr,
                 const float* Ef, const KParams& p, cudaStream_t s);
@@ -115,6 +115,18 @@ int launch_reduce_partials(const double* partials, int64_t n_partials, double* o
 int launch_populations(int vel, int storage, const void* pop, const uint32_t* nbr, float* f, bool deviation,
                        const KParams& p, cudaStream_t s);
 int64_t moments_partial_count(const KParams& p);
+
+// Adjoint (lbm_adjoint.cu).
+int64_t adjoint_slot_count(const KParams& p);
+int launch_adjoint_seed(int vel, int storage, const void* P, const uint32_t* nbr, const float* w_rho,
+                        const float* w_j, float* lam, double* slots, bool in_window, const KParams& p,
+                        cudaStream_t s);
+int launch_adjoint_step(int vel, int storage, int force, bool efield, bool in_window, const void* P,
+                        const float* lam_in, float* lam_out, const uint32_t* nbr, const float* Ef,
+                        const float* w_rho, const float* w_j, double* gE, double* slots, const KParams& p,
+                        cudaStream_t s);
+int launch_reduce_slots(const double* slots, int64_t n_blocks, int n_slots, double* out, cudaStream_t s);
+int launch_accumulate_totals(const double* partials, int64_t n_partials, double* acc4, cudaStream_t s);
 
 }  // namespace lbm
 

@@ -1,121 +1,35 @@
 // Device kernels of the semiclassical LBM step (Sec. 9.1 of arXiv 1710.09472):
-// neighbour bitmask, equilibrium start state, the fused pull-stream + BGK
-// collision + Lorentz forcing step, moments with FP64 reductions, and the
-// population read-back.
+// link mask, equilibrium start state, the fused pull-stream + BGK collision +
+// Lorentz forcing step, moments with FP64 reductions, and the population
+// read-back.
 //
-// Layout: populations are structure-of-arrays, pop[a * N + cell] with
-// cell = (z * ny + y) * nx + x.  The buffer holds the post-collision values of
-// the previous step ("pull" scheme): the state f(x, t) of the method is
-//   f_a(x, t) = P_a(x - e_a)   if x - e_a is fluid,
-//             = P_abar(x)      otherwise (halfway bounce-back, Sec. 9.3-9.4),
-// so one kernel per step reads f(x, t), collides it and writes P for t + 1.
-//
-// Every kernel is a plain grid over cells: blockIdx.x is the row (y, z),
-// blockIdx.y the chunk of x, threads run along x for coalesced access.
+// Layout: populations are structure-of-arrays, P[a * N + cell] with
+// cell = (z * ny + y) * nx + x.  P holds post-collision values ("pull"
+// scheme): the state f(x, t) of the method is f_a(x, t) = P_a(x - e_a).
+// Halfway bounce-back (Sec. 9.3, 9.4) is done on the write side: when x + e_a
+// is solid, the collision at x stores f*_a(x) into slot abar of that solid
+// cell, P_abar(x + e_a), which is exactly where the pull of direction abar at
+// x reads.  Solid cells thus carry only these "ghost" values, every pull is a
+// plain shifted load, and each stored value is read exactly once.
 #include <cstdio>
 
-#include "lbm_internal.h"
+#include "lbm_device.cuh"
 
 namespace lbm {
 namespace {
 
-constexpr int kBlock = 128;
-
-struct Cell {
-    int x, y, z;
-    int64_t cell;
-};
-
-__device__ __forceinline__ bool cell_of_thread(const KParams& p, Cell& c) {
-    c.x = blockIdx.y * blockDim.x + threadIdx.x;
-    if (c.x >= p.nx) return false;
-    const int row = blockIdx.x;
-    c.y = row % p.ny;
-    c.z = row / p.ny;
-    c.cell = (int64_t)row * p.nx + c.x;
-    return true;
-}
-
-// Index of x + s * e_a with periodic wrap (s = +1 or -1).
-template <class L>
-__device__ __forceinline__ int64_t shifted(const KParams& p, const Cell& c, int a, int s) {
-    const int ex = s * L::c(a, 0), ey = s * L::c(a, 1), ez = s * L::c(a, 2);
-    int xs = c.x, ys = c.y, zs = c.z;
-    if (ex > 0) xs = (c.x == p.nx - 1) ? 0 : c.x + 1;
-    if (ex < 0) xs = (c.x == 0) ? p.nx - 1 : c.x - 1;
-    if (ey > 0) ys = (c.y == p.ny - 1) ? 0 : c.y + 1;
-    if (ey < 0) ys = (c.y == 0) ? p.ny - 1 : c.y - 1;
-    if (ez > 0) zs = (c.z == p.nz - 1) ? 0 : c.z + 1;
-    if (ez < 0) zs = (c.z == 0) ? p.nz - 1 : c.z - 1;
-    return ((int64_t)zs * p.ny + ys) * p.nx + xs;
-}
-
-// Pull the deviations h_a(x, t) of one fluid cell (stream + bounce-back).
-template <class L, class S>
-__device__ __forceinline__ void pull(const typename S::T* __restrict__ P, uint32_t m, const KParams& p,
-                                     const Cell& c, float* h) {
-#pragma unroll
-    for (int a = 0; a < L::Q; ++a) {
-        int64_t idx;
-        if (a == 0) {
-            idx = c.cell;
-        } else if ((m >> a) & 1u) {
-            idx = (int64_t)opposite(a) * p.N + c.cell;
-        } else {
-            idx = (int64_t)a * p.N + shifted<L>(p, c, a, -1);
-        }
-        h[a] = S::load(P, idx, p.inv_scale);
-    }
-}
-
-// Moments of the deviations: drho = sum h_a, j = sum h_a e_a / c_s (xi units).
-template <class L>
-__device__ __forceinline__ void moments_of(const float* h, const KParams& p, float& drho, float* j) {
-    float s = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-    for (int a = 0; a < L::Q; ++a) {
-        s += h[a];
-        if (L::c(a, 0) > 0) jx += h[a];
-        if (L::c(a, 0) < 0) jx -= h[a];
-        if (L::c(a, 1) > 0) jy += h[a];
-        if (L::c(a, 1) < 0) jy -= h[a];
-        if (L::c(a, 2) > 0) jz += h[a];
-        if (L::c(a, 2) < 0) jz -= h[a];
-    }
-    drho = s;
-    j[0] = jx * p.cs_inv;
-    j[1] = jy * p.cs_inv;
-    j[2] = (L::D == 3) ? jz * p.cs_inv : 0.f;
-}
-
-template <class L>
-__device__ __forceinline__ float edot(int a, const float* v) {
-    float r = 0.f;
-    if (L::c(a, 0) > 0) r += v[0];
-    if (L::c(a, 0) < 0) r -= v[0];
-    if (L::c(a, 1) > 0) r += v[1];
-    if (L::c(a, 1) < 0) r -= v[1];
-    if (L::D == 3) {
-        if (L::c(a, 2) > 0) r += v[2];
-        if (L::c(a, 2) < 0) r -= v[2];
-    }
-    return r;
-}
-
-template <class L>
-__device__ __forceinline__ constexpr int esq(int a) {
-    return L::c(a, 0) * L::c(a, 0) + L::c(a, 1) * L::c(a, 1) + L::c(a, 2) * L::c(a, 2);
-}
+using dev::Cell;
+using dev::kBlock;
 
 // ---------------------------------------------------------------------------
-// Neighbour bitmask: bit a set when x - e_a is solid; kSolidBit when x is.
+// Link mask: bit a set when x + e_a is solid; kSolidBit when x is solid.
 // ---------------------------------------------------------------------------
 template <class L>
 __global__ void __launch_bounds__(kBlock) k_neighbors(const uint8_t* __restrict__ mask, uint32_t* __restrict__ nbr,
                                                       unsigned long long* __restrict__ fluid_count, KParams p) {
     Cell c;
     unsigned fluid = 0;
-    if (cell_of_thread(p, c)) {
+    if (dev::cell_of_thread(p, c)) {
         uint32_t m = 0;
         if (mask[c.cell]) {
             m = kSolidBit;
@@ -123,91 +37,90 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(const uint8_t* __restrict_
             fluid = 1;
 #pragma unroll
             for (int a = 1; a < L::Q; ++a)
-                if (mask[shifted<L>(p, c, a, -1)]) m |= (1u << a);
+                if (mask[dev::shifted<L>(c, a, +1)]) m |= (1u << a);
         }
         nbr[c.cell] = m;
     }
-    // one atomic per warp
     const unsigned cnt = __popc(__ballot_sync(0xffffffffu, fluid));
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(fluid_count, (unsigned long long)cnt);
 }
 
 // ---------------------------------------------------------------------------
-// Start state: P such that pulling it gives f^eq(rho(x), u(x)):
-//   P_b(y) = f^eq_b(y + e_b) if y + e_b is fluid, else f^eq_bbar(y).
+// Start state f(x, 0) = f^eq(rho(x), u(x)): slot P_b(y) is pulled by the cell
+// y + e_b, so it holds f^eq_b(y + e_b) when that cell is fluid (for solid y
+// this is the ghost value of a bounced link), and 0 otherwise.
 // ---------------------------------------------------------------------------
 template <class L>
-__device__ __forceinline__ float heq_at(const KParams& p, int a, float rho, const float* u) {
-    // f^eq_a - f0_a = w_a [A (rho - rho0) + rho (Bp eu + Cp eu^2 + (Gp e^2 + H) u^2)]
-    const float eu = edot<L>(a, u);
+__device__ __forceinline__ float heq_unscaled(const KParams& p, int a, float rho, const float* u) {
+    const float eu = dev::edot<L>(a, u);
     const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    return p.w[a] * (p.A * (rho - p.rho0) + rho * (p.Bp * eu + p.Cp * eu * eu + (p.Gp * esq<L>(a) + p.H) * u2));
+    return p.w[a] * (p.A * (rho - p.rho0) + rho * (p.Bp * eu + p.Cp * eu * eu + p.k2[a] * u2));
 }
 
 template <class L, class S>
-__global__ void __launch_bounds__(kBlock) k_init(typename S::T* __restrict__ P, const uint32_t* __restrict__ nbr,
+__global__ void __launch_bounds__(kBlock) k_init(typename S::T* __restrict__ P, const uint8_t* __restrict__ mask,
                                                  const float* __restrict__ rho, const float* __restrict__ u,
                                                  KParams p) {
     Cell c;
-    if (!cell_of_thread(p, c)) return;
-    const uint32_t m = nbr[c.cell];
-    if (m & kSolidBit) {
-#pragma unroll
-        for (int a = 0; a < L::Q; ++a) S::store(P, (int64_t)a * p.N + c.cell, 0.f, p.scale);
-        return;
-    }
-    auto fields = [&](int64_t cell, float& r, float* uu) {
-        r = rho ? rho[cell] : p.rho0;
-        uu[0] = u ? u[cell] : 0.f;
-        uu[1] = u ? u[p.N + cell] : 0.f;
-        uu[2] = (u && L::D == 3) ? u[2 * p.N + cell] : 0.f;
-    };
-    float r0, u0[3];
-    fields(c.cell, r0, u0);
+    if (!dev::cell_of_thread(p, c)) return;
 #pragma unroll
     for (int b = 0; b < L::Q; ++b) {
-        float v;
-        if (b != 0 && ((m >> opposite(b)) & 1u)) {
-            v = heq_at<L>(p, opposite(b), r0, u0);
-        } else if (b == 0) {
-            v = heq_at<L>(p, 0, r0, u0);
-        } else {
-            float r1, u1[3];
-            fields(shifted<L>(p, c, b, +1), r1, u1);
-            v = heq_at<L>(p, b, r1, u1);
+        const uint32_t dst = b == 0 ? c.cell : dev::shifted<L>(c, b, +1);
+        float v = 0.f;
+        if (!mask[dst]) {
+            const float r = rho ? rho[dst] : p.rho0;
+            const float uu[3] = {u ? u[dst] : 0.f, u ? u[p.N + dst] : 0.f,
+                                 (u && L::D == 3) ? u[2 * p.N + dst] : 0.f};
+            v = heq_unscaled<L>(p, b, r, uu) * p.scale;
         }
-        S::store(P, (int64_t)b * p.N + c.cell, v, p.scale);
+        S::put(P + (int64_t)b * p.N + c.cell, v);
     }
 }
 
 // ---------------------------------------------------------------------------
 // The fused step.  f(x, t) is pulled, its moments taken, the force applied,
-// f^eq formed and the BGK relaxation written back (Sec. 9.1):
-//   h*_a = (1 - 1/tau) h_a + heq_a / tau + S_a,
-// where h = f - f0 are deviations from the rest equilibrium at rho0.
+// f^eq formed and the BGK relaxation written (Sec. 9.1), all in scaled
+// deviations h~ = s (f - f0):
+//   h~*_a = (1 - w) h~_a + w heq~_a + S~_a,  w = 1/tau,
+//   heq~_a = w_a [A drho~ + s rho (Cp (e.u)^2 + k2_a u^2)] + W1_a (e_a . j~)   (+ shift part)
 // FORCE 0: velocity shift u* = u + tau (E + u x B) (Sec. 7, Eq.
-//          u-update-force-term-eq); S = 0.
+//          u-update-force-term-eq): the odd part uses j~ + s c_s rho tau a.
 // FORCE 1: S_a = a_a . grad_u f^eq_a with a_a = E + xi_a x B (Sec. 7, Eq.
 //          forcing-term-integrals-eq):
-//          S_a = rho w_a [Bp e.E + 2 Cp (e.u)(e.E) + 2 (Gp e^2 + H)(u.E + e.(B x u)/c_s)].
+//          S~_a = s rho w_a [2 Cp (e.u)(e.E) + 2 k2_a u.E]                  (even)
+//               + W1_a (e . s c_s rho E) + 2 s rho w_a k2_a (e.(B x u))/c_s (odd).
+// Opposite directions share the even part and negate the odd part, so the
+// work is done once per pair; the rest population closes the mass balance
+// exactly: h~*_0 = sum_a h~_a - sum_{a>0} h~*_a.
 // ---------------------------------------------------------------------------
 template <class L, class S, int FORCE, bool EF>
 __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict__ Pin, typename S::T* __restrict__ Pout,
                                                  const uint32_t* __restrict__ nbr, const float* __restrict__ Ef,
                                                  KParams p) {
     Cell c;
-    if (!cell_of_thread(p, c)) return;
+    if (!dev::cell_of_thread(p, c)) return;
     const uint32_t m = __ldg(nbr + c.cell);
     if (m & kSolidBit) return;
 
     float h[L::Q];
-    pull<L, S>(Pin, m, p, c, h);
+    dev::pull_raw<L, S>(Pin, p.N, c, h);
 
-    float drho, j[3];
-    moments_of<L>(h, p, drho, j);
-    const float rho = p.rho0 + drho;
-    const float inv_rho = 1.0f / rho;
-    float u[3] = {j[0] * inv_rho, j[1] * inv_rho, j[2] * inv_rho};
+    // moments (scaled): drho~ = sum h~, j~ = sum h~ e (lattice units)
+    float drho = h[0], j[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 1; a < L::Q; a += 2) {
+        const float sum = h[a] + h[a + 1], dif = h[a] - h[a + 1];
+        drho += sum;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (L::c(a, d) > 0) j[d] += dif;
+            if (L::c(a, d) < 0) j[d] -= dif;
+        }
+    }
+    const float rho = p.rho0 + drho * p.inv_scale;
+    const float q = p.inv_scale * p.cs_inv / rho;  // u = j~ q  (xi units)
+    const float u[3] = {j[0] * q, j[1] * q, j[2] * q};
+    const float srho = p.scale * rho;
 
     float E[3];
     if (EF) {
@@ -220,57 +133,93 @@ __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict
         E[2] = p.E[2];
     }
 
-    float ue[3];
+    const float om = p.omega, omm = 1.0f - p.omega;
+    float ue[3], v[3];
+    float uE = 0.f, bu[3] = {0.f, 0.f, 0.f};
+    const float scr = srho * p.cs;  // s c_s rho
     if (FORCE == 0) {
-        // a = E + u x B
-        const float ax = E[0] + (u[1] * p.B[2] - u[2] * p.B[1]);
-        const float ay = E[1] + (u[2] * p.B[0] - u[0] * p.B[2]);
-        const float az = E[2] + (u[0] * p.B[1] - u[1] * p.B[0]);
-        ue[0] = u[0] + p.tau * ax;
-        ue[1] = u[1] + p.tau * ay;
-        ue[2] = (L::D == 3) ? u[2] + p.tau * az : 0.f;
+        const float a0 = E[0] + (u[1] * p.B[2] - u[2] * p.B[1]);
+        const float a1 = E[1] + (u[2] * p.B[0] - u[0] * p.B[2]);
+        const float a2 = (L::D == 3) ? E[2] + (u[0] * p.B[1] - u[1] * p.B[0]) : 0.f;
+        ue[0] = u[0] + p.tau * a0;
+        ue[1] = u[1] + p.tau * a1;
+        ue[2] = u[2] + p.tau * a2;
+        // odd part of w heq~ at u*: W1 (e . w (j~ + s c_s rho tau a)) = W1 (e . (w j~ + s c_s rho a))
+        v[0] = om * j[0] + scr * a0;
+        v[1] = om * j[1] + scr * a1;
+        v[2] = om * j[2] + scr * a2;
     } else {
         ue[0] = u[0];
         ue[1] = u[1];
         ue[2] = u[2];
+        v[0] = om * j[0] + scr * E[0];
+        v[1] = om * j[1] + scr * E[1];
+        v[2] = om * j[2] + scr * E[2];
+        uE = u[0] * E[0] + u[1] * E[1] + u[2] * E[2];
+        const float tb = 2.f * srho * p.cs_inv;  // 2 s rho / c_s times (B x u)
+        bu[0] = tb * (p.B[1] * u[2] - p.B[2] * u[1]);
+        bu[1] = tb * (p.B[2] * u[0] - p.B[0] * u[2]);
+        bu[2] = tb * (p.B[0] * u[1] - p.B[1] * u[0]);
     }
     const float u2 = ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2];
-    const float Adr = p.A * drho;
-    const float one_m_omega = 1.0f - p.omega;
+    const float omAdr = om * p.A * drho;
 
-    // force-term helpers (FORCE 1)
-    float uE = 0.f, bu[3] = {0.f, 0.f, 0.f};
-    if (FORCE == 1) {
-        uE = u[0] * E[0] + u[1] * E[1] + u[2] * E[2];
-        bu[0] = (p.B[1] * u[2] - p.B[2] * u[1]) * p.cs_inv;
-        bu[1] = (p.B[2] * u[0] - p.B[0] * u[2]) * p.cs_inv;
-        bu[2] = (p.B[0] * u[1] - p.B[1] * u[0]) * p.cs_inv;
-    }
-
+    float out[L::Q];
+    float rest = drho;
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) {
-        const float eu = edot<L>(a, ue);
-        const float k2 = p.Gp * (float)esq<L>(a) + p.H;
-        const float heq = p.w[a] * (Adr + rho * (p.Bp * eu + p.Cp * eu * eu + k2 * u2));
-        float hs = one_m_omega * h[a] + p.omega * heq;
+    for (int a = 1; a < L::Q; a += 2) {
+        const float eu = dev::edot<L>(a, ue);
+        const float ev_ = dev::edot<L>(a, v);
+        float even = p.w[a] * (omAdr + om * srho * (p.Cp * eu * eu + p.k2[a] * u2));
+        float odd = p.W1hi[a] * ev_ + p.W1lo[a] * ev_;
         if (FORCE == 1) {
-            const float eE = edot<L>(a, E);
-            const float ua = uE + edot<L>(a, bu);
-            hs += rho * p.w[a] * (p.Bp * eE + 2.f * p.Cp * eu * eE + 2.f * k2 * ua);
+            const float eE = dev::edot<L>(a, E);
+            even += 2.f * srho * p.w[a] * (p.Cp * eu * eE + p.k2[a] * uE);
+            odd += p.w[a] * p.k2[a] * dev::edot<L>(a, bu);
         }
-        S::store(Pout, (int64_t)a * p.N + c.cell, hs, p.scale);
+        const float ha = omm * h[a] + even + odd;
+        const float hb = omm * h[a + 1] + even - odd;
+        out[a] = ha;
+        out[a + 1] = hb;
+        rest -= ha + hb;
+    }
+    out[0] = rest;
+
+    // store; a link into a solid cell writes the ghost slot P_abar(x + e_a)
+    S::put(Pout + c.cell, out[0]);
+#pragma unroll
+    for (int a = 1; a < L::Q; ++a) {
+        const bool bounce = (m >> a) & 1u;
+        const int64_t idx = bounce ? (int64_t)opposite(a) * p.N + dev::shifted<L>(c, a, +1)
+                                   : (int64_t)a * p.N + c.cell;
+        S::put(Pout + idx, out[a]);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Moments of f(x, t) and FP64 block partials of the fluid totals.
-// partials[block] = {sum rho, sum j_x, sum j_y, sum j_z} (warp shuffles, then
-// one warp over the block's warps).
+// Moments of f(x, t) and FP64 block partials of the fluid totals
+// partials[block] = {sum rho, sum j_x, sum j_y, sum j_z}.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum(double v) {
+template <class L, class S>
+__device__ __forceinline__ void cell_moments(const typename S::T* __restrict__ P, const KParams& p, const Cell& c,
+                                             float& rho, float* j) {
+    float h[L::Q];
+    dev::pull_raw<L, S>(P, p.N, c, h);
+    float drho = 0.f, jj[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
+    for (int a = 0; a < L::Q; ++a) {
+        drho += h[a];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (L::c(a, d) > 0) jj[d] += h[a];
+            if (L::c(a, d) < 0) jj[d] -= h[a];
+        }
+    }
+    rho = p.rho0 + drho * p.inv_scale;
+    const float k = p.inv_scale * p.cs_inv;
+    j[0] = jj[0] * k;
+    j[1] = jj[1] * k;
+    j[2] = (L::D == 3) ? jj[2] * k : 0.f;
 }
 
 template <class L, class S>
@@ -279,15 +228,11 @@ __global__ void __launch_bounds__(kBlock) k_moments(const typename S::T* __restr
                                                     double* __restrict__ partials, KParams p) {
     Cell c;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    if (cell_of_thread(p, c)) {
+    if (dev::cell_of_thread(p, c)) {
         const uint32_t m = nbr[c.cell];
         float r = 0.f, j[3] = {0.f, 0.f, 0.f};
         if (!(m & kSolidBit)) {
-            float h[L::Q];
-            pull<L, S>(P, m, p, c, h);
-            float drho;
-            moments_of<L>(h, p, drho, j);
-            r = p.rho0 + drho;
+            cell_moments<L, S>(P, p, c, r, j);
             acc[0] = (double)r;
             acc[1] = (double)j[0];
             acc[2] = (double)j[1];
@@ -303,7 +248,7 @@ __global__ void __launch_bounds__(kBlock) k_moments(const typename S::T* __restr
         __shared__ double sh[kBlock / 32][4];
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k] = warp_sum(acc[k]);
+        for (int k = 0; k < 4; ++k) acc[k] = dev::warp_sum(acc[k]);
         if (lane == 0) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) sh[wid][k] = acc[k];
@@ -314,48 +259,53 @@ __global__ void __launch_bounds__(kBlock) k_moments(const typename S::T* __restr
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 double v = lane < nw ? sh[lane][k] : 0.0;
-                v = warp_sum(v);
+                v = dev::warp_sum(v);
                 if (lane == 0) partials[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 4 + k] = v;
             }
         }
     }
 }
 
-// One block sums the partials in a fixed order (deterministic).
+// One block sums interleaved per-block slots in a fixed order (deterministic);
+// with add != 0 the result is added to out (window sums stay on the device).
 constexpr int kReduceThreads = 512;
-__global__ void __launch_bounds__(kReduceThreads) k_reduce_partials(const double* __restrict__ partials, int64_t n,
-                                                                     double* __restrict__ out4) {
-    __shared__ double sh[kReduceThreads / 32][4];
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+constexpr int kMaxSlots = 8;
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_slots(const double* __restrict__ slots, int64_t nb,
+                                                                 int ns, double* __restrict__ out, int add) {
+    __shared__ double sh[kReduceThreads / 32][kMaxSlots];
+    double acc[kMaxSlots];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k] += partials[i * 4 + k];
+    for (int k = 0; k < kMaxSlots; ++k) acc[k] = 0.0;
+    for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < kMaxSlots; ++k)
+            if (k < ns) acc[k] += slots[i * ns + k];
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k] = warp_sum(acc[k]);
+    for (int k = 0; k < kMaxSlots; ++k) acc[k] = dev::warp_sum(acc[k]);
     if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) sh[wid][k] = acc[k];
+        for (int k = 0; k < kMaxSlots; ++k) sh[wid][k] = acc[k];
     }
     __syncthreads();
     if (wid == 0) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kMaxSlots; ++k) {
             double v = lane < (int)(blockDim.x / 32) ? sh[lane][k] : 0.0;
-            v = warp_sum(v);
-            if (lane == 0) out4[k] = v;
+            v = dev::warp_sum(v);
+            if (lane == 0 && k < ns) out[k] = add ? out[k] + v : v;
         }
     }
 }
 
-// Full FP32 populations f_a(x, t) = f0_a + h_a.
+// FP32 populations f_a(x, t) = f0_a + h_a (or the deviations h_a).
 template <class L, class S>
 __global__ void __launch_bounds__(kBlock) k_populations(const typename S::T* __restrict__ P,
                                                         const uint32_t* __restrict__ nbr, float* __restrict__ f,
                                                         bool deviation, KParams p) {
     Cell c;
-    if (!cell_of_thread(p, c)) return;
+    if (!dev::cell_of_thread(p, c)) return;
     const uint32_t m = nbr[c.cell];
     if (m & kSolidBit) {
 #pragma unroll
@@ -363,9 +313,12 @@ __global__ void __launch_bounds__(kBlock) k_populations(const typename S::T* __r
         return;
     }
     float h[L::Q];
-    pull<L, S>(P, m, p, c, h);
+    dev::pull_raw<L, S>(P, p.N, c, h);
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) f[(int64_t)a * p.N + c.cell] = deviation ? h[a] : p.f0[a] + h[a];
+    for (int a = 0; a < L::Q; ++a) {
+        const float d = h[a] * p.inv_scale;
+        f[(int64_t)a * p.N + c.cell] = deviation ? d : p.f0[a] + d;
+    }
 }
 
 Launch grid_of(const KParams& p) {
@@ -406,14 +359,14 @@ int launch_build_neighbors(int vel, const uint8_t* mask, uint32_t* nbr, unsigned
     });
 }
 
-int launch_init(int vel, int storage, void* pop, const uint32_t* nbr, const float* rho, const float* u,
+int launch_init(int vel, int storage, void* pop, const uint8_t* mask, const float* rho, const float* u,
                 const KParams& p, cudaStream_t s) {
     Launch l = grid_of(p);
     return dispatch_lattice(vel, [&](auto lat) {
         using L = decltype(lat);
         return dispatch_storage(storage, [&](auto st) {
             using S = decltype(st);
-            k_init<L, S><<<l.grid, l.block, 0, s>>>((typename S::T*)pop, nbr, rho, u, p);
+            k_init<L, S><<<l.grid, l.block, 0, s>>>((typename S::T*)pop, mask, rho, u, p);
             return 1;
         });
     });
@@ -460,7 +413,18 @@ int launch_moments(int vel, int storage, const void* pop, const uint32_t* nbr, f
 }
 
 int launch_reduce_partials(const double* partials, int64_t n_partials, double* out4, cudaStream_t s) {
-    k_reduce_partials<<<1, kReduceThreads, 0, s>>>(partials, n_partials, out4);
+    k_reduce_slots<<<1, kReduceThreads, 0, s>>>(partials, n_partials, 4, out4, 0);
+    return 1;
+}
+
+int launch_reduce_slots(const double* slots, int64_t n_blocks, int n_slots, double* out, cudaStream_t s) {
+    if (n_slots > kMaxSlots) return 0;
+    k_reduce_slots<<<1, kReduceThreads, 0, s>>>(slots, n_blocks, n_slots, out, 0);
+    return 1;
+}
+
+int launch_accumulate_totals(const double* partials, int64_t n_partials, double* acc4, cudaStream_t s) {
+    k_reduce_slots<<<1, kReduceThreads, 0, s>>>(partials, n_partials, 4, acc4, 1);
     return 1;
 }
 

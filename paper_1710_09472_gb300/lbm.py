@@ -44,6 +44,14 @@ def _ptr(a, dtype, count: int, name: str):
     raise TypeError(f"{name}: unsupported array type {type(a)}")
 
 
+def weight_integrals(D: int, stat: str = "fd", theta: float = 1.0 / 270.0, mu: float = 1.0):
+    """Host-side I_0..I_8 of the weight (no device needed)."""
+    out = (ctypes.c_double * 5)()
+    _lib.check(_lib.load().lbm_weight_integrals(int(D), _lib.STAT[stat], float(theta), float(mu), out), None,
+               "lbm_weight_integrals")
+    return np.array(list(out))
+
+
 def _vec3(v):
     if v is None:
         return None
@@ -161,6 +169,31 @@ class LBM:
         _lib.check(_lib.load().lbm_get_populations(self._h, _ptr(out, np.float32, self.Q * self.N, "f"),
                                                    int(bool(deviation))), self._h, "lbm_get_populations")
         return out
+
+    def window_totals(self, t_begin: int, t_end: int):
+        """Advance t_end steps; return the FP64 sums over the states after steps
+        t_begin+1..t_end of (sum rho, sum j_x, sum j_y, sum j_z)."""
+        out = (ctypes.c_double * 4)()
+        _lib.check(_lib.load().lbm_window_totals(self._h, int(t_begin), int(t_end), out), self._h,
+                   "lbm_window_totals")
+        return np.array(list(out))
+
+    def adjoint(self, t_begin: int, t_end: int, w_rho=None, w_j=None, checkpoint_every: int = 0, dL_dE=None,
+                dL_df0=None):
+        """Run t_end steps from the current state and return the gradient of
+        L = sum_{t_begin < t <= t_end} sum_x w_rho rho_t + w_j . j_t:
+        dict(loss, dL_dB[3], dL_dtau); dL_dE ([D*N] float64 device tensor) and
+        dL_df0 ([Q*N] float32 device tensor) are filled when given."""
+        dB = (ctypes.c_double * 3)()
+        dtau = ctypes.c_double(0.0)
+        loss = ctypes.c_double(0.0)
+        st = _lib.load().lbm_adjoint(self._h, _ptr(w_rho, np.float32, self.N, "w_rho"),
+                                     _ptr(w_j, np.float32, self.D * self.N, "w_j"), int(t_begin), int(t_end),
+                                     int(checkpoint_every), _ptr(dL_dE, np.float64, self.D * self.N, "dL_dE"), dB,
+                                     ctypes.byref(dtau), ctypes.byref(loss),
+                                     _ptr(dL_df0, np.float32, self.Q * self.N, "dL_df0"))
+        _lib.check(st, self._h, "lbm_adjoint")
+        return {"loss": loss.value, "dL_dB": np.array(list(dB)), "dL_dtau": dtau.value}
 
     def save_state(self) -> bytes:
         used = ctypes.c_size_t(0)

@@ -36,3 +36,24 @@ def test_library_exports_every_declared_symbol():
     # the Python binding names the same entry points
     assert set(_lib.SIGNATURES) >= set(_declared_symbols())
     assert lib.lbm_status_string(0) == b"ok"
+
+
+@pytest.mark.parametrize("D,fname", [(2, "constants_2d.txt"), (3, "constants_3d.txt")])
+def test_library_weight_integrals_host_only(D, fname):
+    """The library's own FP64 weight integrals (host-only entry point) give the
+    printed thetabar = I2/I0 and c0 = I0^-1/2, c1 = I2^-1/2, c2 = I4^-1/2."""
+    import shutil
+
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("no CUDA toolkit")
+    from paper_1710_09472_gb300.build import build
+    from paper_1710_09472_gb300.lbm import weight_integrals
+    from tests.conftest import load_golden
+
+    build()
+    g = load_golden(fname)
+    I = weight_integrals(D)
+    assert abs(I[1] / I[0] / g["thetabar"] - 1) < 1e-14
+    assert abs(I[0] ** -0.5 / g["c0"] - 1) < 1e-14
+    assert abs(I[1] ** -0.5 / g["c1"] - 1) < 1e-14
+    assert abs(I[2] ** -0.5 / g["c2"] - 1) < 1e-14

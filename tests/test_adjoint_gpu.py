@@ -1,0 +1,192 @@
+"""GPU adjoint (lbm_adjoint through the C ABI) against the FP64 oracle's
+adjoint, which tests/test_oracle_adjoint.py pins to finite differences, plus
+GPU-side finite differences, checkpoint invariance and the autograd wrapper."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1710_09472_gb300 import workloads as wl
+from tests.helpers import THETA, rel_linf
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_09472_gb300.build import build
+
+    build()
+
+
+def _case(vel):
+    if vel == "D2V9":
+        shape = (14, 40)
+        mask, _ = wl.boolean_obstacles(shape, 2.5, 0.8, seed=81)
+        B = (0.0, 0.0, 2e-2)
+    else:
+        shape = (6, 7, 36)
+        mask, _ = wl.boolean_obstacles(shape, 1.5, 0.8, seed=82)
+        B = (1e-2, -2e-2, 3e-2)
+    D = len(shape)
+    N = mask.size
+    Ef = np.zeros((D,) + shape, dtype=np.float32)
+    Ef[0] = (1e-3 + 2e-4 * wl.normal(83, N)).reshape(shape)
+    Ef[1] = (3e-4 * wl.normal(84, N)).reshape(shape)
+    rho0 = (1.0 + 0.02 * wl.uniform01(85, N)).reshape(shape).astype(np.float32)
+    u0 = (0.01 * wl.normal(86, D * N)).reshape((D,) + shape).astype(np.float32)
+    wr = wl.normal(87, N).reshape(shape).astype(np.float32)
+    wj = wl.normal(88, D * N).reshape((D,) + shape).astype(np.float32)
+    return shape, mask, B, Ef, rho0, u0, wr, wj
+
+
+def _gpu_sim(vel, shape, mask, B, Ef, rho0, u0, tau, force, storage="f32"):
+    from paper_1710_09472_gb300.lbm import LBM
+
+    sim = LBM(vel, tuple(reversed(shape)), tau, B=B, storage=storage, force=force)
+    sim.set_geometry(mask.reshape(-1))
+    sim.set_E_field(torch.from_numpy(Ef.reshape(-1)).cuda())
+    sim.init_equilibrium(torch.from_numpy(rho0.reshape(-1)).cuda(), torch.from_numpy(u0.reshape(-1)).cuda())
+    return sim
+
+
+@pytest.mark.parametrize("vel", ["D2V9", "D3V19"])
+@pytest.mark.parametrize("force", ["term", "shift"])
+def test_adjoint_matches_oracle(vel, force):
+    shape, mask, B, Ef, rho0, u0, wr, wj = _case(vel)
+    tau, T, tb = 0.75, 14, 6
+    sim = _gpu_sim(vel, shape, mask, B, Ef, rho0, u0, tau, force)
+    D, Q, N = sim.D, sim.Q, sim.N
+    dE = torch.empty(D * N, dtype=torch.float64, device="cuda")
+    lam0 = torch.empty(Q * N, dtype=torch.float32, device="cuda")
+    res = sim.adjoint(tb, T, torch.from_numpy(wr.reshape(-1)).cuda(), torch.from_numpy(wj.reshape(-1)).cuda(),
+                      checkpoint_every=4, dL_dE=dE, dL_df0=lam0)
+    m = oracle.Model(vel, "fd", THETA, 1.0, tau=tau, B=B, force=force)
+    f0 = m.init_equilibrium(shape, mask, rho0.astype(np.float64), u0.astype(np.float64))
+    states = m.trajectory(shape, mask, f0, T, Ef.astype(np.float64))
+    ref = m.adjoint(shape, mask, states, tb, T, wr.astype(np.float64), wj.astype(np.float64), Ef.astype(np.float64))
+    assert abs(res["loss"] / ref["loss"] - 1) < 1e-5
+    gE = dE.cpu().numpy().reshape(ref["gE"].shape)
+    assert rel_linf(gE, ref["gE"]) < 1e-4, rel_linf(gE, ref["gE"])
+    assert rel_linf(lam0.cpu().numpy(), ref["lam0"]) < 1e-4
+    comps = [2] if vel == "D2V9" else [0, 1, 2]
+    for c in comps:
+        assert abs(res["dL_dB"][c] - ref["gB"][c]) < 1e-4 * max(abs(ref["gB"][c]), 1e-2 * np.abs(ref["gB"]).max())
+    assert abs(res["dL_dtau"] / ref["gtau"] - 1) < 1e-4
+    sim.close()
+
+
+def test_checkpoint_spacing_does_not_change_the_result():
+    shape, mask, B, Ef, rho0, u0, wr, wj = _case("D2V9")
+    outs = []
+    for K in (1, 3, 0, 20):
+        sim = _gpu_sim("D2V9", shape, mask, B, Ef, rho0, u0, 0.8, "term")
+        dE = torch.empty(sim.D * sim.N, dtype=torch.float64, device="cuda")
+        res = sim.adjoint(10, 20, wr.reshape(-1), wj.reshape(-1), checkpoint_every=K, dL_dE=dE)
+        outs.append((res, dE.cpu().numpy()))
+        assert sim.info()["steps"] == 20
+        sim.close()
+    for res, dE in outs[1:]:
+        assert res["loss"] == outs[0][0]["loss"] and res["dL_dtau"] == outs[0][0]["dL_dtau"]
+        assert np.array_equal(dE, outs[0][1])
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_adjoint_vs_gpu_finite_differences(storage):
+    """Central differences of the GPU forward (window totals) in tau, B_z and
+    the uniform E_x: relative agreement 1e-3."""
+    from paper_1710_09472_gb300.lbm import LBM
+
+    shape = (32, 48)
+    mask, _ = wl.boolean_obstacles(shape, 3.0, 0.75, seed=91)
+    tau, E, B = 0.7, (2e-3, 5e-4), (0.0, 0.0, 5e-2)
+    T, tb = 60, 40
+
+    def loss(tau_, E_, B_):
+        sim = LBM("D2V9", (48, 32), tau_, E=E_, B=B_, storage=storage, force="term")
+        sim.set_geometry(mask.reshape(-1))
+        sim.init_equilibrium()
+        tot = sim.window_totals(tb, T)
+        sim.close()
+        return tot[1]  # sum over the window of the total x-current
+
+    sim = LBM("D2V9", (48, 32), tau, E=E, B=B, storage=storage, force="term")
+    sim.set_geometry(mask.reshape(-1))
+    sim.init_equilibrium()
+    wj = np.zeros((2, sim.N), dtype=np.float32)
+    wj[0] = 1.0
+    dE = torch.empty(2 * sim.N, dtype=torch.float64, device="cuda")
+    res = sim.adjoint(tb, T, None, wj.reshape(-1), 0, dL_dE=dE)
+    sim.close()
+    gEx = float(dE.view(2, -1)[0].sum())
+    h = 0.02
+    fd_tau = (loss(tau * (1 + h), E, B) - loss(tau * (1 - h), E, B)) / (2 * h * tau)
+    fd_B = (loss(tau, E, (0, 0, B[2] * (1 + h))) - loss(tau, E, (0, 0, B[2] * (1 - h)))) / (2 * h * B[2])
+    fd_E = (loss(tau, (E[0] * (1 + h), E[1]), B) - loss(tau, (E[0] * (1 - h), E[1]), B)) / (2 * h * E[0])
+    assert abs(res["dL_dtau"] / fd_tau - 1) < 1e-3, (res["dL_dtau"], fd_tau)
+    assert abs(res["dL_dB"][2] / fd_B - 1) < 1e-3, (res["dL_dB"][2], fd_B)
+    assert abs(gEx / fd_E - 1) < 1e-3, (gEx, fd_E)
+
+
+def test_differentiable_porous_reduced_vs_oracle():
+    """A 128^2 copy of the differentiable porous workload (disks r = 8,
+    porosity 0.6, per-cell E_x ~ N(1e-6, 1e-7), tau = 0.7): 300 steps, loss =
+    total x-current over the last 50, checkpoints every 20; per-cell dL/dE
+    against the FP64 oracle adjoint."""
+    w = wl.porous_2d_differentiable(n=128, steps=300)
+    shape, mask, Ef = w["shape"], w["solid"], w["Efield"]
+    T, tb = 300, 250
+    from paper_1710_09472_gb300.lbm import LBM
+
+    sim = LBM("D2V9", (128, 128), w["tau"], storage="f32", force="term")
+    sim.set_geometry(mask.reshape(-1))
+    sim.set_E_field(torch.from_numpy(Ef.reshape(-1)).cuda())
+    sim.init_equilibrium()
+    wj = np.zeros((2,) + shape, dtype=np.float32)
+    wj[0] = 1.0
+    dE = torch.empty(2 * sim.N, dtype=torch.float64, device="cuda")
+    res = sim.adjoint(tb, T, None, wj.reshape(-1), 20, dL_dE=dE)
+    sim.close()
+    m = oracle.Model("D2V9", "fd", THETA, 1.0, tau=w["tau"], force="term")
+    f0 = m.init_equilibrium(shape, mask, np.ones(shape))
+    states = m.trajectory(shape, mask, f0, T, Ef.astype(np.float64))
+    ref = m.adjoint(shape, mask, states, tb, T, None, wj.astype(np.float64), Ef.astype(np.float64))
+    gE = dE.cpu().numpy().reshape(ref["gE"].shape)
+    assert abs(res["loss"] / ref["loss"] - 1) < 1e-4
+    assert rel_linf(gE, ref["gE"]) < 1e-4, rel_linf(gE, ref["gE"])
+
+
+def test_autograd_function():
+    from paper_1710_09472_gb300.autograd import WindowCurrent
+    from paper_1710_09472_gb300.lbm import LBM
+
+    shape = (20, 30)
+    mask, _ = wl.boolean_obstacles(shape, 2.0, 0.8, seed=95)
+    sim = LBM("D2V9", (30, 20), 0.8, storage="f32", force="term")
+    sim.set_geometry(mask.reshape(-1))
+    sim.init_equilibrium()
+    E = torch.full((2,) + shape, 1e-4, dtype=torch.float32, device="cuda")
+    E[1] = 0.0
+    E.requires_grad_(True)
+    B = torch.tensor([0.0, 0.0, 1e-2], dtype=torch.float64, requires_grad=True)
+    tau = torch.tensor(0.8, dtype=torch.float64, requires_grad=True)
+    J = WindowCurrent.apply(E, B, tau, sim, 20, 40, 5)
+    L = J[1] + 0.5 * J[2]
+    L.backward()
+    # the same gradient through the library call directly
+    sim2 = LBM("D2V9", (30, 20), 0.8, B=(0, 0, 1e-2), storage="f32", force="term")
+    sim2.set_geometry(mask.reshape(-1))
+    sim2.set_E_field(E.detach().contiguous().view(-1))
+    sim2.init_equilibrium()
+    wj = torch.zeros(2, sim2.N, device="cuda")
+    wj[0] = 1.0
+    wj[1] = 0.5
+    dE = torch.empty(2 * sim2.N, dtype=torch.float64, device="cuda")
+    res = sim2.adjoint(20, 40, None, wj.view(-1), 5, dL_dE=dE)
+    assert torch.allclose(E.grad.double().view(-1), dE, rtol=1e-6, atol=0)
+    assert abs(float(tau.grad) - res["dL_dtau"]) <= 1e-9 * abs(res["dL_dtau"])
+    assert abs(float(B.grad[2]) - res["dL_dB"][2]) <= 1e-9 * abs(res["dL_dB"][2])
+    sim.close()
+    sim2.close()

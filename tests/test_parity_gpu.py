@@ -67,6 +67,7 @@ def test_parity_2d_ragged(storage, force, efield):
     rg, jg, totg, sim = gpu_run("D2V9", shape, solid, 0.7, T, storage, force, E, B, rho, u, Ef)
     ro, jo, toto, _, _ = oracle_run("D2V9", shape, solid, 0.7, T, force, E, B, rho, u, Ef)
     er, ej = rel_linf(rg, ro), rel_linf(jg, jo)
+    print(f"2d {storage} {force} efield={efield}: rho {er:.3e} j {ej:.3e}")
     assert er <= TOL[storage] and ej <= TOL[storage], (er, ej)
     assert abs(totg[0] / toto[0] - 1) < 1e-6
     sim.close()
@@ -91,6 +92,7 @@ def test_parity_3d_ragged(storage, force, efield):
     rg, jg, totg, sim = gpu_run("D3V19", shape, solid, 0.8, T, storage, force, E, B, rho, u, Ef)
     ro, jo, toto, _, _ = oracle_run("D3V19", shape, solid, 0.8, T, force, E, B, rho, u, Ef)
     er, ej = rel_linf(rg, ro), rel_linf(jg, jo)
+    print(f"3d {storage} {force} efield={efield}: rho {er:.3e} j {ej:.3e}")
     assert er <= TOL[storage] and ej <= TOL[storage], (er, ej)
     sim.close()
 
@@ -112,18 +114,20 @@ def test_populations_elementwise(vel):
     sim.close()
 
 
-def test_config_poiseuille_32x64():
-    """Config: Poiseuille 32 x 64, E_x = 1e-6, tau = 0.8, 5000 steps (shift
-    forcing, as in Sec. 9.3)."""
+@pytest.mark.parametrize("force", ["term", "shift"])
+def test_config_poiseuille_32x64(force):
+    """Config: Poiseuille 32 x 64, E_x = 1e-6, tau = 0.8, 5000 steps (Sec. 9.3
+    forces with the velocity shift; the explicit term is the default here)."""
     w = wl.poiseuille_32x64()
-    ro, jo, toto, _, _ = oracle_run("D2V9", w["shape"], w["solid"], w["tau"], w["steps"], "shift", w["E"])
+    ro, jo, toto, _, _ = oracle_run("D2V9", w["shape"], w["solid"], w["tau"], w["steps"], force, w["E"])
+    errs = {}
     for storage in ("f32", "f16", "bf16"):
-        rg, jg, totg, sim = gpu_run("D2V9", w["shape"], w["solid"], w["tau"], w["steps"], storage, "shift", w["E"])
-        er, ej = rel_linf(rg, ro), rel_linf(jg, jo)
-        print(f"poiseuille {storage}: rho {er:.3e} j {ej:.3e}")
-        if storage != "bf16":
-            assert er <= TOL[storage] and ej <= TOL[storage], (storage, er, ej)
+        rg, jg, totg, sim = gpu_run("D2V9", w["shape"], w["solid"], w["tau"], w["steps"], storage, force, w["E"])
+        errs[storage] = (rel_linf(rg, ro), rel_linf(jg, jo))
+        print(f"poiseuille {force} {storage}: rho {errs[storage][0]:.3e} j {errs[storage][1]:.3e}")
         sim.close()
+    for storage, (er, ej) in errs.items():
+        assert er <= TOL[storage] and ej <= TOL[storage], (storage, er, ej)
 
 
 def test_config_riemann_4096x8():
@@ -131,13 +135,14 @@ def test_config_riemann_4096x8():
     w = wl.riemann_4096x8()
     rho = w["rho"].astype(np.float32)
     ro, jo, toto, _, _ = oracle_run("D2V9", w["shape"], w["solid"], w["tau"], w["steps"], "term", rho=rho)
+    errs = {}
     for storage in ("f32", "f16", "bf16"):
         rg, jg, totg, sim = gpu_run("D2V9", w["shape"], w["solid"], w["tau"], w["steps"], storage, "term", rho=rho)
-        er, ej = rel_linf(rg, ro), rel_linf(jg, jo)
-        print(f"riemann {storage}: rho {er:.3e} j {ej:.3e}")
-        if storage != "bf16":
-            assert er <= TOL[storage] and ej <= TOL[storage], (storage, er, ej)
+        errs[storage] = (rel_linf(rg, ro), rel_linf(jg, jo))
+        print(f"riemann {storage}: rho {errs[storage][0]:.3e} j {errs[storage][1]:.3e}")
         sim.close()
+    for storage, (er, ej) in errs.items():
+        assert er <= TOL[storage] and ej <= TOL[storage], (storage, er, ej)
 
 
 # ---------------------------------------------------------------------------
@@ -216,7 +221,10 @@ def test_porous256_mass_conserved(porous256):
         m0, _ = sim.moments()
         sim.step(100)
         m1, j1 = sim.moments()
-        assert abs(m1 / m0 - 1) < 1e-9, (storage, m0, m1)
+        # FP32: summation round-off only; FP16: 100 roundings of each stored
+        # deviation (|h| ~ 1e-6 here, half an ulp ~ 2^-12 |h|)
+        bound = 1e-9 if storage == "f32" else 1e-7
+        assert abs(m1 / m0 - 1) < bound, (storage, m0, m1)
         assert sim.info()["n_fluid"] == int((w["solid"] == 0).sum())
         sim.close()
 
