@@ -209,6 +209,28 @@ lbm_status lbm_weight_integrals(int D, int stat, double theta, double mu, double
 lbm_status lbm_save_state(lbm_ctx* ctx, void* host_buf, size_t cap, size_t* used);
 lbm_status lbm_load_state(lbm_ctx* ctx, const void* host_buf, size_t len);
 
+/* FP64 fluid totals of the current state, like the totals of lbm_moments, but
+ * without any device allocation; the paper has no counterpart (this is a
+ * library service).  It is meant for callers that cannot or must not call
+ * the CUDA allocator where they read the totals, for example an application
+ * that reserves all device memory for its own pool up front, or a
+ * time-critical loop in which allocation calls are forbidden.
+ *   totals : 4 doubles in device memory, owned by the caller, written
+ *            asynchronously on the context's stream with
+ *            {sum rho, sum j_x, sum j_y, sum j_z} over fluid cells.
+ * The per-block partial sums live in one file-scope device array of 262144
+ * x 4 doubles (8 MiB), held by every GPU that loads the library until the
+ * process exits; grids needing more partials than that, i.e.
+ * ny * nz * ceil(nx / 128) > 262144, are rejected with INVALID_ARG and a
+ * message.  Each call overwrites every partial it reads, so nothing needs
+ * clearing; but every call in the process shares the one array, so calls
+ * whose kernels overlap on the GPU (different streams or contexts running
+ * concurrently) race and must be serialised by the caller.  The first call on
+ * a device looks up the array's device address once (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  The context's device must
+ * be current.  Errors: INVALID_ARG, STATE, CUDA. */
+lbm_status lbm_moment_totals_static(lbm_ctx* ctx, double* totals);
+
 /* Message of the last failed call on this context ("" if none). */
 const char* lbm_last_error(const lbm_ctx* ctx);
 

@@ -42,6 +42,7 @@ SIGNATURES = {
     "lbm_window_totals": (_i, [_vp, _i64, _i64, _vp]),
     "lbm_adjoint": (_i, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp]),
     "lbm_weight_integrals": (_i, [_i, _i, _d, _d, _vp]),
+    "lbm_moment_totals_static": (_i, [_vp, _vp]),
     "lbm_last_error": (ctypes.c_char_p, [_vp]),
     "lbm_status_string": (ctypes.c_char_p, [_i]),
     "lbm_launch_count": (_i64, [_vp]),

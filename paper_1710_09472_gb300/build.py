@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm.so")
-SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_adjoint.cu"]
+SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_adjoint.cu", "lbm_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

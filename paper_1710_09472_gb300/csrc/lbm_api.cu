@@ -11,6 +11,7 @@
 #include "lbm_internal.h"
 
 using lbm::KParams;
+using lbm::make_params;
 
 namespace {
 
@@ -138,7 +139,9 @@ bool is_device_ptr(const void* p) {
 
 size_t pop_elem_bytes(int storage) { return storage == LBM_F32 ? 4 : 2; }
 
-KParams make_params(const lbm_ctx* c) {
+}  // namespace
+
+lbm::KParams lbm::make_params(const lbm_ctx* c) {
     KParams p;
     std::memset(&p, 0, sizeof p);
     p.nx = (int)c->nx;
@@ -173,6 +176,8 @@ KParams make_params(const lbm_ctx* c) {
     p.inv_scale = (float)(1.0 / c->scale);
     return p;
 }
+
+namespace {
 
 void sanitize_fields(lbm_ctx* c) {
     if (c->D == 2) {  // only in-plane E and B_z act in 2D

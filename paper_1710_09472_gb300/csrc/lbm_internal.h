@@ -130,6 +130,11 @@ int launch_accumulate_totals(const double* partials, int64_t n_partials, double*
 
 }  // namespace lbm
 
+namespace lbm {
+// Kernel parameter block of a context (lbm_api.cu).
+KParams make_params(const lbm_ctx* c);
+}  // namespace lbm
+
 // The context (opaque to C callers).
 struct lbm_ctx {
     int device = 0;

@@ -162,6 +162,13 @@ class LBM:
             return tr.value, np.array(list(tj))
         return None
 
+    def moment_totals_static(self, out):
+        """FP64 totals into `out` (a float64 device tensor of 4) without any
+        device allocation (lbm_moment_totals_static)."""
+        _lib.check(_lib.load().lbm_moment_totals_static(self._h, _ptr(out, np.float64, 4, "totals")), self._h,
+                   "lbm_moment_totals_static")
+        return out
+
     def populations(self, out=None, deviation: bool = False):
         """f_a(x, t) (or the stored deviations h_a when deviation=True), Q*N FP32."""
         if out is None:
