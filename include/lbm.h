@@ -134,6 +134,16 @@ lbm_status lbm_set_geometry(lbm_ctx* ctx, const uint8_t* solid_mask);
  * Errors: INVALID_ARG, OOM, CUDA. */
 lbm_status lbm_set_E_field(lbm_ctx* ctx, const float* E);
 
+/* Rounding of FP16/BF16 stores: stochastic != 0 rounds each stored deviation
+ * up or down with probability given by its distance to the two neighbouring
+ * representable values (unbiased; the random bits are a hash of the step
+ * index, the cell and the direction, so a replayed step is bit-identical);
+ * 0 rounds to nearest even.  The default for FP16/BF16 storage is stochastic:
+ * with nearest rounding, per-step increments below half an ulp of the stored
+ * deviation are lost (for example the force increment of a 1e-6 field on
+ * a flow at u ~ 3e-3).  Errors: INVALID_ARG (FP32 storage with stochastic). */
+lbm_status lbm_set_rounding(lbm_ctx* ctx, int stochastic);
+
 /* Change tau, the uniform E and B between steps without reallocating.
  * E or B may be NULL (unchanged).  Errors: INVALID_ARG (tau <= 1/2). */
 lbm_status lbm_set_params(lbm_ctx* ctx, double tau, const double E[3], const double B[3]);

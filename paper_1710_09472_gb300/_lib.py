@@ -33,6 +33,7 @@ SIGNATURES = {
     "lbm_set_geometry": (_i, [_vp, _vp]),
     "lbm_set_E_field": (_i, [_vp, _vp]),
     "lbm_set_params": (_i, [_vp, _d, _vp, _vp]),
+    "lbm_set_rounding": (_i, [_vp, _i]),
     "lbm_init_equilibrium": (_i, [_vp, _vp, _vp]),
     "lbm_step": (_i, [_vp, _i64]),
     "lbm_moments": (_i, [_vp, _vp, _vp, _vp, _vp]),

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm.so")
-SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_adjoint.cu", "lbm_static.cu"]
+SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_adjoint.cu", "lbm_static.cu", "lbm_step_f32.cu", "lbm_step_f16.cu",
+           "lbm_step_bf16.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -41,7 +42,7 @@ def _stale(target, deps):
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "lbm.h"))
     objs = []
     jobs = []

@@ -283,6 +283,7 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_lattice* lat, const int64_t dims[
     }
     sanitize_fields(c);
     c->scale = storage == LBM_F16_DEV ? 4096.0 : 1.0;
+    c->stochastic = storage != LBM_F32;
 
     // --- constants (Sec. 3, 5.1, 8, 9.1) ---
     if (!weight_integrals(c->D, lat->stat, lat->theta, lat->mu, c->I)) {
@@ -435,6 +436,14 @@ lbm_status lbm_set_E_field(lbm_ctx* c, const float* E) {
     return LBM_OK;
 }
 
+lbm_status lbm_set_rounding(lbm_ctx* c, int stochastic) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (stochastic && c->storage == LBM_F32)
+        return fail(c, LBM_ERR_INVALID_ARG, "stochastic rounding applies to FP16/BF16 storage only");
+    c->stochastic = stochastic != 0;
+    return LBM_OK;
+}
+
 lbm_status lbm_set_params(lbm_ctx* c, double tau, const double E[3], const double B[3]) {
     if (!c) return LBM_ERR_INVALID_ARG;
     if (!(tau > 0.5) || !std::isfinite(tau)) return fail(c, LBM_ERR_INVALID_ARG, "tau must be > 1/2");
@@ -483,8 +492,9 @@ lbm_status lbm_step(lbm_ctx* c, int64_t n) {
     KParams p = make_params(c);
     const bool ef = c->use_Efield;
     for (int64_t t = 0; t < n; ++t) {
-        c->launches += lbm::launch_step(c->lat.vel, c->storage, c->lat.force, ef, c->pop[c->cur], c->pop[c->cur ^ 1],
-                                        c->nbr, c->Efield, p, c->stream);
+        p.step = (uint32_t)(c->steps + t);
+        c->launches += lbm::launch_step(c->lat.vel, c->storage, c->lat.force, ef, c->stochastic, c->pop[c->cur],
+                                        c->pop[c->cur ^ 1], c->nbr, c->Efield, p, c->stream);
         c->cur ^= 1;
     }
     c->steps += n;
@@ -614,8 +624,9 @@ lbm_status lbm_window_totals(lbm_ctx* c, int64_t t_begin, int64_t t_end, double 
         c->launches += lbm::launch_accumulate_totals(c->partials, np, c->totals_dev, c->stream);
     }
     for (int64_t t = 1; t <= t_end; ++t) {
-        c->launches += lbm::launch_step(c->lat.vel, c->storage, c->lat.force, c->use_Efield, c->pop[c->cur],
-                                        c->pop[c->cur ^ 1], c->nbr, c->Efield, p, c->stream);
+        p.step = (uint32_t)(c->steps + t - 1);
+        c->launches += lbm::launch_step(c->lat.vel, c->storage, c->lat.force, c->use_Efield, c->stochastic,
+                                        c->pop[c->cur], c->pop[c->cur ^ 1], c->nbr, c->Efield, p, c->stream);
         c->cur ^= 1;
         if (t > t_begin) {
             c->launches += lbm::launch_moments(c->lat.vel, c->storage, c->pop[c->cur], c->nbr, nullptr, nullptr,
@@ -714,13 +725,15 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
     if (dL_dE) ADJ_CHECK(cudaMemsetAsync(dL_dE, 0, sizeof(double) * (size_t)c->D * c->N, c->stream));
 
     const int vel = c->lat.vel, sto = c->storage, force = c->lat.force;
-    const bool ef = c->use_Efield;
+    const bool ef = c->use_Efield, sr = c->stochastic;
+    const int64_t step0 = c->steps;
     // --- forward with checkpoints every K steps ---
     for (int64_t t = 0; t < T; ++t) {
         if (t % K == 0)
             ADJ_CHECK(cudaMemcpyAsync(ckpt[t / K], c->pop[c->cur], pop_bytes, cudaMemcpyDeviceToDevice, c->stream));
-        c->launches += lbm::launch_step(vel, sto, force, ef, c->pop[c->cur], c->pop[c->cur ^ 1], c->nbr, c->Efield,
-                                        p, c->stream);
+        p.step = (uint32_t)(step0 + t);
+        c->launches += lbm::launch_step(vel, sto, force, ef, sr, c->pop[c->cur], c->pop[c->cur ^ 1], c->nbr,
+                                        c->Efield, p, c->stream);
         c->cur ^= 1;
     }
     ADJ_CHECK(cudaGetLastError());
@@ -733,8 +746,11 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
         const int64_t t0 = s * K, t1 = std::min(t0 + K, T);
         seg[0] = ckpt[s];
         for (int64_t t = t0; t < t1 - 1; ++t)
-            c->launches += lbm::launch_step(vel, sto, force, ef, seg[t - t0], seg[t - t0 + 1], c->nbr, c->Efield, p,
-                                            c->stream);
+        {
+            p.step = (uint32_t)(step0 + t);
+            c->launches += lbm::launch_step(vel, sto, force, ef, sr, seg[t - t0], seg[t - t0 + 1], c->nbr, c->Efield,
+                                            p, c->stream);
+        }
         for (int64_t t = t1 - 1; t >= t0; --t) {
             const bool win = t > t_begin && t <= t_end;
             c->launches += lbm::launch_adjoint_step(vel, sto, force, ef, win, seg[t - t0], lam[li], lam[li ^ 1],

@@ -52,22 +52,40 @@ __host__ __device__ constexpr int opposite(int a) { return a == 0 ? 0 : ((a & 1)
 // otherwise): raw() decodes to FP32 without unscaling, put() rounds to
 // nearest even.
 // ---------------------------------------------------------------------------
+// put_sr() rounds stochastically with 16 random bits r: the value is rounded
+// up in magnitude with probability equal to the dropped fraction, so the
+// expected stored value is the exact FP32 value (unbiased; no stagnation of
+// increments smaller than half an ulp).  FP16: 13 mantissa bits are dropped
+// from FP32 (exact for the normal FP16 range); BF16: 16 bits.
 struct StoreF32 {
     using T = float;
+    static constexpr int kBytes = 4;
     __device__ __forceinline__ static float raw(const T* p) { return __ldg(p); }
+    __device__ __forceinline__ static float cvt(T v) { return v; }
     __device__ __forceinline__ static void put(T* p, float v) { *p = v; }
+    __device__ __forceinline__ static void put_sr(T* p, float v, uint32_t) { *p = v; }
 };
 
 struct StoreF16 {
     using T = __half;
+    static constexpr int kBytes = 2;
     __device__ __forceinline__ static float raw(const T* p) { return __half2float(__ldg(p)); }
+    __device__ __forceinline__ static float cvt(T v) { return __half2float(v); }
     __device__ __forceinline__ static void put(T* p, float v) { *p = __float2half_rn(v); }
+    __device__ __forceinline__ static void put_sr(T* p, float v, uint32_t r) {
+        *p = __float2half_rz(__uint_as_float(__float_as_uint(v) + (r & 0x1FFFu)));
+    }
 };
 
 struct StoreBF16 {
     using T = __nv_bfloat16;
+    static constexpr int kBytes = 2;
     __device__ __forceinline__ static float raw(const T* p) { return __bfloat162float(__ldg(p)); }
+    __device__ __forceinline__ static float cvt(T v) { return __bfloat162float(v); }
     __device__ __forceinline__ static void put(T* p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ __forceinline__ static void put_sr(T* p, float v, uint32_t r) {
+        *p = __float2bfloat16_rz(__uint_as_float((__float_as_uint(v) + (r & 0xFFFFu)) & 0xFFFF0000u));
+    }
 };
 
 // ---------------------------------------------------------------------------
@@ -96,6 +114,8 @@ struct KParams {
     float f0[kMaxQ];  // rho0 w_a A: the rest equilibrium at rho0 (unscaled)
     float E[3], B[3];
     float scale, inv_scale;
+    uint32_t step;  // global step index of this launch (stochastic rounding stream)
+    uint32_t seed;
 };
 
 struct Launch {
@@ -107,8 +127,14 @@ int launch_build_neighbors(int vel, const uint8_t* mask, uint32_t* nbr, unsigned
                            const KParams& p, cudaStream_t s);
 int launch_init(int vel, int storage, void* pop, const uint8_t* mask, const float* rho, const float* u,
                 const KParams& p, cudaStream_t s);
-int launch_step(int vel, int storage, int force, bool efield, const void* fin, void* fout, const uint32_t* nbr,
-                const float* Ef, const KParams& p, cudaStream_t s);
+int launch_step(int vel, int storage, int force, bool efield, bool sr, const void* fin, void* fout,
+                const uint32_t* nbr, const float* Ef, const KParams& p, cudaStream_t s);
+int launch_step_f32(int vel, int force, bool efield, bool sr, const void* fin, void* fout, const uint32_t* nbr,
+                    const float* Ef, const KParams& p, cudaStream_t s);
+int launch_step_f16(int vel, int force, bool efield, bool sr, const void* fin, void* fout, const uint32_t* nbr,
+                    const float* Ef, const KParams& p, cudaStream_t s);
+int launch_step_bf16(int vel, int force, bool efield, bool sr, const void* fin, void* fout, const uint32_t* nbr,
+                     const float* Ef, const KParams& p, cudaStream_t s);
 int launch_moments(int vel, int storage, const void* pop, const uint32_t* nbr, float* rho, float* j,
                    double* partials, int64_t* n_partials, const KParams& p, cudaStream_t s);
 int launch_reduce_partials(const double* partials, int64_t n_partials, double* out4, cudaStream_t s);
@@ -144,6 +170,7 @@ struct lbm_ctx {
     int64_t nx = 1, ny = 1, nz = 1, N = 0;
     int64_t n_fluid = 0;
     int storage = 0;
+    bool stochastic = false;  // stochastic rounding of FP16/BF16 stores
     double tau = 1.0;
     double E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
     // host-side constants (FP64)

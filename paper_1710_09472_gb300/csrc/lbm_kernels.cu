@@ -22,7 +22,8 @@ using dev::Cell;
 using dev::kBlock;
 
 // ---------------------------------------------------------------------------
-// Link mask: bit a set when x + e_a is solid; kSolidBit when x is solid.
+// Link mask: fluid x: bit a set when x + e_a is solid; solid x: kSolidBit and
+// bit b set when x + e_b is fluid.
 // ---------------------------------------------------------------------------
 template <class L>
 __global__ void __launch_bounds__(kBlock) k_neighbors(const uint8_t* __restrict__ mask, uint32_t* __restrict__ nbr,
@@ -32,7 +33,12 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(const uint8_t* __restrict_
     if (dev::cell_of_thread(p, c)) {
         uint32_t m = 0;
         if (mask[c.cell]) {
+            // solid: bit b set when x + e_b is fluid (slot b is a ghost slot
+            // that the fluid cell x + e_b writes)
             m = kSolidBit;
+#pragma unroll
+            for (int b = 1; b < L::Q; ++b)
+                if (!mask[dev::shifted<L>(c, b, +1)]) m |= (1u << b);
         } else {
             fluid = 1;
 #pragma unroll
@@ -74,125 +80,6 @@ __global__ void __launch_bounds__(kBlock) k_init(typename S::T* __restrict__ P, 
             v = heq_unscaled<L>(p, b, r, uu) * p.scale;
         }
         S::put(P + (int64_t)b * p.N + c.cell, v);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// The fused step.  f(x, t) is pulled, its moments taken, the force applied,
-// f^eq formed and the BGK relaxation written (Sec. 9.1), all in scaled
-// deviations h~ = s (f - f0):
-//   h~*_a = (1 - w) h~_a + w heq~_a + S~_a,  w = 1/tau,
-//   heq~_a = w_a [A drho~ + s rho (Cp (e.u)^2 + k2_a u^2)] + W1_a (e_a . j~)   (+ shift part)
-// FORCE 0: velocity shift u* = u + tau (E + u x B) (Sec. 7, Eq.
-//          u-update-force-term-eq): the odd part uses j~ + s c_s rho tau a.
-// FORCE 1: S_a = a_a . grad_u f^eq_a with a_a = E + xi_a x B (Sec. 7, Eq.
-//          forcing-term-integrals-eq):
-//          S~_a = s rho w_a [2 Cp (e.u)(e.E) + 2 k2_a u.E]                  (even)
-//               + W1_a (e . s c_s rho E) + 2 s rho w_a k2_a (e.(B x u))/c_s (odd).
-// Opposite directions share the even part and negate the odd part, so the
-// work is done once per pair; the rest population closes the mass balance
-// exactly: h~*_0 = sum_a h~_a - sum_{a>0} h~*_a.
-// ---------------------------------------------------------------------------
-template <class L, class S, int FORCE, bool EF>
-__global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict__ Pin, typename S::T* __restrict__ Pout,
-                                                 const uint32_t* __restrict__ nbr, const float* __restrict__ Ef,
-                                                 KParams p) {
-    Cell c;
-    if (!dev::cell_of_thread(p, c)) return;
-    const uint32_t m = __ldg(nbr + c.cell);
-    if (m & kSolidBit) return;
-
-    float h[L::Q];
-    dev::pull_raw<L, S>(Pin, p.N, c, h);
-
-    // moments (scaled): drho~ = sum h~, j~ = sum h~ e (lattice units)
-    float drho = h[0], j[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int a = 1; a < L::Q; a += 2) {
-        const float sum = h[a] + h[a + 1], dif = h[a] - h[a + 1];
-        drho += sum;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (L::c(a, d) > 0) j[d] += dif;
-            if (L::c(a, d) < 0) j[d] -= dif;
-        }
-    }
-    const float rho = p.rho0 + drho * p.inv_scale;
-    const float q = p.inv_scale * p.cs_inv / rho;  // u = j~ q  (xi units)
-    const float u[3] = {j[0] * q, j[1] * q, j[2] * q};
-    const float srho = p.scale * rho;
-
-    float E[3];
-    if (EF) {
-        E[0] = __ldg(Ef + c.cell);
-        E[1] = __ldg(Ef + p.N + c.cell);
-        E[2] = (L::D == 3) ? __ldg(Ef + 2 * p.N + c.cell) : 0.f;
-    } else {
-        E[0] = p.E[0];
-        E[1] = p.E[1];
-        E[2] = p.E[2];
-    }
-
-    const float om = p.omega, omm = 1.0f - p.omega;
-    float ue[3], v[3];
-    float uE = 0.f, bu[3] = {0.f, 0.f, 0.f};
-    const float scr = srho * p.cs;  // s c_s rho
-    if (FORCE == 0) {
-        const float a0 = E[0] + (u[1] * p.B[2] - u[2] * p.B[1]);
-        const float a1 = E[1] + (u[2] * p.B[0] - u[0] * p.B[2]);
-        const float a2 = (L::D == 3) ? E[2] + (u[0] * p.B[1] - u[1] * p.B[0]) : 0.f;
-        ue[0] = u[0] + p.tau * a0;
-        ue[1] = u[1] + p.tau * a1;
-        ue[2] = u[2] + p.tau * a2;
-        // odd part of w heq~ at u*: W1 (e . w (j~ + s c_s rho tau a)) = W1 (e . (w j~ + s c_s rho a))
-        v[0] = om * j[0] + scr * a0;
-        v[1] = om * j[1] + scr * a1;
-        v[2] = om * j[2] + scr * a2;
-    } else {
-        ue[0] = u[0];
-        ue[1] = u[1];
-        ue[2] = u[2];
-        v[0] = om * j[0] + scr * E[0];
-        v[1] = om * j[1] + scr * E[1];
-        v[2] = om * j[2] + scr * E[2];
-        uE = u[0] * E[0] + u[1] * E[1] + u[2] * E[2];
-        const float tb = 2.f * srho * p.cs_inv;  // 2 s rho / c_s times (B x u)
-        bu[0] = tb * (p.B[1] * u[2] - p.B[2] * u[1]);
-        bu[1] = tb * (p.B[2] * u[0] - p.B[0] * u[2]);
-        bu[2] = tb * (p.B[0] * u[1] - p.B[1] * u[0]);
-    }
-    const float u2 = ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2];
-    const float omAdr = om * p.A * drho;
-
-    float out[L::Q];
-    float rest = drho;
-#pragma unroll
-    for (int a = 1; a < L::Q; a += 2) {
-        const float eu = dev::edot<L>(a, ue);
-        const float ev_ = dev::edot<L>(a, v);
-        float even = p.w[a] * (omAdr + om * srho * (p.Cp * eu * eu + p.k2[a] * u2));
-        float odd = p.W1hi[a] * ev_ + p.W1lo[a] * ev_;
-        if (FORCE == 1) {
-            const float eE = dev::edot<L>(a, E);
-            even += 2.f * srho * p.w[a] * (p.Cp * eu * eE + p.k2[a] * uE);
-            odd += p.w[a] * p.k2[a] * dev::edot<L>(a, bu);
-        }
-        const float ha = omm * h[a] + even + odd;
-        const float hb = omm * h[a + 1] + even - odd;
-        out[a] = ha;
-        out[a + 1] = hb;
-        rest -= ha + hb;
-    }
-    out[0] = rest;
-
-    // store; a link into a solid cell writes the ghost slot P_abar(x + e_a)
-    S::put(Pout + c.cell, out[0]);
-#pragma unroll
-    for (int a = 1; a < L::Q; ++a) {
-        const bool bounce = (m >> a) & 1u;
-        const int64_t idx = bounce ? (int64_t)opposite(a) * p.N + dev::shifted<L>(c, a, +1)
-                                   : (int64_t)a * p.N + c.cell;
-        S::put(Pout + idx, out[a]);
     }
 }
 
@@ -372,30 +259,11 @@ int launch_init(int vel, int storage, void* pop, const uint8_t* mask, const floa
     });
 }
 
-int launch_step(int vel, int storage, int force, bool efield, const void* fin, void* fout, const uint32_t* nbr,
-                const float* Ef, const KParams& p, cudaStream_t s) {
-    Launch l = grid_of(p);
-    return dispatch_lattice(vel, [&](auto lat) {
-        using L = decltype(lat);
-        return dispatch_storage(storage, [&](auto st) {
-            using S = decltype(st);
-            using T = typename S::T;
-            const T* in = (const T*)fin;
-            T* out = (T*)fout;
-            if (force == LBM_FORCE_SHIFT) {
-                if (efield)
-                    k_step<L, S, 0, true><<<l.grid, l.block, 0, s>>>(in, out, nbr, Ef, p);
-                else
-                    k_step<L, S, 0, false><<<l.grid, l.block, 0, s>>>(in, out, nbr, Ef, p);
-            } else {
-                if (efield)
-                    k_step<L, S, 1, true><<<l.grid, l.block, 0, s>>>(in, out, nbr, Ef, p);
-                else
-                    k_step<L, S, 1, false><<<l.grid, l.block, 0, s>>>(in, out, nbr, Ef, p);
-            }
-            return 1;
-        });
-    });
+int launch_step(int vel, int storage, int force, bool efield, bool sr, const void* fin, void* fout,
+                const uint32_t* nbr, const float* Ef, const KParams& p, cudaStream_t s) {
+    if (storage == LBM_F16_DEV) return launch_step_f16(vel, force, efield, sr, fin, fout, nbr, Ef, p, s);
+    if (storage == LBM_BF16_DEV) return launch_step_bf16(vel, force, efield, sr, fin, fout, nbr, Ef, p, s);
+    return launch_step_f32(vel, force, efield, false, fin, fout, nbr, Ef, p, s);
 }
 
 int launch_moments(int vel, int storage, const void* pop, const uint32_t* nbr, float* rho, float* j,

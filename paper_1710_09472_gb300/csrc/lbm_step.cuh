@@ -1,0 +1,537 @@
+// Step kernels of the semiclassical LBM (templates): the fused pull-stream +
+// BGK collision + Lorentz forcing update of Sec. 9.1, a general one-thread-
+// per-cell kernel and a row-staged persistent kernel, plus their launcher.
+// Included by one translation unit per storage type.
+#pragma once
+
+#include <mutex>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+namespace stepk {
+
+using dev::Cell;
+using dev::kBlock;
+
+// ---------------------------------------------------------------------------
+// The fused step.  f(x, t) is pulled, its moments taken, the force applied,
+// f^eq formed and the BGK relaxation written (Sec. 9.1), all in scaled
+// deviations h~ = s (f - f0):
+//   h~*_a = (1 - w) h~_a + w heq~_a + S~_a,  w = 1/tau,
+//   heq~_a = w_a [A drho~ + s rho (Cp (e.u)^2 + k2_a u^2)] + W1_a (e_a . j~)   (+ shift part)
+// FORCE 0: velocity shift u* = u + tau (E + u x B) (Sec. 7, Eq.
+//          u-update-force-term-eq): the odd part uses j~ + s c_s rho tau a.
+// FORCE 1: S_a = a_a . grad_u f^eq_a with a_a = E + xi_a x B (Sec. 7, Eq.
+//          forcing-term-integrals-eq):
+//          S~_a = s rho w_a [2 Cp (e.u)(e.E) + 2 k2_a u.E]                  (even)
+//               + W1_a (e . s c_s rho E) + 2 s rho w_a k2_a (e.(B x u))/c_s (odd).
+// Opposite directions share the even part and negate the odd part, so the
+// work is done once per pair; the rest population closes the mass balance
+// exactly: h~*_0 = sum_a h~_a - sum_{a>0} h~*_a.
+// ---------------------------------------------------------------------------
+template <class L, int FORCE>
+__device__ __forceinline__ void collide(const float* h, const float* E, const KParams& p, float* out) {
+    float drho = h[0], j[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 1; a < L::Q; a += 2) {
+        const float sum = h[a] + h[a + 1], dif = h[a] - h[a + 1];
+        drho += sum;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (L::c(a, d) > 0) j[d] += dif;
+            if (L::c(a, d) < 0) j[d] -= dif;
+        }
+    }
+    const float rho = p.rho0 + drho * p.inv_scale;
+    const float q = p.inv_scale * p.cs_inv / rho;  // u = j~ q  (xi units)
+    const float u[3] = {j[0] * q, j[1] * q, j[2] * q};
+    const float srho = p.scale * rho;
+    const float om = p.omega, omm = 1.0f - p.omega;
+    float ue[3], v[3];
+    float uE = 0.f, bu[3] = {0.f, 0.f, 0.f};
+    const float scr = srho * p.cs;  // s c_s rho
+    if (FORCE == 0) {
+        const float a0 = E[0] + (u[1] * p.B[2] - u[2] * p.B[1]);
+        const float a1 = E[1] + (u[2] * p.B[0] - u[0] * p.B[2]);
+        const float a2 = (L::D == 3) ? E[2] + (u[0] * p.B[1] - u[1] * p.B[0]) : 0.f;
+        ue[0] = u[0] + p.tau * a0;
+        ue[1] = u[1] + p.tau * a1;
+        ue[2] = u[2] + p.tau * a2;
+        // odd part of w heq~ at u*: W1 (e . w (j~ + s c_s rho tau a)) = W1 (e . (w j~ + s c_s rho a))
+        v[0] = om * j[0] + scr * a0;
+        v[1] = om * j[1] + scr * a1;
+        v[2] = om * j[2] + scr * a2;
+    } else {
+        ue[0] = u[0];
+        ue[1] = u[1];
+        ue[2] = u[2];
+        v[0] = om * j[0] + scr * E[0];
+        v[1] = om * j[1] + scr * E[1];
+        v[2] = om * j[2] + scr * E[2];
+        uE = u[0] * E[0] + u[1] * E[1] + u[2] * E[2];
+        const float tb = 2.f * srho * p.cs_inv;  // 2 s rho / c_s times (B x u)
+        bu[0] = tb * (p.B[1] * u[2] - p.B[2] * u[1]);
+        bu[1] = tb * (p.B[2] * u[0] - p.B[0] * u[2]);
+        bu[2] = tb * (p.B[0] * u[1] - p.B[1] * u[0]);
+    }
+    const float u2 = ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2];
+    const float omAdr = om * p.A * drho;
+    float rest = drho;
+#pragma unroll
+    for (int a = 1; a < L::Q; a += 2) {
+        const float eu = dev::edot<L>(a, ue);
+        const float ev_ = dev::edot<L>(a, v);
+        float even = p.w[a] * (omAdr + om * srho * (p.Cp * eu * eu + p.k2[a] * u2));
+        float odd = p.W1hi[a] * ev_ + p.W1lo[a] * ev_;
+        if (FORCE == 1) {
+            const float eE = dev::edot<L>(a, E);
+            even += 2.f * srho * p.w[a] * (p.Cp * eu * eE + p.k2[a] * uE);
+            odd += p.w[a] * p.k2[a] * dev::edot<L>(a, bu);
+        }
+        const float ha = omm * h[a] + even + odd;
+        const float hb = omm * h[a + 1] + even - odd;
+        out[a] = ha;
+        out[a + 1] = hb;
+        rest -= ha + hb;
+    }
+    out[0] = rest;
+}
+
+// Error-free transformations (Knuth TwoSum, FMA TwoProd) for the compensated
+// FP32 collision below.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = a * b;
+    e = __fmaf_rn(a, b, -p);
+}
+
+// Compensated collision for FP32 storage.  Same formulas as collide(), but the
+// moments, the momentum-carrying odd parts (w j~ + s c_s rho E, times W1) and
+// the final combination (1 - w) h + even + odd are carried as double-float
+// (hi + lo) and rounded once when stored.  With plain FP32 these steps add
+// several roundings of size eps |h| per population and step, which over
+// thousands of steps exceed the 1e-5 target for FP32 storage (the FP32
+// storage rounding alone stays near 1e-6).
+template <class L, int FORCE>
+__device__ __forceinline__ void collide_acc(const float* h, const float* E, const KParams& p, float* out) {
+    float drho = h[0], drho_lo = 0.f, j[3] = {0.f, 0.f, 0.f}, jl[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 1; a < L::Q; a += 2) {
+        float sum, es, dif, ed, e;
+        two_sum(h[a], h[a + 1], sum, es);
+        two_sum(h[a], -h[a + 1], dif, ed);
+        two_sum(drho, sum, drho, e);
+        drho_lo += e + es;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (L::c(a, d) > 0) {
+                two_sum(j[d], dif, j[d], e);
+                jl[d] += e + ed;
+            }
+            if (L::c(a, d) < 0) {
+                two_sum(j[d], -dif, j[d], e);
+                jl[d] += e - ed;
+            }
+        }
+    }
+    const float drho_f = drho + drho_lo;
+    const float rho = p.rho0 + drho_f * p.inv_scale;
+    const float jf[3] = {j[0] + jl[0], j[1] + jl[1], j[2] + jl[2]};
+    const float q = p.inv_scale * p.cs_inv / rho;
+    const float u[3] = {jf[0] * q, jf[1] * q, jf[2] * q};
+    const float srho = p.scale * rho;
+    const float om = p.omega, omm = 1.0f - p.omega;
+    const float scr = srho * p.cs;
+    float ue[3], F[3], uE = 0.f, bu[3] = {0.f, 0.f, 0.f};
+    if (FORCE == 0) {
+        F[0] = E[0] + (u[1] * p.B[2] - u[2] * p.B[1]);
+        F[1] = E[1] + (u[2] * p.B[0] - u[0] * p.B[2]);
+        F[2] = (L::D == 3) ? E[2] + (u[0] * p.B[1] - u[1] * p.B[0]) : 0.f;
+        ue[0] = u[0] + p.tau * F[0];
+        ue[1] = u[1] + p.tau * F[1];
+        ue[2] = u[2] + p.tau * F[2];
+    } else {
+        F[0] = E[0];
+        F[1] = E[1];
+        F[2] = E[2];
+        ue[0] = u[0];
+        ue[1] = u[1];
+        ue[2] = u[2];
+        uE = u[0] * E[0] + u[1] * E[1] + u[2] * E[2];
+        const float tb = 2.f * srho * p.cs_inv;
+        bu[0] = tb * (p.B[1] * u[2] - p.B[2] * u[1]);
+        bu[1] = tb * (p.B[2] * u[0] - p.B[0] * u[2]);
+        bu[2] = tb * (p.B[0] * u[1] - p.B[1] * u[0]);
+    }
+    // v = w j~ + s c_s rho F as hi + lo
+    float vh[3], vl[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float pp, ep, e;
+        two_prod(om, j[d], pp, ep);
+        two_sum(pp, scr * F[d], vh[d], e);
+        vl[d] = e + ep + om * jl[d];
+    }
+    const float u2 = ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2];
+    const float omAdr = om * p.A * drho_f;
+    float rest = drho, rest_lo = drho_lo;
+#pragma unroll
+    for (int a = 1; a < L::Q; a += 2) {
+        const float eu = dev::edot<L>(a, ue);
+        float even = p.w[a] * (omAdr + om * srho * (p.Cp * eu * eu + p.k2[a] * u2));
+        // e . v in double-float
+        float evh = 0.f, evl = 0.f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            float e;
+            if (L::c(a, d) > 0) {
+                two_sum(evh, vh[d], evh, e);
+                evl += e + vl[d];
+            }
+            if (L::c(a, d) < 0) {
+                two_sum(evh, -vh[d], evh, e);
+                evl += e - vl[d];
+            }
+        }
+        // odd = W1 (e . v): double-float product
+        float oh, ol;
+        two_prod(p.W1hi[a], evh, oh, ol);
+        ol += p.W1hi[a] * evl + p.W1lo[a] * evh;
+        if (FORCE == 1) {
+            const float eE = dev::edot<L>(a, E);
+            even += 2.f * srho * p.w[a] * (p.Cp * eu * eE + p.k2[a] * uE);
+            ol += p.w[a] * p.k2[a] * dev::edot<L>(a, bu);
+        }
+        // (1 - w) h + even +/- odd, rounded once
+        float pa, ea, pb, eb, sa, sb, e1, e2;
+        two_prod(omm, h[a], pa, ea);
+        two_prod(omm, h[a + 1], pb, eb);
+        two_sum(pa, even, sa, e1);
+        two_sum(pb, even, sb, e2);
+        float ta, tb2, e3, e4;
+        two_sum(sa, oh, ta, e3);
+        two_sum(sb, -oh, tb2, e4);
+        const float ha = ta + (ea + e1 + e3 + ol);
+        const float hb = tb2 + (eb + e2 + e4 - ol);
+        out[a] = ha;
+        out[a + 1] = hb;
+        float e5, e6;
+        two_sum(rest, -ha, rest, e5);
+        two_sum(rest, -hb, rest, e6);
+        rest_lo += e5 + e6;
+    }
+    out[0] = rest + rest_lo;
+}
+
+// Counter-based random bits for stochastic rounding: a hash of (step, cell,
+// direction pair) (the "lowbias32" integer hash of C. Wellons), so that a
+// replayed step reproduces its stores bit for bit.
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+template <class S, bool SR>
+__device__ __forceinline__ void store_val(typename S::T* ptr, float v, uint32_t rnd) {
+    if (SR)
+        S::put_sr(ptr, v, rnd);
+    else
+        S::put(ptr, v);
+}
+
+// Store one fluid cell's post-collision values.  Every own slot is written
+// (0 on a bounced link), and a link into a solid cell also writes the ghost
+// slot P_abar(x + e_a), so that together with the solid cells' own writes
+// every slot is written once per step (whole sectors, no partial-sector
+// merges in L2).
+template <class L, class S, bool SR>
+__device__ __forceinline__ void store_fluid(typename S::T* __restrict__ Pout, uint32_t m, const Cell& c,
+                                            const float* out, const KParams& p) {
+    // random stream: one hash of (cell, step) per cell, then a 32-bit LCG
+    // (Numerical Recipes constants) whose upper 16 bits feed each store
+    uint32_t x = 0;
+    if (SR) x = hash32(c.cell ^ hash32(p.step * 0x9E3779B9u + p.seed));
+    auto next = [&]() {
+        x = x * 1664525u + 1013904223u;
+        return x >> 16;
+    };
+    store_val<S, SR>(Pout + c.cell, out[0], SR ? next() : 0u);
+#pragma unroll
+    for (int a = 1; a < L::Q; ++a) {
+        const uint32_t rnd = SR ? next() : 0u;
+        const bool bounce = (m >> a) & 1u;
+        typename S::T* own = Pout + (int64_t)a * p.N + c.cell;
+        if (bounce) {
+            S::put(own, 0.f);
+            store_val<S, SR>(Pout + (int64_t)opposite(a) * p.N + dev::shifted<L>(c, a, +1), out[a], rnd);
+        } else {
+            store_val<S, SR>(own, out[a], rnd);
+        }
+    }
+}
+
+// A solid cell writes 0 into every slot that is not a ghost slot (bit b of its
+// mask: x + e_b is fluid, so that fluid cell writes slot b).
+template <class L, class S>
+__device__ __forceinline__ void store_solid(typename S::T* __restrict__ Pout, uint32_t m, const Cell& c,
+                                            const KParams& p) {
+    S::put(Pout + c.cell, 0.f);
+#pragma unroll
+    for (int b = 1; b < L::Q; ++b)
+        if (!((m >> b) & 1u)) S::put(Pout + (int64_t)b * p.N + c.cell, 0.f);
+}
+
+template <class L>
+__device__ __forceinline__ void load_E(const float* __restrict__ Ef, bool ef, const KParams& p, uint32_t cell,
+                                       float* E) {
+    if (ef) {
+        E[0] = __ldg(Ef + cell);
+        E[1] = __ldg(Ef + p.N + cell);
+        E[2] = (L::D == 3) ? __ldg(Ef + 2 * p.N + cell) : 0.f;
+    } else {
+        E[0] = p.E[0];
+        E[1] = p.E[1];
+        E[2] = p.E[2];
+    }
+}
+
+// General step kernel: one thread per cell, pulls straight from global memory.
+template <class L, class S, int FORCE, bool EF, bool SR>
+__global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict__ Pin, typename S::T* __restrict__ Pout,
+                                                 const uint32_t* __restrict__ nbr, const float* __restrict__ Ef,
+                                                 KParams p) {
+    Cell c;
+    if (!dev::cell_of_thread(p, c)) return;
+    const uint32_t m = __ldg(nbr + c.cell);
+    if (m & kSolidBit) {
+        store_solid<L, S>(Pout, m, c, p);
+        return;
+    }
+    float h[L::Q];
+    dev::pull_raw<L, S>(Pin, p.N, c, h);
+    float E[3];
+    load_E<L>(Ef, EF, p, c.cell, E);
+    float out[L::Q];
+    if (S::kBytes == 4)
+        collide_acc<L, FORCE>(h, E, p, out);
+    else
+        collide<L, FORCE>(h, E, p, out);
+    store_fluid<L, S, SR>(Pout, m, c, out, p);
+}
+
+// ---------------------------------------------------------------------------
+// Row-staged step kernel (used when a whole x-row of one direction is a
+// multiple of 16 bytes and fits the shared-memory ring).  A persistent block
+// walks rows r = blockIdx.x, blockIdx.x + gridDim.x, ...; for each row the 19
+// (or 9) source rows P_a(y - e_ay, z - e_az, :) are copied whole into shared
+// memory with 16-byte asynchronous copies (cp.async.cg, L1 bypass), STAGES - 1
+// rows ahead of the row being computed.  The x-shift (with its periodic wrap)
+// is then a shared-memory index, global reads are aligned full rows, and each
+// block keeps (STAGES - 1) x Q x nx x b bytes in flight.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// e_ay + 1 and e_az + 1 of every direction, 2 bits each, in two 64-bit words
+// (19 directions need 38 bits per word); the unrolled loops fold to constants.
+template <class L>
+__device__ __forceinline__ unsigned long long packed_y() {
+    unsigned long long v = 0;
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) v |= (unsigned long long)(L::c(a, 1) + 1) << (2 * a);
+    return v;
+}
+template <class L>
+__device__ __forceinline__ unsigned long long packed_z() {
+    unsigned long long v = 0;
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) v |= (unsigned long long)(L::c(a, 2) + 1) << (2 * a);
+    return v;
+}
+
+template <class L, class S>
+__device__ __forceinline__ void stage_row(typename S::T* __restrict__ buf, const typename S::T* __restrict__ Pin,
+                                          int row, int cpr_shift, const KParams& p) {
+    constexpr int kElem16 = 16 / S::kBytes;
+    const unsigned long long kPy = packed_y<L>(), kPz = packed_z<L>();
+    static_assert(L::Q <= 32, "direction codes must fit 64 bits");
+    const int cpr = 1 << cpr_shift;  // 16-byte chunks per row (a power of two)
+    const int y = row % p.ny, z = row / p.ny;
+    const int total = L::Q << cpr_shift;
+    for (int k = threadIdx.x; k < total; k += blockDim.x) {
+        const int a = k >> cpr_shift, off = k & (cpr - 1);
+        const int ey = (int)((kPy >> (2 * a)) & 3ull) - 1, ez = (int)((kPz >> (2 * a)) & 3ull) - 1;
+        // source row of direction a: (y - e_ay, z - e_az) with periodic wrap
+        int ys = y - ey, zs = z - ez;
+        ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
+        zs = zs < 0 ? zs + p.nz : (zs >= p.nz ? zs - p.nz : zs);
+        const int64_t src = (int64_t)a * p.N + ((int64_t)zs * p.ny + ys) * p.nx + (int64_t)off * kElem16;
+        cp_async16(buf + a * p.nx + off * kElem16, Pin + src);
+    }
+}
+
+template <class L, class S, int FORCE, bool EF, bool SR, int STAGES>
+__global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restrict__ Pin,
+                                                   typename S::T* __restrict__ Pout, const uint32_t* __restrict__ nbr,
+                                                   const float* __restrict__ Ef, int cpr_shift, KParams p) {
+    using T = typename S::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* ring = reinterpret_cast<T*>(smem_raw);
+    const int stage_elems = L::Q * p.nx;
+    const int R = p.ny * p.nz;
+    const int G = gridDim.x;
+    // prologue: the first STAGES - 1 rows of this block
+#pragma unroll
+    for (int k = 0; k < STAGES - 1; ++k) {
+        const int rk = blockIdx.x + k * G;
+        if (rk < R) stage_row<L, S>(ring + k * stage_elems, Pin, rk, cpr_shift, p);
+        cp_async_commit();
+    }
+    int it = 0;
+    for (int r = blockIdx.x; r < R; r += G, ++it) {
+        const int rn = r + (STAGES - 1) * G;
+        if (rn < R) stage_row<L, S>(ring + ((it + STAGES - 1) % STAGES) * stage_elems, Pin, rn, cpr_shift, p);
+        cp_async_commit();
+        cp_async_wait<STAGES - 1>();
+        __syncthreads();
+        const T* buf = ring + (it % STAGES) * stage_elems;
+        Cell c;
+        c.y = r % p.ny;
+        c.z = r / p.ny;
+        const int ys[3] = {c.y == 0 ? p.ny - 1 : c.y - 1, c.y, c.y == p.ny - 1 ? 0 : c.y + 1};
+        const int zs[3] = {c.z == 0 ? p.nz - 1 : c.z - 1, c.z, c.z == p.nz - 1 ? 0 : c.z + 1};
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                c.r[i][k] = ((uint32_t)zs[k] * (uint32_t)p.ny + (uint32_t)ys[i]) * (uint32_t)p.nx;
+        for (int x = threadIdx.x; x < p.nx; x += blockDim.x) {
+            c.x = x;
+            c.xm = x == 0 ? p.nx - 1 : x - 1;
+            c.xp = x == p.nx - 1 ? 0 : x + 1;
+            c.cell = (uint32_t)r * (uint32_t)p.nx + (uint32_t)x;
+            const uint32_t m = __ldg(nbr + c.cell);
+            if (m & kSolidBit) {
+                store_solid<L, S>(Pout, m, c, p);
+                continue;
+            }
+            float h[L::Q];
+#pragma unroll
+            for (int a = 0; a < L::Q; ++a) {
+                const int ex = L::c(a, 0);
+                const int xs = ex > 0 ? c.xm : (ex < 0 ? c.xp : x);
+                h[a] = S::cvt(buf[a * p.nx + xs]);
+            }
+            float E[3];
+            load_E<L>(Ef, EF, p, c.cell, E);
+            float out[L::Q];
+            if (S::kBytes == 4)
+                collide_acc<L, FORCE>(h, E, p, out);
+            else
+                collide<L, FORCE>(h, E, p, out);
+            store_fluid<L, S, SR>(Pout, m, c, out, p);
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+}
+
+
+// ---------------------------------------------------------------------------
+// Launch policy.  The row-staged kernel runs when a row of one direction is a
+// multiple of 16 bytes and STAGES rows of all directions fit the shared-memory
+// budget; otherwise the general kernel runs.  The persistent grid is the
+// number of co-resident blocks (occupancy API) times the SM count, capped by
+// the number of rows.
+// ---------------------------------------------------------------------------
+constexpr int kStages = 3;
+constexpr int kRowThreads = 256;
+constexpr size_t kSmemBudget = 160 * 1024;
+
+template <class K>
+int persistent_grid(K kernel, int threads, size_t smem) {
+    static std::mutex mu;
+    static const void* last_k = nullptr;
+    static size_t last_smem = 0;
+    static int last_threads = 0, last_blocks = 0, sms = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((const void*)kernel != last_k || smem != last_smem || threads != last_threads) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+        last_k = (const void*)kernel;
+        last_smem = smem;
+        last_threads = threads;
+        last_blocks = per_sm > 0 ? per_sm * sms : 0;
+    }
+    return last_blocks;
+}
+
+template <class L, class S, int FORCE, bool EF, bool SR>
+int launch_one(const void* fin, void* fout, const uint32_t* nbr, const float* Ef, const KParams& p, cudaStream_t s) {
+    using T = typename S::T;
+    const T* in = (const T*)fin;
+    T* out = (T*)fout;
+    const size_t row_bytes = (size_t)p.nx * S::kBytes;
+    const size_t smem = (size_t)kStages * L::Q * row_bytes;
+    const size_t cpr = row_bytes / 16;
+    int cpr_shift = 0;
+    while ((size_t(1) << cpr_shift) < cpr) ++cpr_shift;
+    if (row_bytes % 16 == 0 && (size_t(1) << cpr_shift) == cpr && smem <= kSmemBudget && p.nx >= 32) {
+        const int threads = p.nx >= kRowThreads ? kRowThreads : ((p.nx + 31) / 32) * 32;
+        auto kern = k_step_rows<L, S, FORCE, EF, SR, kStages>;
+        const int blocks = persistent_grid(kern, threads, smem);
+        if (blocks > 0) {
+            const int rows = p.ny * p.nz;
+            kern<<<blocks < rows ? blocks : rows, threads, smem, s>>>(in, out, nbr, Ef, cpr_shift, p);
+            return 1;
+        }
+    }
+    const int bx = p.nx >= kBlock ? kBlock : ((p.nx + 31) / 32) * 32;
+    const dim3 grid((unsigned)(p.ny * p.nz), (unsigned)((p.nx + bx - 1) / bx));
+    k_step<L, S, FORCE, EF, SR><<<grid, bx, 0, s>>>(in, out, nbr, Ef, p);
+    return 1;
+}
+
+template <class L, class S, bool SR>
+int launch_lat(int force, bool efield, const void* fin, void* fout, const uint32_t* nbr, const float* Ef,
+               const KParams& p, cudaStream_t s) {
+    if (force == LBM_FORCE_SHIFT)
+        return efield ? launch_one<L, S, 0, true, SR>(fin, fout, nbr, Ef, p, s)
+                      : launch_one<L, S, 0, false, SR>(fin, fout, nbr, Ef, p, s);
+    return efield ? launch_one<L, S, 1, true, SR>(fin, fout, nbr, Ef, p, s)
+                  : launch_one<L, S, 1, false, SR>(fin, fout, nbr, Ef, p, s);
+}
+
+template <class S, bool HAS_SR>
+int launch_storage(int vel, int force, bool efield, bool sr, const void* fin, void* fout, const uint32_t* nbr,
+                   const float* Ef, const KParams& p, cudaStream_t s) {
+    if (HAS_SR && sr) {
+        if (vel == LBM_D2V9) return launch_lat<LatD2V9, S, HAS_SR>(force, efield, fin, fout, nbr, Ef, p, s);
+        return launch_lat<LatD3V19, S, HAS_SR>(force, efield, fin, fout, nbr, Ef, p, s);
+    }
+    if (vel == LBM_D2V9) return launch_lat<LatD2V9, S, false>(force, efield, fin, fout, nbr, Ef, p, s);
+    return launch_lat<LatD3V19, S, false>(force, efield, fin, fout, nbr, Ef, p, s);
+}
+
+}  // namespace stepk
+}  // namespace lbm

@@ -140,6 +140,10 @@ class LBM:
     def set_params(self, tau: float, E=None, B=None):
         _lib.check(_lib.load().lbm_set_params(self._h, float(tau), _vec3(E), _vec3(B)), self._h, "lbm_set_params")
 
+    def set_rounding(self, stochastic: bool):
+        """Stochastic (default for f16/bf16) or round-to-nearest stores."""
+        _lib.check(_lib.load().lbm_set_rounding(self._h, int(bool(stochastic))), self._h, "lbm_set_rounding")
+
     def init_equilibrium(self, rho=None, u=None):
         _lib.check(_lib.load().lbm_init_equilibrium(self._h, _ptr(rho, np.float32, self.N, "rho"),
                                                     _ptr(u, np.float32, self.D * self.N, "u")), self._h,

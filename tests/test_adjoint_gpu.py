@@ -93,10 +93,12 @@ def test_checkpoint_spacing_does_not_change_the_result():
         assert np.array_equal(dE, outs[0][1])
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
-def test_adjoint_vs_gpu_finite_differences(storage):
-    """Central differences of the GPU forward (window totals) in tau, B_z and
-    the uniform E_x: relative agreement 1e-3."""
+def test_adjoint_vs_gpu_finite_differences():
+    """Central differences of the GPU forward (window totals, FP32 storage) in
+    tau, B_z and the uniform E_x: relative agreement 1e-3.  (Finite differences
+    of a 16-bit-stored forward measure the storage rounding, not the
+    derivative; the FP16 adjoint is compared with the FP32 one instead.)"""
+    storage = "f32"
     from paper_1710_09472_gb300.lbm import LBM
 
     shape = (32, 48)
@@ -190,3 +192,28 @@ def test_autograd_function():
     assert abs(float(B.grad[2]) - res["dL_dB"][2]) <= 1e-9 * abs(res["dL_dB"][2])
     sim.close()
     sim2.close()
+
+
+def test_adjoint_f16_storage_close_to_f32():
+    """The adjoint of an FP16-deviation-stored run agrees with the FP32-stored
+    one to 1e-2 relative (the two forwards differ by the FP16 rounding)."""
+    from paper_1710_09472_gb300.lbm import LBM
+
+    shape = (32, 48)
+    mask, _ = wl.boolean_obstacles(shape, 3.0, 0.75, seed=92)
+    res = {}
+    for storage in ("f32", "f16"):
+        sim = LBM("D2V9", (48, 32), 0.7, E=(2e-3, 5e-4), B=(0, 0, 5e-2), storage=storage, force="term")
+        sim.set_geometry(mask.reshape(-1))
+        sim.init_equilibrium()
+        wj = np.zeros((2, sim.N), dtype=np.float32)
+        wj[0] = 1.0
+        dE = torch.empty(2 * sim.N, dtype=torch.float64, device="cuda")
+        r = sim.adjoint(40, 60, None, wj.reshape(-1), 0, dL_dE=dE)
+        r["dE"] = dE.cpu().numpy()
+        res[storage] = r
+        sim.close()
+    a, b = res["f16"], res["f32"]
+    assert abs(a["dL_dtau"] / b["dL_dtau"] - 1) < 1e-2
+    assert abs(a["dL_dB"][2] / b["dL_dB"][2] - 1) < 1e-2
+    assert rel_linf(a["dE"], b["dE"]) < 1e-2
