@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_seed(const typename S::T* __
                 for (int d = 0; d < L::D; ++d) wj[d] = w_j ? w_j[(int64_t)d * p.N + c.cell] * p.cs_inv : 0.f;
                 // loss of step T: w_rho rho + w_j . j
                 float h[L::Q];
-                dev::pull_raw<L, S>(P, p.N, c, h);
+                dev::pull<L, S>(P, p.N, m, c, h);
                 float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
                 for (int a = 0; a < L::Q; ++a) {
@@ -119,9 +119,10 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(
             for (int a = 0; a < L::Q; ++a) lam_out[(int64_t)a * p.N + c.cell] = 0.f;
         } else {
             // f_t(y): pull of the stored buffer; lamt(y): gather from downstream,
-            // lamt_a(y) = lam_a(y + e_a), or lam_abar(y) when y + e_a is solid (bit a)
+            // lamt_a(y) = lam_a(y + e_a), or lam_abar(y) when y + e_a is solid
+            // (y + e_a = y - e_abar: bit abar of the link mask)
             float h[L::Q], lt[L::Q];
-            dev::pull_raw<L, S>(P, p.N, c, h);
+            dev::pull<L, S>(P, p.N, m, c, h);
 #pragma unroll
             for (int a = 0; a < L::Q; ++a) {
                 h[a] *= p.inv_scale;
@@ -129,8 +130,8 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(
                 if (a == 0)
                     lidx = c.cell;
                 else
-                    lidx = ((m >> a) & 1u) ? (int64_t)opposite(a) * p.N + c.cell
-                                           : (int64_t)a * p.N + dev::shifted<L>(c, a, +1);
+                    lidx = ((m >> opposite(a)) & 1u) ? (int64_t)opposite(a) * p.N + c.cell
+                                                     : (int64_t)a * p.N + dev::shifted<L>(c, a, +1);
                 lt[a] = __ldg(lam_in + lidx);
             }
             // forward quantities

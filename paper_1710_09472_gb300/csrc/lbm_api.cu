@@ -478,7 +478,7 @@ lbm_status lbm_init_equilibrium(lbm_ctx* c, const float* rho, const float* u) {
     }
     KParams p = make_params(c);
     c->cur = 0;
-    lbm_status st = after_launch(c, lbm::launch_init(c->lat.vel, c->storage, c->pop[0], c->mask_dev, rho_d, u_d, p,
+    lbm_status st = after_launch(c, lbm::launch_init(c->lat.vel, c->storage, c->pop[0], c->nbr, rho_d, u_d, p,
                                                       c->stream));
     if (st != LBM_OK) return st;
     c->has_state = true;

@@ -75,15 +75,22 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Pull the stored (scaled) deviations of f(x, t): f_a(x) = P_a(x - e_a).
-// Links into solid cells need no test here: the collision wrote the bounced
-// value into the solid neighbour's slot (see the step kernel).
+// Pull the stored (scaled) deviations of f(x, t) (halfway bounce-back on the
+// read side): f_a(x) = P_a(x - e_a) when x - e_a is fluid, and
+// f_a(x) = P_abar(x) when it is solid (bit a of the fluid cell's link mask).
 template <class L, class S>
-__device__ __forceinline__ void pull_raw(const typename S::T* __restrict__ P, int64_t N, const Cell& c, float* h) {
+__device__ __forceinline__ void pull(const typename S::T* __restrict__ P, int64_t N, uint32_t m, const Cell& c,
+                                     float* h) {
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
-        const uint32_t src = a == 0 ? c.cell : shifted<L>(c, a, -1);
-        h[a] = S::raw(P + (int64_t)a * N + src);
+        int64_t idx;
+        if (a == 0)
+            idx = c.cell;
+        else if ((m >> a) & 1u)
+            idx = (int64_t)opposite(a) * N + c.cell;
+        else
+            idx = (int64_t)a * N + shifted<L>(c, a, -1);
+        h[a] = S::raw(P + idx);
     }
 }
 

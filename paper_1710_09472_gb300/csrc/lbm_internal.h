@@ -14,8 +14,8 @@
 namespace lbm {
 
 constexpr int kMaxQ = 19;
-// Per-cell link mask: bit a set when x + e_a is solid (a >= 1); kSolidBit
-// when x itself is solid.
+// Per-cell link mask: bit a set when x - e_a is solid (a >= 1), i.e. the link
+// that streams into x along e_a bounces back; kSolidBit when x itself is solid.
 constexpr uint32_t kSolidBit = 0x80000000u;
 
 // ---------------------------------------------------------------------------
@@ -125,7 +125,7 @@ struct Launch {
 // Launchers (lbm_kernels.cu).  Each returns the number of kernels launched.
 int launch_build_neighbors(int vel, const uint8_t* mask, uint32_t* nbr, unsigned long long* fluid_count,
                            const KParams& p, cudaStream_t s);
-int launch_init(int vel, int storage, void* pop, const uint8_t* mask, const float* rho, const float* u,
+int launch_init(int vel, int storage, void* pop, const uint32_t* nbr, const float* rho, const float* u,
                 const KParams& p, cudaStream_t s);
 int launch_step(int vel, int storage, int force, bool efield, bool sr, const void* fin, void* fout,
                 const uint32_t* nbr, const float* Ef, const KParams& p, cudaStream_t s);

@@ -5,12 +5,10 @@
 //
 // Layout: populations are structure-of-arrays, P[a * N + cell] with
 // cell = (z * ny + y) * nx + x.  P holds post-collision values ("pull"
-// scheme): the state f(x, t) of the method is f_a(x, t) = P_a(x - e_a).
-// Halfway bounce-back (Sec. 9.3, 9.4) is done on the write side: when x + e_a
-// is solid, the collision at x stores f*_a(x) into slot abar of that solid
-// cell, P_abar(x + e_a), which is exactly where the pull of direction abar at
-// x reads.  Solid cells thus carry only these "ghost" values, every pull is a
-// plain shifted load, and each stored value is read exactly once.
+// scheme): the state f(x, t) of the method is f_a(x, t) = P_a(x - e_a) when
+// x - e_a is fluid.
+// Halfway bounce-back (Sec. 9.3, 9.4) is done on the read side: when x - e_a
+// is solid, f_a(x, t) = P_abar(x), the value x itself sent towards the wall.
 #include <cstdio>
 
 #include "lbm_device.cuh"
@@ -22,8 +20,8 @@ using dev::Cell;
 using dev::kBlock;
 
 // ---------------------------------------------------------------------------
-// Link mask: fluid x: bit a set when x + e_a is solid; solid x: kSolidBit and
-// bit b set when x + e_b is fluid.
+// Link mask: bit a set when x - e_a is solid (the link streaming into x along
+// e_a bounces back); kSolidBit when x is solid.
 // ---------------------------------------------------------------------------
 template <class L>
 __global__ void __launch_bounds__(kBlock) k_neighbors(const uint8_t* __restrict__ mask, uint32_t* __restrict__ nbr,
@@ -33,17 +31,12 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(const uint8_t* __restrict_
     if (dev::cell_of_thread(p, c)) {
         uint32_t m = 0;
         if (mask[c.cell]) {
-            // solid: bit b set when x + e_b is fluid (slot b is a ghost slot
-            // that the fluid cell x + e_b writes)
             m = kSolidBit;
-#pragma unroll
-            for (int b = 1; b < L::Q; ++b)
-                if (!mask[dev::shifted<L>(c, b, +1)]) m |= (1u << b);
         } else {
             fluid = 1;
 #pragma unroll
             for (int a = 1; a < L::Q; ++a)
-                if (mask[dev::shifted<L>(c, a, +1)]) m |= (1u << a);
+                if (mask[dev::shifted<L>(c, a, -1)]) m |= (1u << a);
         }
         nbr[c.cell] = m;
     }
@@ -52,9 +45,11 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(const uint8_t* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// Start state f(x, 0) = f^eq(rho(x), u(x)): slot P_b(y) is pulled by the cell
-// y + e_b, so it holds f^eq_b(y + e_b) when that cell is fluid (for solid y
-// this is the ghost value of a bounced link), and 0 otherwise.
+// Start state f(x, 0) = f^eq(rho(x), u(x)) for the pull with read-side
+// bounce-back: slot P_b(y) of a fluid cell y is pulled by y + e_b when that
+// cell is fluid (value f^eq_b(y + e_b)), and by y itself as its bounced
+// population bbar when y + e_b is solid (value f^eq_bbar(y)); solid cells'
+// slots are never read and hold 0.
 // ---------------------------------------------------------------------------
 template <class L>
 __device__ __forceinline__ float heq_unscaled(const KParams& p, int a, float rho, const float* u) {
@@ -64,22 +59,35 @@ __device__ __forceinline__ float heq_unscaled(const KParams& p, int a, float rho
 }
 
 template <class L, class S>
-__global__ void __launch_bounds__(kBlock) k_init(typename S::T* __restrict__ P, const uint8_t* __restrict__ mask,
+__global__ void __launch_bounds__(kBlock) k_init(typename S::T* __restrict__ P, const uint32_t* __restrict__ nbr,
                                                  const float* __restrict__ rho, const float* __restrict__ u,
                                                  KParams p) {
     Cell c;
     if (!dev::cell_of_thread(p, c)) return;
+    const uint32_t m = nbr[c.cell];
+    auto fields = [&](uint32_t cell, float& r, float* uu) {
+        r = rho ? rho[cell] : p.rho0;
+        uu[0] = u ? u[cell] : 0.f;
+        uu[1] = u ? u[p.N + cell] : 0.f;
+        uu[2] = (u && L::D == 3) ? u[2 * p.N + cell] : 0.f;
+    };
+    float r0, u0[3];
+    fields(c.cell, r0, u0);
 #pragma unroll
     for (int b = 0; b < L::Q; ++b) {
-        const uint32_t dst = b == 0 ? c.cell : dev::shifted<L>(c, b, +1);
         float v = 0.f;
-        if (!mask[dst]) {
-            const float r = rho ? rho[dst] : p.rho0;
-            const float uu[3] = {u ? u[dst] : 0.f, u ? u[p.N + dst] : 0.f,
-                                 (u && L::D == 3) ? u[2 * p.N + dst] : 0.f};
-            v = heq_unscaled<L>(p, b, r, uu) * p.scale;
+        if (!(m & kSolidBit)) {
+            if (b != 0 && ((m >> opposite(b)) & 1u)) {
+                v = heq_unscaled<L>(p, opposite(b), r0, u0);
+            } else if (b == 0) {
+                v = heq_unscaled<L>(p, 0, r0, u0);
+            } else {
+                float r1, u1[3];
+                fields(dev::shifted<L>(c, b, +1), r1, u1);
+                v = heq_unscaled<L>(p, b, r1, u1);
+            }
         }
-        S::put(P + (int64_t)b * p.N + c.cell, v);
+        S::put(P + (int64_t)b * p.N + c.cell, v * p.scale);
     }
 }
 
@@ -88,10 +96,10 @@ __global__ void __launch_bounds__(kBlock) k_init(typename S::T* __restrict__ P, 
 // partials[block] = {sum rho, sum j_x, sum j_y, sum j_z}.
 // ---------------------------------------------------------------------------
 template <class L, class S>
-__device__ __forceinline__ void cell_moments(const typename S::T* __restrict__ P, const KParams& p, const Cell& c,
-                                             float& rho, float* j) {
+__device__ __forceinline__ void cell_moments(const typename S::T* __restrict__ P, const uint32_t* __restrict__ nbr,
+                                             const KParams& p, const Cell& c, float& rho, float* j) {
     float h[L::Q];
-    dev::pull_raw<L, S>(P, p.N, c, h);
+    dev::pull<L, S>(P, p.N, __ldg(nbr + c.cell), c, h);
     float drho = 0.f, jj[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
@@ -119,7 +127,7 @@ __global__ void __launch_bounds__(kBlock) k_moments(const typename S::T* __restr
         const uint32_t m = nbr[c.cell];
         float r = 0.f, j[3] = {0.f, 0.f, 0.f};
         if (!(m & kSolidBit)) {
-            cell_moments<L, S>(P, p, c, r, j);
+            cell_moments<L, S>(P, nbr, p, c, r, j);
             acc[0] = (double)r;
             acc[1] = (double)j[0];
             acc[2] = (double)j[1];
@@ -200,7 +208,7 @@ __global__ void __launch_bounds__(kBlock) k_populations(const typename S::T* __r
         return;
     }
     float h[L::Q];
-    dev::pull_raw<L, S>(P, p.N, c, h);
+    dev::pull<L, S>(P, p.N, m, c, h);
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
         const float d = h[a] * p.inv_scale;
@@ -246,14 +254,14 @@ int launch_build_neighbors(int vel, const uint8_t* mask, uint32_t* nbr, unsigned
     });
 }
 
-int launch_init(int vel, int storage, void* pop, const uint8_t* mask, const float* rho, const float* u,
+int launch_init(int vel, int storage, void* pop, const uint32_t* nbr, const float* rho, const float* u,
                 const KParams& p, cudaStream_t s) {
     Launch l = grid_of(p);
     return dispatch_lattice(vel, [&](auto lat) {
         using L = decltype(lat);
         return dispatch_storage(storage, [&](auto st) {
             using S = decltype(st);
-            k_init<L, S><<<l.grid, l.block, 0, s>>>((typename S::T*)pop, mask, rho, u, p);
+            k_init<L, S><<<l.grid, l.block, 0, s>>>((typename S::T*)pop, nbr, rho, u, p);
             return 1;
         });
     });

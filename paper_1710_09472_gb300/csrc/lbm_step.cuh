@@ -248,47 +248,17 @@ __device__ __forceinline__ void store_val(typename S::T* ptr, float v, uint32_t 
         S::put(ptr, v);
 }
 
-// Store one fluid cell's post-collision values.  Every own slot is written
-// (0 on a bounced link), and a link into a solid cell also writes the ghost
-// slot P_abar(x + e_a), so that together with the solid cells' own writes
-// every slot is written once per step (whole sectors, no partial-sector
-// merges in L2).
-template <class L, class S, bool SR>
-__device__ __forceinline__ void store_fluid(typename S::T* __restrict__ Pout, uint32_t m, const Cell& c,
-                                            const float* out, const KParams& p) {
-    // random stream: one hash of (cell, step) per cell, then a 32-bit LCG
-    // (Numerical Recipes constants) whose upper 16 bits feed each store
-    uint32_t x = 0;
-    if (SR) x = hash32(c.cell ^ hash32(p.step * 0x9E3779B9u + p.seed));
-    auto next = [&]() {
+// Random stream for stochastic rounding: one hash of (cell, step) per cell,
+// then a 32-bit LCG (Numerical Recipes constants) whose upper 16 bits feed
+// each store.  A replayed step reproduces its stores bit for bit.
+struct Rng {
+    uint32_t x;
+    __device__ __forceinline__ Rng(uint32_t cell, const KParams& p) : x(hash32(cell ^ hash32(p.step * 0x9E3779B9u + p.seed))) {}
+    __device__ __forceinline__ uint32_t next() {
         x = x * 1664525u + 1013904223u;
         return x >> 16;
-    };
-    store_val<S, SR>(Pout + c.cell, out[0], SR ? next() : 0u);
-#pragma unroll
-    for (int a = 1; a < L::Q; ++a) {
-        const uint32_t rnd = SR ? next() : 0u;
-        const bool bounce = (m >> a) & 1u;
-        typename S::T* own = Pout + (int64_t)a * p.N + c.cell;
-        if (bounce) {
-            S::put(own, 0.f);
-            store_val<S, SR>(Pout + (int64_t)opposite(a) * p.N + dev::shifted<L>(c, a, +1), out[a], rnd);
-        } else {
-            store_val<S, SR>(own, out[a], rnd);
-        }
     }
-}
-
-// A solid cell writes 0 into every slot that is not a ghost slot (bit b of its
-// mask: x + e_b is fluid, so that fluid cell writes slot b).
-template <class L, class S>
-__device__ __forceinline__ void store_solid(typename S::T* __restrict__ Pout, uint32_t m, const Cell& c,
-                                            const KParams& p) {
-    S::put(Pout + c.cell, 0.f);
-#pragma unroll
-    for (int b = 1; b < L::Q; ++b)
-        if (!((m >> b) & 1u)) S::put(Pout + (int64_t)b * p.N + c.cell, 0.f);
-}
+};
 
 template <class L>
 __device__ __forceinline__ void load_E(const float* __restrict__ Ef, bool ef, const KParams& p, uint32_t cell,
@@ -304,7 +274,17 @@ __device__ __forceinline__ void load_E(const float* __restrict__ Ef, bool ef, co
     }
 }
 
-// General step kernel: one thread per cell, pulls straight from global memory.
+template <class L, class S, int FORCE>
+__device__ __forceinline__ void collide_any(const float* h, const float* E, const KParams& p, float* out) {
+    if (S::kBytes == 4)
+        collide_acc<L, FORCE>(h, E, p, out);
+    else
+        collide<L, FORCE>(h, E, p, out);
+}
+
+// General step kernel: one thread per cell, pulls straight from global memory
+// (bounce-back on the read side) and writes every own slot; solid cells write
+// zeros so that every sector is written whole.
 template <class L, class S, int FORCE, bool EF, bool SR>
 __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict__ Pin, typename S::T* __restrict__ Pout,
                                                  const uint32_t* __restrict__ nbr, const float* __restrict__ Ef,
@@ -313,30 +293,35 @@ __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict
     if (!dev::cell_of_thread(p, c)) return;
     const uint32_t m = __ldg(nbr + c.cell);
     if (m & kSolidBit) {
-        store_solid<L, S>(Pout, m, c, p);
+#pragma unroll
+        for (int a = 0; a < L::Q; ++a) S::put(Pout + (int64_t)a * p.N + c.cell, 0.f);
         return;
     }
     float h[L::Q];
-    dev::pull_raw<L, S>(Pin, p.N, c, h);
+    dev::pull<L, S>(Pin, p.N, m, c, h);
     float E[3];
     load_E<L>(Ef, EF, p, c.cell, E);
     float out[L::Q];
-    if (S::kBytes == 4)
-        collide_acc<L, FORCE>(h, E, p, out);
-    else
-        collide<L, FORCE>(h, E, p, out);
-    store_fluid<L, S, SR>(Pout, m, c, out, p);
+    collide_any<L, S, FORCE>(h, E, p, out);
+    Rng rng(c.cell, p);
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) store_val<S, SR>(Pout + (int64_t)a * p.N + c.cell, out[a], SR ? rng.next() : 0u);
 }
 
 // ---------------------------------------------------------------------------
 // Row-staged step kernel (used when a whole x-row of one direction is a
-// multiple of 16 bytes and fits the shared-memory ring).  A persistent block
-// walks rows r = blockIdx.x, blockIdx.x + gridDim.x, ...; for each row the 19
-// (or 9) source rows P_a(y - e_ay, z - e_az, :) are copied whole into shared
-// memory with 16-byte asynchronous copies (cp.async.cg, L1 bypass), STAGES - 1
-// rows ahead of the row being computed.  The x-shift (with its periodic wrap)
-// is then a shared-memory index, global reads are aligned full rows, and each
-// block keeps (STAGES - 1) x Q x nx x b bytes in flight.
+// power-of-two number of 16-byte chunks and the rings fit shared memory).  A
+// persistent block walks rows r = blockIdx.x, blockIdx.x + gridDim.x, ...:
+//  - the Q source rows P_a(y - e_ay, z - e_az, :) of the row are copied whole
+//    into a ring of STAGES row sets with 16-byte asynchronous copies
+//    (cp.async.cg, L1 bypass), STAGES - 1 rows ahead of the row being computed;
+//  - the row's fluid cells are compacted into a list, so the collision runs on
+//    full warps (solid cells do no work);
+//  - f_a(x) is read from the ring at x - e_ax (periodic wrap in x is a
+//    shared-memory index); a bounced link reads P_abar(x) from global memory;
+//  - results go into a shared-memory output row set (zero for solid cells),
+//    which is then written with 16-byte vector stores: whole sectors, fully
+//    coalesced, no scattered stores.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -369,9 +354,9 @@ template <class L, class S>
 __device__ __forceinline__ void stage_row(typename S::T* __restrict__ buf, const typename S::T* __restrict__ Pin,
                                           int row, int cpr_shift, const KParams& p) {
     constexpr int kElem16 = 16 / S::kBytes;
-    const unsigned long long kPy = packed_y<L>(), kPz = packed_z<L>();
     static_assert(L::Q <= 32, "direction codes must fit 64 bits");
-    const int cpr = 1 << cpr_shift;  // 16-byte chunks per row (a power of two)
+    const unsigned long long kPy = packed_y<L>(), kPz = packed_z<L>();
+    const int cpr = 1 << cpr_shift;  // 16-byte chunks per row
     const int y = row % p.ny, z = row / p.ny;
     const int total = L::Q << cpr_shift;
     for (int k = threadIdx.x; k < total; k += blockDim.x) {
@@ -391,12 +376,23 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
                                                    typename S::T* __restrict__ Pout, const uint32_t* __restrict__ nbr,
                                                    const float* __restrict__ Ef, int cpr_shift, KParams p) {
     using T = typename S::T;
+    constexpr int kElem16 = 16 / S::kBytes;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = p.nx;
+    const int stage_elems = L::Q * nx;
     T* ring = reinterpret_cast<T*>(smem_raw);
-    const int stage_elems = L::Q * p.nx;
+    T* outrow = ring + STAGES * stage_elems;
+    uint32_t* flist = reinterpret_cast<uint32_t*>(outrow + stage_elems);  // x of the row's fluid cells
+    uint32_t* fmask = flist + nx;                                        // their link masks
+    __shared__ int fcount;
     const int R = p.ny * p.nz;
     const int G = gridDim.x;
-    // prologue: the first STAGES - 1 rows of this block
+    const int cpr = 1 << cpr_shift;
+    const int chunks = L::Q << cpr_shift;
+    for (int k = threadIdx.x; k < chunks; k += blockDim.x)
+        reinterpret_cast<uint4*>(outrow)[k] = make_uint4(0u, 0u, 0u, 0u);
+    if (threadIdx.x == 0) fcount = 0;
+    __syncthreads();
 #pragma unroll
     for (int k = 0; k < STAGES - 1; ++k) {
         const int rk = blockIdx.x + k * G;
@@ -408,50 +404,72 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
         const int rn = r + (STAGES - 1) * G;
         if (rn < R) stage_row<L, S>(ring + ((it + STAGES - 1) % STAGES) * stage_elems, Pin, rn, cpr_shift, p);
         cp_async_commit();
+        // compact the row's fluid cells (warp ballots, one shared atomic per warp)
+        const uint32_t rowbase = (uint32_t)r * (uint32_t)nx;
+        for (int x0 = 0; x0 < nx; x0 += blockDim.x) {
+            const int x = x0 + threadIdx.x;
+            uint32_t m = kSolidBit;
+            if (x < nx) m = __ldg(nbr + rowbase + x);
+            const bool fluid = !(m & kSolidBit);
+            const unsigned ball = __ballot_sync(0xffffffffu, fluid);
+            int base = 0;
+            if ((threadIdx.x & 31) == 0 && ball) base = atomicAdd(&fcount, __popc(ball));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (fluid) {
+                const int idx = base + __popc(ball & ((1u << (threadIdx.x & 31)) - 1u));
+                flist[idx] = (uint32_t)x;
+                fmask[idx] = m;
+            }
+        }
         cp_async_wait<STAGES - 1>();
-        __syncthreads();
+        __syncthreads();  // ring row ready, list complete
         const T* buf = ring + (it % STAGES) * stage_elems;
+        const int nf = fcount;
         Cell c;
         c.y = r % p.ny;
         c.z = r / p.ny;
-        const int ys[3] = {c.y == 0 ? p.ny - 1 : c.y - 1, c.y, c.y == p.ny - 1 ? 0 : c.y + 1};
-        const int zs[3] = {c.z == 0 ? p.nz - 1 : c.z - 1, c.z, c.z == p.nz - 1 ? 0 : c.z + 1};
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-                c.r[i][k] = ((uint32_t)zs[k] * (uint32_t)p.ny + (uint32_t)ys[i]) * (uint32_t)p.nx;
-        for (int x = threadIdx.x; x < p.nx; x += blockDim.x) {
+        for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+            const int x = (int)flist[i];
+            const uint32_t m = fmask[i];
             c.x = x;
-            c.xm = x == 0 ? p.nx - 1 : x - 1;
-            c.xp = x == p.nx - 1 ? 0 : x + 1;
-            c.cell = (uint32_t)r * (uint32_t)p.nx + (uint32_t)x;
-            const uint32_t m = __ldg(nbr + c.cell);
-            if (m & kSolidBit) {
-                store_solid<L, S>(Pout, m, c, p);
-                continue;
-            }
+            c.cell = rowbase + (uint32_t)x;
+            const int xm = x == 0 ? nx - 1 : x - 1;
+            const int xp = x == nx - 1 ? 0 : x + 1;
             float h[L::Q];
 #pragma unroll
             for (int a = 0; a < L::Q; ++a) {
                 const int ex = L::c(a, 0);
-                const int xs = ex > 0 ? c.xm : (ex < 0 ? c.xp : x);
-                h[a] = S::cvt(buf[a * p.nx + xs]);
+                const int xs = ex > 0 ? xm : (ex < 0 ? xp : x);
+                h[a] = S::cvt(buf[a * nx + xs]);
+            }
+            if (m != 0u) {  // bounced links: f_a(x) = P_abar(x)
+#pragma unroll
+                for (int a = 1; a < L::Q; ++a)
+                    if ((m >> a) & 1u) h[a] = S::raw(Pin + (int64_t)opposite(a) * p.N + c.cell);
             }
             float E[3];
             load_E<L>(Ef, EF, p, c.cell, E);
             float out[L::Q];
-            if (S::kBytes == 4)
-                collide_acc<L, FORCE>(h, E, p, out);
-            else
-                collide<L, FORCE>(h, E, p, out);
-            store_fluid<L, S, SR>(Pout, m, c, out, p);
+            collide_any<L, S, FORCE>(h, E, p, out);
+            Rng rng(c.cell, p);
+#pragma unroll
+            for (int a = 0; a < L::Q; ++a) store_val<S, SR>(outrow + a * nx + x, out[a], SR ? rng.next() : 0u);
         }
-        __syncthreads();
+        __syncthreads();  // output rows complete
+        // write the output rows with 16-byte vector stores; each chunk is
+        // zeroed again by the thread that read it (solid cells stay 0)
+        for (int k = threadIdx.x; k < chunks; k += blockDim.x) {
+            const int a = k >> cpr_shift, off = k & (cpr - 1);
+            uint4* src = reinterpret_cast<uint4*>(outrow + a * nx) + off;
+            T* dst = Pout + (int64_t)a * p.N + rowbase + (int64_t)off * kElem16;
+            *reinterpret_cast<uint4*>(dst) = *src;
+            *src = make_uint4(0u, 0u, 0u, 0u);
+        }
+        if (threadIdx.x == 0) fcount = 0;
+        __syncthreads();  // list and counter free for the next row
     }
     cp_async_wait<0>();
 }
-
 
 // ---------------------------------------------------------------------------
 // Launch policy.  The row-staged kernel runs when a row of one direction is a
@@ -492,7 +510,7 @@ int launch_one(const void* fin, void* fout, const uint32_t* nbr, const float* Ef
     const T* in = (const T*)fin;
     T* out = (T*)fout;
     const size_t row_bytes = (size_t)p.nx * S::kBytes;
-    const size_t smem = (size_t)kStages * L::Q * row_bytes;
+    const size_t smem = (size_t)(kStages + 1) * L::Q * row_bytes + 8 * (size_t)p.nx;
     const size_t cpr = row_bytes / 16;
     int cpr_shift = 0;
     while ((size_t(1) << cpr_shift) < cpr) ++cpr_shift;
