@@ -33,14 +33,14 @@ WORKLOAD_NAME = ("porous-3d-256^3 D3V19 FD(theta=1/270,mu=1) spheres r=6 porosit
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by storage, with the
 # hash of the kernel source it was taken on; reported as null once the
 # source has changed.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"f16": (1478718976, "94ce989d984b2b3a")}  # profiles/step_d3v19_f16_porous256.md
 
 FALLBACK_HBM_GBS = 6800.0
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("lbm_kernels.cu", "lbm_internal.h"):
+    for f in ("lbm_step.cuh", "lbm_device.cuh", "lbm_internal.h", "lbm_step_f16.cu"):
         with open(os.path.join(ROOT, "paper_1710_09472_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
