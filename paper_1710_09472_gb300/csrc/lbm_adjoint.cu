@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_seed(const typename S::T* __
                 for (int d = 0; d < L::D; ++d) wj[d] = w_j ? w_j[(int64_t)d * p.N + c.cell] * p.cs_inv : 0.f;
                 // loss of step T: w_rho rho + w_j . j
                 float h[L::Q];
-                dev::pull<L, S>(P, p.N, m, c, h);
+                dev::pull<L, S>(P, p, m, c, h);
                 float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
                 for (int a = 0; a < L::Q; ++a) {
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(
             // lamt_a(y) = lam_a(y + e_a), or lam_abar(y) when y + e_a is solid
             // (y + e_a = y - e_abar: bit abar of the link mask)
             float h[L::Q], lt[L::Q];
-            dev::pull<L, S>(P, p.N, m, c, h);
+            dev::pull<L, S>(P, p, m, c, h);
 #pragma unroll
             for (int a = 0; a < L::Q; ++a) {
                 h[a] *= p.inv_scale;

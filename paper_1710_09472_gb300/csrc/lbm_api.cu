@@ -174,6 +174,10 @@ lbm::KParams lbm::make_params(const lbm_ctx* c) {
     }
     p.scale = (float)c->scale;
     p.inv_scale = (float)(1.0 / c->scale);
+    p.gofs = c->gofs;
+    p.lbase = c->lbase;
+    p.rowG = c->rowG;
+    p.max_row_links = c->max_row_links;
     return p;
 }
 
@@ -220,6 +224,45 @@ struct StateHeader {
     uint32_t crc;
     uint32_t pad;
 };
+
+// Link-buffer layout for the current link masks, then state buffers sized
+// for populations + links (contents undefined until lbm_init_equilibrium).
+lbm_status build_links_and_state(lbm_ctx* c) {
+    KParams p = make_params(c);
+    size_t temp_bytes = 0;
+    if (lbm::launch_build_links(c->lat.vel, c->nbr, c->lbase, c->rowG, nullptr, &temp_bytes, p, c->stream) != 0)
+        return fail(c, LBM_ERR_CUDA, "link layout: scan size query failed");
+    void* temp = nullptr;
+    LBM_CUDA(c, cudaMalloc(&temp, temp_bytes > 0 ? temp_bytes : 16));
+    c->launches += lbm::launch_build_links(c->lat.vel, c->nbr, c->lbase, c->rowG, temp, &temp_bytes, p, c->stream);
+    lbm_status st = cuda_check(c, cudaGetLastError(), "link layout kernels");
+    const int64_t R = c->ny * c->nz;
+    std::vector<uint32_t> rowG((size_t)R + 1);
+    if (st == LBM_OK)
+        st = cuda_check(c, cudaMemcpyAsync(rowG.data(), c->rowG, sizeof(uint32_t) * (R + 1), cudaMemcpyDeviceToHost,
+                                           c->stream), "copy row link offsets");
+    if (st == LBM_OK) st = cuda_check(c, cudaStreamSynchronize(c->stream), "link layout");
+    cudaFree(temp);
+    if (st != LBM_OK) return st;
+    c->n_links = rowG[R];
+    int mx = 0;
+    for (int64_t r = 0; r < R; ++r) mx = std::max(mx, (int)(rowG[r + 1] - rowG[r]));
+    c->max_row_links = mx;
+    const size_t eb = pop_elem_bytes(c->storage);
+    const size_t pbytes = (size_t)c->Q * (size_t)c->N * eb;
+    c->gofs = (pbytes + 255) & ~(size_t)255;
+    const size_t need = c->gofs + ((((size_t)c->n_links * eb) + 16 + 255) & ~(size_t)255);
+    if (need != c->state_bytes) {
+        cudaFree(c->pop[0]);
+        cudaFree(c->pop[1]);
+        c->pop[0] = c->pop[1] = nullptr;
+        c->state_bytes = 0;
+        LBM_CUDA(c, cudaMalloc(&c->pop[0], need));
+        LBM_CUDA(c, cudaMalloc(&c->pop[1], need));
+        c->state_bytes = need;
+    }
+    return LBM_OK;
+}
 
 }  // namespace
 
@@ -336,10 +379,13 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_lattice* lat, const int64_t dims[
     const size_t pop_bytes = (size_t)c->Q * (size_t)c->N * pop_elem_bytes(storage);
     KParams p = make_params(c);
     c->partials_cap = lbm::moments_partial_count(p);
-    if ((st = cuda_check(c, cudaMalloc(&c->pop[0], pop_bytes), "cudaMalloc populations")) != LBM_OK ||
-        (st = cuda_check(c, cudaMalloc(&c->pop[1], pop_bytes), "cudaMalloc populations")) != LBM_OK ||
-        (st = cuda_check(c, cudaMalloc((void**)&c->nbr, sizeof(uint32_t) * c->N), "cudaMalloc neighbours")) !=
+    (void)pop_bytes;
+    if ((st = cuda_check(c, cudaMalloc((void**)&c->nbr, sizeof(uint32_t) * c->N), "cudaMalloc neighbours")) !=
             LBM_OK ||
+        (st = cuda_check(c, cudaMalloc((void**)&c->lbase, sizeof(uint32_t) * c->N), "cudaMalloc link bases")) !=
+            LBM_OK ||
+        (st = cuda_check(c, cudaMalloc((void**)&c->rowG, sizeof(uint32_t) * (c->ny * c->nz + 1)),
+                         "cudaMalloc row links")) != LBM_OK ||
         (st = cuda_check(c, cudaMalloc((void**)&c->mask_dev, c->N), "cudaMalloc mask")) != LBM_OK ||
         (st = cuda_check(c, cudaMalloc((void**)&c->partials, sizeof(double) * 4 * c->partials_cap),
                          "cudaMalloc partials")) != LBM_OK ||
@@ -359,7 +405,8 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_lattice* lat, const int64_t dims[
     }
     cudaMemsetAsync(c->count_dev, 0, sizeof(unsigned long long), c->stream);
     c->launches += lbm::launch_build_neighbors(c->lat.vel, c->mask_dev, c->nbr, c->count_dev, p, c->stream);
-    if ((st = cuda_check(c, cudaGetLastError(), "neighbour kernel")) != LBM_OK) {
+    if ((st = cuda_check(c, cudaGetLastError(), "neighbour kernel")) != LBM_OK ||
+        (st = build_links_and_state(c)) != LBM_OK) {
         lbm_destroy(c);
         return st;
     }
@@ -374,6 +421,8 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->pop[0]);
     cudaFree(c->pop[1]);
     cudaFree(c->nbr);
+    cudaFree(c->lbase);
+    cudaFree(c->rowG);
     cudaFree(c->mask_dev);
     cudaFree(c->Efield);
     cudaFree(c->partials);
@@ -419,7 +468,8 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* mask) {
                                                                  c->stream));
     c->geometry_counted = false;
     c->has_state = false;
-    return st;
+    if (st != LBM_OK) return st;
+    return build_links_and_state(c);
 }
 
 lbm_status lbm_set_E_field(lbm_ctx* c, const float* E) {
@@ -566,7 +616,7 @@ lbm_status lbm_get_populations(lbm_ctx* c, float* f, int deviation) {
 
 lbm_status lbm_save_state(lbm_ctx* c, void* host_buf, size_t cap, size_t* used) {
     if (!c || !used) return LBM_ERR_INVALID_ARG;
-    const size_t payload = (size_t)c->Q * (size_t)c->N * pop_elem_bytes(c->storage);
+    const size_t payload = c->state_bytes;
     const size_t total = sizeof(StateHeader) + payload;
     *used = total;
     if (!host_buf) return LBM_OK;
@@ -595,7 +645,7 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t len) {
     if (len < sizeof(StateHeader)) return fail(c, LBM_ERR_INVALID_ARG, "lbm_load_state: short buffer");
     StateHeader h;
     std::memcpy(&h, host_buf, sizeof h);
-    const size_t payload = (size_t)c->Q * (size_t)c->N * pop_elem_bytes(c->storage);
+    const size_t payload = c->state_bytes;
     if (std::memcmp(h.magic, "LBMSTAT", 8) != 0 || h.vel != c->lat.vel || h.storage != c->storage || h.nx != c->nx ||
         h.ny != c->ny || h.nz != c->nz || h.payload != payload)
         return fail(c, LBM_ERR_INVALID_ARG, "lbm_load_state: header does not match this context");
@@ -663,7 +713,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
     }
     if (K > T) K = T;
     const int64_t nseg = (T + K - 1) / K;
-    const size_t pop_bytes = (size_t)c->Q * (size_t)c->N * pop_elem_bytes(c->storage);
+    const size_t pop_bytes = c->state_bytes;  // populations + link buffer
     const size_t lam_bytes = sizeof(float) * (size_t)c->Q * (size_t)c->N;
     KParams p = make_params(c);
     const int64_t nslot = lbm::adjoint_slot_count(p);

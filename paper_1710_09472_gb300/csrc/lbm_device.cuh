@@ -75,22 +75,24 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Pull the stored (scaled) deviations of f(x, t) (halfway bounce-back on the
-// read side): f_a(x) = P_a(x - e_a) when x - e_a is fluid, and
-// f_a(x) = P_abar(x) when it is solid (bit a of the fluid cell's link mask).
+// Pull the stored (scaled) deviations of f(x, t) from a state (populations P
+// followed by the link buffer G): f_a(x) = P_a(x - e_a) when x - e_a is fluid;
+// when it is solid (bit a of the link mask) the halfway bounce-back value
+// f_a(x) = f*_abar(x), which the collision at x stored in the link slot of its
+// outgoing direction abar.
 template <class L, class S>
-__device__ __forceinline__ void pull(const typename S::T* __restrict__ P, int64_t N, uint32_t m, const Cell& c,
+__device__ __forceinline__ void pull(const typename S::T* __restrict__ P, const KParams& p, uint32_t m, const Cell& c,
                                      float* h) {
+    const typename S::T* __restrict__ G =
+        reinterpret_cast<const typename S::T*>(reinterpret_cast<const char*>(P) + p.gofs);
+    const uint32_t o = outgoing<L::Q>(m);
+    const uint32_t base = m ? __ldg(p.lbase + c.cell) : 0u;
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
-        int64_t idx;
-        if (a == 0)
-            idx = c.cell;
-        else if ((m >> a) & 1u)
-            idx = (int64_t)opposite(a) * N + c.cell;
+        if (a != 0 && ((m >> a) & 1u))
+            h[a] = S::raw(G + link_slot(base, o, opposite(a)));
         else
-            idx = (int64_t)a * N + shifted<L>(c, a, -1);
-        h[a] = S::raw(P + idx);
+            h[a] = S::raw(P + (int64_t)a * p.N + (a == 0 ? c.cell : shifted<L>(c, a, -1)));
     }
 }
 

@@ -18,6 +18,30 @@ constexpr int kMaxQ = 19;
 // that streams into x along e_a bounces back; kSolidBit when x itself is solid.
 constexpr uint32_t kSolidBit = 0x80000000u;
 
+// Outgoing-link mask from the incoming one: bit b set when x + e_b is solid,
+// i.e. bit bbar of the incoming mask (opposite pairs are (a, a + 1), a odd).
+template <int Q>
+__host__ __device__ constexpr uint32_t odd_bits() {
+    uint32_t v = 0;
+    for (int b = 1; b < Q; b += 2) v |= 1u << b;
+    return v;
+}
+template <int Q>
+__host__ __device__ __forceinline__ uint32_t outgoing(uint32_t m) {
+    constexpr uint32_t kOdd = odd_bits<Q>();
+    constexpr uint32_t kEven = kOdd << 1;
+    return ((m >> 1) & kOdd) | ((m << 1) & kEven);
+}
+// Link slot of outgoing direction b of a cell: base + number of its outgoing
+// links below b.
+__host__ __device__ __forceinline__ uint32_t link_slot(uint32_t base, uint32_t o, int b) {
+#ifdef __CUDA_ARCH__
+    return base + (uint32_t)__popc(o & ((1u << b) - 1u));
+#else
+    return base + (uint32_t)__builtin_popcount(o & ((1u << b) - 1u));
+#endif
+}
+
 // ---------------------------------------------------------------------------
 // Lattices (Sec. 8.2 and Table lattices-tab).  Order: rest vector, then
 // opposite pairs (a odd, a + 1 = -e_a), as documented in lbm.h.
@@ -116,6 +140,13 @@ struct KParams {
     float scale, inv_scale;
     uint32_t step;  // global step index of this launch (stochastic rounding stream)
     uint32_t seed;
+    // Bounce-back link buffer G (see lbm_kernels.cu): byte offset of G inside
+    // a state buffer, per-cell first link slot, per-row first link slot
+    // (ny * nz + 1 entries) and the largest number of links in one row.
+    uint64_t gofs;
+    const uint32_t* lbase;
+    const uint32_t* rowG;
+    int max_row_links;
 };
 
 struct Launch {
@@ -125,6 +156,10 @@ struct Launch {
 // Launchers (lbm_kernels.cu).  Each returns the number of kernels launched.
 int launch_build_neighbors(int vel, const uint8_t* mask, uint32_t* nbr, unsigned long long* fluid_count,
                            const KParams& p, cudaStream_t s);
+// Link buffer layout: lbase[cell] (exclusive prefix of outgoing-link counts),
+// rowG[0..ny*nz]; needs a temporary of *temp_bytes (queried with temp == NULL).
+int launch_build_links(int vel, const uint32_t* nbr, uint32_t* lbase, uint32_t* rowG, void* temp,
+                       size_t* temp_bytes, const KParams& p, cudaStream_t s);
 int launch_init(int vel, int storage, void* pop, const uint32_t* nbr, const float* rho, const float* u,
                 const KParams& p, cudaStream_t s);
 int launch_step(int vel, int storage, int force, bool efield, bool sr, const void* fin, void* fout,
@@ -183,6 +218,12 @@ struct lbm_ctx {
     void* pop[2] = {nullptr, nullptr};
     int cur = 0;
     uint32_t* nbr = nullptr;
+    uint32_t* lbase = nullptr;     // per-cell first slot in the link buffer
+    uint32_t* rowG = nullptr;      // per-row first slot (ny * nz + 1)
+    int64_t n_links = 0;           // outgoing links into solid cells
+    int max_row_links = 0;
+    size_t state_bytes = 0;        // populations + link buffer
+    size_t gofs = 0;               // byte offset of the link buffer in a state
     uint8_t* mask_dev = nullptr;
     float* Efield = nullptr;
     bool use_Efield = false;

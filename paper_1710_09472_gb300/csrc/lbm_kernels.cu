@@ -7,9 +7,15 @@
 // cell = (z * ny + y) * nx + x.  P holds post-collision values ("pull"
 // scheme): the state f(x, t) of the method is f_a(x, t) = P_a(x - e_a) when
 // x - e_a is fluid.
-// Halfway bounce-back (Sec. 9.3, 9.4) is done on the read side: when x - e_a
-// is solid, f_a(x, t) = P_abar(x), the value x itself sent towards the wall.
+// Halfway bounce-back (Sec. 9.3, 9.4) uses a link buffer G stored after P in
+// the same state buffer: every link from a fluid cell x into a solid cell
+// (x + e_b solid) owns one slot, numbered in cell order (lbase[x] + rank of b
+// among x's outgoing links), so the links of one row form a contiguous range
+// rowG[r] .. rowG[r+1].  The collision stores f*_b(x) there, and the next
+// step reads it back as f_bbar(x).
 #include <cstdio>
+
+#include <cub/device/device_scan.cuh>
 
 #include "lbm_device.cuh"
 
@@ -65,6 +71,7 @@ __global__ void __launch_bounds__(kBlock) k_init(typename S::T* __restrict__ P, 
     Cell c;
     if (!dev::cell_of_thread(p, c)) return;
     const uint32_t m = nbr[c.cell];
+    typename S::T* G = reinterpret_cast<typename S::T*>(reinterpret_cast<char*>(P) + p.gofs);
     auto fields = [&](uint32_t cell, float& r, float* uu) {
         r = rho ? rho[cell] : p.rho0;
         uu[0] = u ? u[cell] : 0.f;
@@ -73,21 +80,47 @@ __global__ void __launch_bounds__(kBlock) k_init(typename S::T* __restrict__ P, 
     };
     float r0, u0[3];
     fields(c.cell, r0, u0);
+    const bool fluid = !(m & kSolidBit);
+    const uint32_t o = fluid ? outgoing<L::Q>(m) : 0u;
+    const uint32_t base = (fluid && o) ? p.lbase[c.cell] : 0u;
 #pragma unroll
     for (int b = 0; b < L::Q; ++b) {
         float v = 0.f;
-        if (!(m & kSolidBit)) {
-            if (b != 0 && ((m >> opposite(b)) & 1u)) {
-                v = heq_unscaled<L>(p, opposite(b), r0, u0);
-            } else if (b == 0) {
-                v = heq_unscaled<L>(p, 0, r0, u0);
+        if (fluid) {
+            if (b != 0 && ((o >> b) & 1u)) {
+                // link into a solid cell: next pull of bbar at this cell reads f^eq_bbar here
+                S::put(G + link_slot(base, o, b), heq_unscaled<L>(p, opposite(b), r0, u0) * p.scale);
             } else {
-                float r1, u1[3];
-                fields(dev::shifted<L>(c, b, +1), r1, u1);
+                float r1 = r0, u1[3] = {u0[0], u0[1], u0[2]};
+                if (b != 0) fields(dev::shifted<L>(c, b, +1), r1, u1);
                 v = heq_unscaled<L>(p, b, r1, u1);
             }
         }
         S::put(P + (int64_t)b * p.N + c.cell, v * p.scale);
+    }
+}
+
+// Link layout: count outgoing links per fluid cell, exclusive scan, row starts.
+template <class L>
+__global__ void __launch_bounds__(kBlock) k_link_counts(const uint32_t* __restrict__ nbr, uint32_t* __restrict__ cnt,
+                                                        KParams p) {
+    Cell c;
+    if (!dev::cell_of_thread(p, c)) return;
+    const uint32_t m = nbr[c.cell];
+    cnt[c.cell] = (m & kSolidBit) ? 0u : (uint32_t)__popc(outgoing<L::Q>(m));
+}
+
+template <class L>
+__global__ void k_row_starts(const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ lbase,
+                             uint32_t* __restrict__ rowG, KParams p) {
+    const int64_t R = (int64_t)p.ny * p.nz;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= R; r += (int64_t)gridDim.x * blockDim.x) {
+        if (r < R) {
+            rowG[r] = lbase[r * p.nx];
+        } else {
+            const uint32_t m = nbr[p.N - 1];
+            rowG[R] = lbase[p.N - 1] + ((m & kSolidBit) ? 0u : (uint32_t)__popc(outgoing<L::Q>(m)));
+        }
     }
 }
 
@@ -99,7 +132,7 @@ template <class L, class S>
 __device__ __forceinline__ void cell_moments(const typename S::T* __restrict__ P, const uint32_t* __restrict__ nbr,
                                              const KParams& p, const Cell& c, float& rho, float* j) {
     float h[L::Q];
-    dev::pull<L, S>(P, p.N, __ldg(nbr + c.cell), c, h);
+    dev::pull<L, S>(P, p, __ldg(nbr + c.cell), c, h);
     float drho = 0.f, jj[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
@@ -208,7 +241,7 @@ __global__ void __launch_bounds__(kBlock) k_populations(const typename S::T* __r
         return;
     }
     float h[L::Q];
-    dev::pull<L, S>(P, p.N, m, c, h);
+    dev::pull<L, S>(P, p, m, c, h);
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
         const float d = h[a] * p.inv_scale;
@@ -252,6 +285,30 @@ int launch_build_neighbors(int vel, const uint8_t* mask, uint32_t* nbr, unsigned
         k_neighbors<L><<<l.grid, l.block, 0, s>>>(mask, nbr, fluid_count, p);
         return 1;
     });
+}
+
+int launch_build_links(int vel, const uint32_t* nbr, uint32_t* lbase, uint32_t* rowG, void* temp,
+                       size_t* temp_bytes, const KParams& p, cudaStream_t s) {
+    const int n = (int)p.N;
+    if (!temp) {
+        // query the scan's temporary size
+        return cub::DeviceScan::ExclusiveSum(nullptr, *temp_bytes, lbase, lbase, n, s) == cudaSuccess ? 0 : -1;
+    }
+    Launch l = grid_of(p);
+    dispatch_lattice(vel, [&](auto lat) {
+        using L = decltype(lat);
+        k_link_counts<L><<<l.grid, l.block, 0, s>>>(nbr, lbase, p);
+        return 1;
+    });
+    cub::DeviceScan::ExclusiveSum(temp, *temp_bytes, lbase, lbase, n, s);
+    const int64_t R = (int64_t)p.ny * p.nz;
+    const int blocks = (int)((R + 1 + 255) / 256 < 4096 ? (R + 1 + 255) / 256 : 4096);
+    dispatch_lattice(vel, [&](auto lat) {
+        using L = decltype(lat);
+        k_row_starts<L><<<blocks, 256, 0, s>>>(nbr, lbase, rowG, p);
+        return 1;
+    });
+    return 3;
 }
 
 int launch_init(int vel, int storage, void* pop, const uint32_t* nbr, const float* rho, const float* u,

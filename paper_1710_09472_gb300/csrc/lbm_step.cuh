@@ -252,11 +252,21 @@ __device__ __forceinline__ void store_val(typename S::T* ptr, float v, uint32_t 
 // then a 32-bit LCG (Numerical Recipes constants) whose upper 16 bits feed
 // each store.  A replayed step reproduces its stores bit for bit.
 struct Rng {
-    uint32_t x;
-    __device__ __forceinline__ Rng(uint32_t cell, const KParams& p) : x(hash32(cell ^ hash32(p.step * 0x9E3779B9u + p.seed))) {}
+    uint32_t x, cur;
+    int half;
+    __device__ __forceinline__ Rng(uint32_t cell, const KParams& p)
+        : x(hash32(cell ^ hash32(p.step * 0x9E3779B9u + p.seed))), cur(0u), half(0) {}
+    // 16 random bits; one LCG step serves two calls (high then low half of a
+    // fresh state, whose low half is decorrelated by a multiply-xorshift)
     __device__ __forceinline__ uint32_t next() {
-        x = x * 1664525u + 1013904223u;
-        return x >> 16;
+        if (half == 0) {
+            x = x * 1664525u + 1013904223u;
+            cur = x;
+            half = 1;
+            return cur >> 16;
+        }
+        half = 0;
+        return ((cur * 0x2c1b3c6du) ^ (cur >> 15)) & 0xFFFFu;
     }
 };
 
@@ -283,8 +293,8 @@ __device__ __forceinline__ void collide_any(const float* h, const float* E, cons
 }
 
 // General step kernel: one thread per cell, pulls straight from global memory
-// (bounce-back on the read side) and writes every own slot; solid cells write
-// zeros so that every sector is written whole.
+// and writes every own slot (solid cells write zeros, so that every sector is
+// written whole); links into solid cells also store into their link slot.
 template <class L, class S, int FORCE, bool EF, bool SR>
 __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict__ Pin, typename S::T* __restrict__ Pout,
                                                  const uint32_t* __restrict__ nbr, const float* __restrict__ Ef,
@@ -298,14 +308,21 @@ __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict
         return;
     }
     float h[L::Q];
-    dev::pull<L, S>(Pin, p.N, m, c, h);
+    dev::pull<L, S>(Pin, p, m, c, h);
     float E[3];
     load_E<L>(Ef, EF, p, c.cell, E);
     float out[L::Q];
     collide_any<L, S, FORCE>(h, E, p, out);
     Rng rng(c.cell, p);
+    typename S::T* Gout = reinterpret_cast<typename S::T*>(reinterpret_cast<char*>(Pout) + p.gofs);
+    const uint32_t o = outgoing<L::Q>(m);
+    const uint32_t base = m ? __ldg(p.lbase + c.cell) : 0u;
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) store_val<S, SR>(Pout + (int64_t)a * p.N + c.cell, out[a], SR ? rng.next() : 0u);
+    for (int a = 0; a < L::Q; ++a) {
+        const uint32_t rnd = SR ? rng.next() : 0u;
+        store_val<S, SR>(Pout + (int64_t)a * p.N + c.cell, out[a], rnd);
+        if (a != 0 && ((o >> a) & 1u)) store_val<S, SR>(Gout + link_slot(base, o, a), out[a], rnd);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -350,14 +367,37 @@ __device__ __forceinline__ unsigned long long packed_z() {
     return v;
 }
 
+// Shared-memory layout of one stage: Q source rows (Q nx elements), the row's
+// link masks (nx words), its first link slots (nx words), and its range of the
+// link buffer (gcap bytes, 16-byte aligned window).
 template <class L, class S>
-__device__ __forceinline__ void stage_row(typename S::T* __restrict__ buf, const typename S::T* __restrict__ Pin,
-                                          int row, int cpr_shift, const KParams& p) {
+struct StageLayout {
+    int nx, gcap;
+    __device__ __forceinline__ int bytes() const { return L::Q * nx * S::kBytes + 8 * nx + gcap; }
+    __device__ __forceinline__ typename S::T* rows(unsigned char* st) const {
+        return reinterpret_cast<typename S::T*>(st);
+    }
+    __device__ __forceinline__ uint32_t* masks(unsigned char* st) const {
+        return reinterpret_cast<uint32_t*>(st + L::Q * nx * S::kBytes);
+    }
+    __device__ __forceinline__ uint32_t* bases(unsigned char* st) const { return masks(st) + nx; }
+    __device__ __forceinline__ typename S::T* links(unsigned char* st) const {
+        return reinterpret_cast<typename S::T*>(st + L::Q * nx * S::kBytes + 8 * nx);
+    }
+};
+
+template <class L, class S>
+__device__ __forceinline__ void stage_row(unsigned char* st, const StageLayout<L, S>& lay,
+                                          const typename S::T* __restrict__ Pin, const uint32_t* __restrict__ nbr,
+                                          int row, uint32_t g0, uint32_t g1, int cpr_shift, uint32_t* gstart,
+                                          const KParams& p) {
+    using T = typename S::T;
     constexpr int kElem16 = 16 / S::kBytes;
     static_assert(L::Q <= 32, "direction codes must fit 64 bits");
     const unsigned long long kPy = packed_y<L>(), kPz = packed_z<L>();
-    const int cpr = 1 << cpr_shift;  // 16-byte chunks per row
+    const int cpr = 1 << cpr_shift;  // 16-byte chunks per population row
     const int y = row % p.ny, z = row / p.ny;
+    T* rows = lay.rows(st);
     const int total = L::Q << cpr_shift;
     for (int k = threadIdx.x; k < total; k += blockDim.x) {
         const int a = k >> cpr_shift, off = k & (cpr - 1);
@@ -367,24 +407,42 @@ __device__ __forceinline__ void stage_row(typename S::T* __restrict__ buf, const
         ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
         zs = zs < 0 ? zs + p.nz : (zs >= p.nz ? zs - p.nz : zs);
         const int64_t src = (int64_t)a * p.N + ((int64_t)zs * p.ny + ys) * p.nx + (int64_t)off * kElem16;
-        cp_async16(buf + a * p.nx + off * kElem16, Pin + src);
+        cp_async16(rows + a * p.nx + off * kElem16, Pin + src);
     }
+    // link masks and first link slots of the row (nx words each)
+    const int wchunks = p.nx >> 2;
+    const uint32_t* mrow = nbr + (int64_t)row * p.nx;
+    const uint32_t* brow = p.lbase + (int64_t)row * p.nx;
+    for (int k = threadIdx.x; k < 2 * wchunks; k += blockDim.x) {
+        if (k < wchunks)
+            cp_async16(lay.masks(st) + 4 * k, mrow + 4 * k);
+        else
+            cp_async16(lay.bases(st) + 4 * (k - wchunks), brow + 4 * (k - wchunks));
+    }
+    // the row's links [g0, g1), in a 16-byte aligned window
+    const uint64_t b0 = ((uint64_t)g0 * S::kBytes) & ~15ull;
+    const uint64_t b1 = ((uint64_t)g1 * S::kBytes + 15ull) & ~15ull;
+    const unsigned char* G = reinterpret_cast<const unsigned char*>(Pin) + p.gofs;
+    for (int k = threadIdx.x; k < (int)((b1 - b0) >> 4); k += blockDim.x)
+        cp_async16(reinterpret_cast<unsigned char*>(lay.links(st)) + 16 * k, G + b0 + 16 * (uint64_t)k);
+    if (threadIdx.x == 0) *gstart = (uint32_t)(b0 / S::kBytes);
 }
 
 template <class L, class S, int FORCE, bool EF, bool SR, int STAGES>
 __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restrict__ Pin,
                                                    typename S::T* __restrict__ Pout, const uint32_t* __restrict__ nbr,
-                                                   const float* __restrict__ Ef, int cpr_shift, KParams p) {
+                                                   const float* __restrict__ Ef, int cpr_shift, int gcap, KParams p) {
     using T = typename S::T;
     constexpr int kElem16 = 16 / S::kBytes;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = p.nx;
-    const int stage_elems = L::Q * nx;
-    T* ring = reinterpret_cast<T*>(smem_raw);
-    T* outrow = ring + STAGES * stage_elems;
-    uint32_t* flist = reinterpret_cast<uint32_t*>(outrow + stage_elems);  // x of the row's fluid cells
-    uint32_t* fmask = flist + nx;                                        // their link masks
+    const StageLayout<L, S> lay{nx, gcap};
+    const int sbytes = lay.bytes();
+    T* outrow = reinterpret_cast<T*>(smem_raw + STAGES * sbytes);
+    uint32_t* flist = reinterpret_cast<uint32_t*>(outrow + L::Q * nx);  // x of the row's fluid cells
     __shared__ int fcount;
+    __shared__ uint32_t gstart[STAGES];
+    T* Gout = reinterpret_cast<T*>(reinterpret_cast<char*>(Pout) + p.gofs);
     const int R = p.ny * p.nz;
     const int G = gridDim.x;
     const int cpr = 1 << cpr_shift;
@@ -392,49 +450,64 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
     for (int k = threadIdx.x; k < chunks; k += blockDim.x)
         reinterpret_cast<uint4*>(outrow)[k] = make_uint4(0u, 0u, 0u, 0u);
     if (threadIdx.x == 0) fcount = 0;
-    __syncthreads();
+    auto range = [&](int row, uint32_t& g0, uint32_t& g1) {
+        g0 = g1 = 0u;
+        if (row < R) {
+            g0 = __ldg(p.rowG + row);
+            g1 = __ldg(p.rowG + row + 1);
+        }
+    };
 #pragma unroll
     for (int k = 0; k < STAGES - 1; ++k) {
         const int rk = blockIdx.x + k * G;
-        if (rk < R) stage_row<L, S>(ring + k * stage_elems, Pin, rk, cpr_shift, p);
+        uint32_t g0, g1;
+        range(rk, g0, g1);
+        if (rk < R) stage_row<L, S>(smem_raw + k * sbytes, lay, Pin, nbr, rk, g0, g1, cpr_shift, &gstart[k], p);
         cp_async_commit();
     }
+    uint32_t ng0, ng1;  // link range of the next row to stage, loaded one iteration ahead
+    range(blockIdx.x + (STAGES - 1) * G, ng0, ng1);
+    __syncthreads();
     int it = 0;
     for (int r = blockIdx.x; r < R; r += G, ++it) {
         const int rn = r + (STAGES - 1) * G;
-        if (rn < R) stage_row<L, S>(ring + ((it + STAGES - 1) % STAGES) * stage_elems, Pin, rn, cpr_shift, p);
+        const int sn = (it + STAGES - 1) % STAGES;
+        if (rn < R) stage_row<L, S>(smem_raw + sn * sbytes, lay, Pin, nbr, rn, ng0, ng1, cpr_shift, &gstart[sn], p);
         cp_async_commit();
-        // compact the row's fluid cells (warp ballots, one shared atomic per warp)
+        range(rn + G, ng0, ng1);
+        cp_async_wait<STAGES - 1>();
+        __syncthreads();  // this row's stage has landed
+        unsigned char* st = smem_raw + (it % STAGES) * sbytes;
+        const T* buf = lay.rows(st);
+        const uint32_t* mrow = lay.masks(st);
+        const uint32_t* brow = lay.bases(st);
+        const T* lbuf = lay.links(st);
+        const uint32_t g_base = gstart[it % STAGES];
         const uint32_t rowbase = (uint32_t)r * (uint32_t)nx;
+        // compact the row's fluid cells (warp ballots, one shared atomic per warp)
         for (int x0 = 0; x0 < nx; x0 += blockDim.x) {
             const int x = x0 + threadIdx.x;
-            uint32_t m = kSolidBit;
-            if (x < nx) m = __ldg(nbr + rowbase + x);
-            const bool fluid = !(m & kSolidBit);
+            const bool fluid = x < nx && !(mrow[x] & kSolidBit);
             const unsigned ball = __ballot_sync(0xffffffffu, fluid);
             int base = 0;
             if ((threadIdx.x & 31) == 0 && ball) base = atomicAdd(&fcount, __popc(ball));
             base = __shfl_sync(0xffffffffu, base, 0);
-            if (fluid) {
-                const int idx = base + __popc(ball & ((1u << (threadIdx.x & 31)) - 1u));
-                flist[idx] = (uint32_t)x;
-                fmask[idx] = m;
-            }
+            if (fluid) flist[base + __popc(ball & ((1u << (threadIdx.x & 31)) - 1u))] = (uint32_t)x;
         }
-        cp_async_wait<STAGES - 1>();
-        __syncthreads();  // ring row ready, list complete
-        const T* buf = ring + (it % STAGES) * stage_elems;
+        __syncthreads();  // list complete
         const int nf = fcount;
         Cell c;
         c.y = r % p.ny;
         c.z = r / p.ny;
         for (int i = threadIdx.x; i < nf; i += blockDim.x) {
             const int x = (int)flist[i];
-            const uint32_t m = fmask[i];
+            const uint32_t m = mrow[x];
             c.x = x;
             c.cell = rowbase + (uint32_t)x;
             const int xm = x == 0 ? nx - 1 : x - 1;
             const int xp = x == nx - 1 ? 0 : x + 1;
+            const uint32_t o = outgoing<L::Q>(m);
+            const uint32_t lb = brow[x];
             float h[L::Q];
 #pragma unroll
             for (int a = 0; a < L::Q; ++a) {
@@ -442,18 +515,27 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
                 const int xs = ex > 0 ? xm : (ex < 0 ? xp : x);
                 h[a] = S::cvt(buf[a * nx + xs]);
             }
-            if (m != 0u) {  // bounced links: f_a(x) = P_abar(x)
+            if (m != 0u) {  // bounced links: f_a(x) = f*_abar(x) from the link buffer
 #pragma unroll
                 for (int a = 1; a < L::Q; ++a)
-                    if ((m >> a) & 1u) h[a] = S::raw(Pin + (int64_t)opposite(a) * p.N + c.cell);
+                    if ((m >> a) & 1u) h[a] = S::cvt(lbuf[link_slot(lb, o, opposite(a)) - g_base]);
             }
             float E[3];
             load_E<L>(Ef, EF, p, c.cell, E);
             float out[L::Q];
             collide_any<L, S, FORCE>(h, E, p, out);
             Rng rng(c.cell, p);
+            uint32_t rnd[L::Q];
 #pragma unroll
-            for (int a = 0; a < L::Q; ++a) store_val<S, SR>(outrow + a * nx + x, out[a], SR ? rng.next() : 0u);
+            for (int a = 0; a < L::Q; ++a) {
+                rnd[a] = SR ? rng.next() : 0u;
+                store_val<S, SR>(outrow + a * nx + x, out[a], rnd[a]);
+            }
+            if (o != 0u) {  // links into solid cells also store into their slots
+#pragma unroll
+                for (int a = 1; a < L::Q; ++a)
+                    if ((o >> a) & 1u) store_val<S, SR>(Gout + link_slot(lb, o, a), out[a], rnd[a]);
+            }
         }
         __syncthreads();  // output rows complete
         // write the output rows with 16-byte vector stores; each chunk is
@@ -466,7 +548,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
             *src = make_uint4(0u, 0u, 0u, 0u);
         }
         if (threadIdx.x == 0) fcount = 0;
-        __syncthreads();  // list and counter free for the next row
+        __syncthreads();  // list, counter and stage slot free for reuse
     }
     cp_async_wait<0>();
 }
@@ -510,17 +592,20 @@ int launch_one(const void* fin, void* fout, const uint32_t* nbr, const float* Ef
     const T* in = (const T*)fin;
     T* out = (T*)fout;
     const size_t row_bytes = (size_t)p.nx * S::kBytes;
-    const size_t smem = (size_t)(kStages + 1) * L::Q * row_bytes + 8 * (size_t)p.nx;
+    const int gcap = (int)((((size_t)p.max_row_links * S::kBytes + 15) & ~(size_t)15) + 32);
+    const size_t stage_bytes = (size_t)L::Q * row_bytes + 8 * (size_t)p.nx + gcap;
+    const size_t smem = (size_t)kStages * stage_bytes + (size_t)L::Q * row_bytes + 4 * (size_t)p.nx;
     const size_t cpr = row_bytes / 16;
     int cpr_shift = 0;
     while ((size_t(1) << cpr_shift) < cpr) ++cpr_shift;
-    if (row_bytes % 16 == 0 && (size_t(1) << cpr_shift) == cpr && smem <= kSmemBudget && p.nx >= 32) {
+    if (row_bytes % 16 == 0 && (size_t(1) << cpr_shift) == cpr && smem <= kSmemBudget && p.nx >= 32 &&
+        p.nx % 4 == 0) {
         const int threads = p.nx >= kRowThreads ? kRowThreads : ((p.nx + 31) / 32) * 32;
         auto kern = k_step_rows<L, S, FORCE, EF, SR, kStages>;
         const int blocks = persistent_grid(kern, threads, smem);
         if (blocks > 0) {
             const int rows = p.ny * p.nz;
-            kern<<<blocks < rows ? blocks : rows, threads, smem, s>>>(in, out, nbr, Ef, cpr_shift, p);
+            kern<<<blocks < rows ? blocks : rows, threads, smem, s>>>(in, out, nbr, Ef, cpr_shift, gcap, p);
             return 1;
         }
     }
