@@ -26,8 +26,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(n=256, radius=6.0, porosity=0.7, seed=1, Ex=1e-6, Bz=1e-3, tau=0.8)
-WORKLOAD_NAME = ("porous-3d-256^3 D3V19 FD(theta=1/270,mu=1) spheres r=6 porosity=0.7 seed=1, "
-                 "tau=0.8 E_x=1e-6 B_z=1e-3 force=term")
+
+
+def workload_name(n: int) -> str:
+    return (f"porous-3d-{n}^3 D3V19 FD(theta=1/270,mu=1) spheres r=6 porosity=0.7 seed=1, "
+            "tau=0.8 E_x=1e-6 B_z=1e-3 force=term")
 
 # DRAM traffic per launch of the step kernel from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by storage, with the
@@ -262,13 +265,13 @@ def run_gpu(args, rank, world):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "storage": "f16-deviation (2^12 scale), FP32 collision",
+        "config": {"workload": workload_name(n), "storage": "f16-deviation (2^12 scale), FP32 collision",
                    "cells": N, "fluid_cells": n_fluid, "spheres": count, "parallelism": f"replicas x{world}",
-                   "l2": "state 1.2 GB > 129 MB L2; no flush needed"},
+                   "l2": f"state {2 * Q * N / 1e9:.2f} GB > 129 MB L2; no flush needed"},
         "mflups": round(world * n_fluid * args.steps / (ms16 * 1e-3) / 1e6, 1),
         "roofline": {"bound": "hbm", "achieved": round(ach16, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(ach16 / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "k_step<D3V19,f16,term>", "alg_bytes_per_launch": alg16},
+                     "kernel": "k_step_rows<D3V19,f16,term>", "alg_bytes_per_launch": alg16},
         "fp32": {"value": round(mlups(ms32), 1), "unit": "MLUPS", "ms_per_step": round(ms32 / args.steps, 5),
                  "roofline": {"bound": "hbm", "achieved": round(ach32, 1), "peak": peak, "unit": "GB/s",
                               "frac": round(ach32 / peak, 4), "alg_bytes_per_launch": alg32}},
@@ -352,7 +355,7 @@ def run_reference(args, rank, world):
     return {"metric": "MLUPS", "value": v, "unit": "MLUPS", "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "sample": sample},
+            "config": {"workload": workload_name(n), "sample": sample},
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -367,7 +370,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--adjoint-checkpoint", type=int, default=14)
+    ap.add_argument("--n", type=int, default=256, help="box edge (256 is the benchmark; smaller for profiling)")
     args = ap.parse_args()
+    WORKLOAD["n"] = args.n
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world = int(os.environ.get("WORLD_SIZE", "1"))

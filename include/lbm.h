@@ -197,9 +197,10 @@ lbm_status lbm_window_totals(lbm_ctx* ctx, int64_t t_begin, int64_t t_end, doubl
  *   dL_dB   : 3 host doubles, dL/dB (2D: only the z component), or NULL.
  *   dL_dtau : host double, or NULL.   loss : host double (L itself), or NULL.
  *   dL_df0  : [Q * N] FP32 device, dL/df_0 (population layout), or NULL.
- * Device memory: (ceil(t_end / K) + K - 1) copies of the stored populations
- * plus two FP32 adjoint fields, allocated for the call and released before it
- * returns.  Gradients accumulate in FP64; the sweep is deterministic.
+ * Device memory: (ceil(t_end / K) + K - 1) copies of the stored state
+ * (populations + bounce-back link buffer) plus two FP32 adjoint fields (Q N
+ * values + one per bounce-back link each), allocated for the call and
+ * released before it returns.  Gradients accumulate in FP64; the sweep is deterministic.
  * Synchronises.  Errors: INVALID_ARG, STATE, OOM (with the size needed), CUDA,
  * NONFINITE. */
 lbm_status lbm_adjoint(lbm_ctx* ctx, const float* w_rho, const float* w_j, int64_t t_begin, int64_t t_end,

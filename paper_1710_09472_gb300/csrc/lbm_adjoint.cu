@@ -13,10 +13,19 @@
 // kernel's own expressions (direct N = 2 EDF of Sec. 5.1, forcing term of
 // Sec. 7), so the reverse step is consistent with the FP32 forward.
 //
-// f_t is rebuilt by pulling the stored buffer P_t of the forward replay.
+// An adjoint field is lam[a * N + cell] (f-space, population layout) followed,
+// at byte offset p.lgofs, by a link buffer: for every link of a fluid cell y
+// into a solid cell (outgoing direction b) the slot of (y, b) in the forward's
+// link numbering holds lam_bbar(y).  The bounced gather lamt_b(y) =
+// lam_{t+1,bbar}(y) is then one contiguous range per row, as in the forward's
+// pull.
+//
+// f_t is rebuilt by pulling the stored state of the forward replay.
 // Parameter gradients: dL/dE(x) is accumulated per cell in FP64; dL/dB,
 // dL/dtau and the loss are block-reduced into per-block FP64 slots that each
-// block owns (one read-modify-write per block per launch, deterministic).
+// block owns (deterministic for a fixed launch shape).
+#include <mutex>
+
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -25,14 +34,13 @@ namespace {
 using dev::Cell;
 using dev::cross3;
 using dev::edot;
-using dev::esq;
 using dev::kBlock;
 using dev::warp_sum;
 constexpr int kSlots = 5;  // gB[3], gtau, loss
 
 // Adds the block's sums of acc[kSlots] into slots[block * kSlots + k].
-__device__ __forceinline__ void block_accumulate(double* acc, double* __restrict__ slots) {
-    __shared__ double sh[kBlock / 32][kSlots];
+__device__ __forceinline__ void block_accumulate(double* acc, double* __restrict__ slots, int64_t block) {
+    __shared__ double sh[32][kSlots];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < kSlots; ++k) acc[k] = warp_sum(acc[k]);
@@ -43,14 +51,197 @@ __device__ __forceinline__ void block_accumulate(double* acc, double* __restrict
     __syncthreads();
     if (wid == 0) {
         const int nw = (blockDim.x + 31) / 32;
-        const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
 #pragma unroll
         for (int k = 0; k < kSlots; ++k) {
             double v = lane < nw ? sh[lane][k] : 0.0;
             v = warp_sum(v);
-            if (lane == 0) slots[b * kSlots + k] += v;
+            if (lane == 0) slots[block * kSlots + k] += v;
         }
     }
+}
+
+template <class L, bool EF>
+__device__ __forceinline__ void load_E(const float* __restrict__ Ef, const KParams& p, uint32_t cell, float* E) {
+    if (EF) {
+        E[0] = __ldg(Ef + cell);
+        E[1] = __ldg(Ef + p.N + cell);
+        E[2] = (L::D == 3) ? __ldg(Ef + 2 * p.N + cell) : 0.f;
+    } else {
+        E[0] = p.E[0];
+        E[1] = p.E[1];
+        E[2] = p.E[2];
+    }
+}
+
+template <class L, bool WIN>
+__device__ __forceinline__ void load_weights(const float* __restrict__ w_rho, const float* __restrict__ w_j,
+                                             const KParams& p, uint32_t cell, float& wr, float* wj) {
+    wr = 0.f;
+    wj[0] = wj[1] = wj[2] = 0.f;
+    if (WIN) {
+        wr = w_rho ? __ldg(w_rho + cell) : 0.f;
+#pragma unroll
+        for (int d = 0; d < L::D; ++d) wj[d] = w_j ? __ldg(w_j + (int64_t)d * p.N + cell) : 0.f;
+    }
+}
+
+// The reverse step at one fluid cell.  h: unscaled deviations of f_t at the
+// cell; lt: lamt; E: the field there; wr, wj: its loss weights (used when WIN).
+// Writes lam = lam_t at the cell and gEc = its dL/dE term; adds
+// {dL/dB, dL/dtau, loss} into acc[0..4].
+template <class L, int FORCE, bool WIN>
+__device__ __forceinline__ void adjoint_cell(const float* h, const float* lt, const float* E, const KParams& p,
+                                             float wr, const float* wj, float* lam, float* gEc, double* acc) {
+    float drho = 0.f, j[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) {
+        drho += h[a];
+        j[0] += L::c(a, 0) * h[a];
+        j[1] += L::c(a, 1) * h[a];
+        j[2] += L::c(a, 2) * h[a];
+    }
+    j[0] *= p.cs_inv;
+    j[1] *= p.cs_inv;
+    j[2] = (L::D == 3) ? j[2] * p.cs_inv : 0.f;
+    const float rho = p.rho0 + drho;
+    const float inv_rho = 1.0f / rho;
+    const float u[3] = {j[0] * inv_rho, j[1] * inv_rho, j[2] * inv_rho};
+    float acc_f[3], ue[3];
+    if (FORCE == 0) {
+        float uxb[3];
+        cross3(u, p.B, uxb);
+        acc_f[0] = E[0] + uxb[0];
+        acc_f[1] = E[1] + uxb[1];
+        acc_f[2] = (L::D == 3) ? E[2] + uxb[2] : 0.f;
+        ue[0] = u[0] + p.tau * acc_f[0];
+        ue[1] = u[1] + p.tau * acc_f[1];
+        ue[2] = u[2] + p.tau * acc_f[2];
+    } else {
+        ue[0] = u[0];
+        ue[1] = u[1];
+        ue[2] = u[2];
+    }
+    const float u2 = ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2];
+    const float Adr = p.A * drho;
+    const float inv_tau = p.omega;
+
+    float rho_bar = 0.f;
+    float gtau = 0.f;
+    // sums over a of lt_a w_a X for the vector derivatives
+    float s_e[3] = {0.f, 0.f, 0.f};     // sum lt w e
+    float s_eue[3] = {0.f, 0.f, 0.f};   // sum lt w (e.ue) e
+    float s_k2 = 0.f;                   // sum lt w k2
+    float s_eE_e[3] = {0.f, 0.f, 0.f};  // sum lt w (e.E) e        (term mode)
+    float s_k2_e[3] = {0.f, 0.f, 0.f};  // sum lt w k2 e           (term mode)
+    float s_k2_a[3] = {0.f, 0.f, 0.f};  // sum lt w k2 (e x B)/c_s (term mode)
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) {
+        const float eu = edot<L>(a, ue);
+        const float k2 = p.k2[a];
+        const float Fr = p.w[a] * (p.A + p.Bp * eu + p.Cp * eu * eu + k2 * u2);  // F_a / rho
+        const float heq = p.w[a] * (Adr + rho * (p.Bp * eu + p.Cp * eu * eu + k2 * u2));
+        const float lw = lt[a] * p.w[a];
+        gtau += lt[a] * (h[a] - heq);
+        s_k2 += lw * k2;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int ed = L::c(a, d);
+            if (ed != 0) {
+                s_e[d] += ed * lw;
+                s_eue[d] += ed * lw * eu;
+            }
+        }
+        if (FORCE == 0) {
+            rho_bar += lt[a] * Fr * inv_tau;
+        } else {
+            const float eE = edot<L>(a, E);
+            float exb[3] = {0.f, 0.f, 0.f};
+            const float e3[3] = {(float)L::c(a, 0), (float)L::c(a, 1), (float)L::c(a, 2)};  // e_a
+            cross3(e3, p.B, exb);
+            const float ua = u[0] * E[0] + u[1] * E[1] + u[2] * E[2] +
+                             (u[0] * exb[0] + u[1] * exb[1] + u[2] * exb[2]) * p.cs_inv;
+            const float Sr = p.w[a] * (p.Bp * eE + 2.f * p.Cp * eu * eE + 2.f * k2 * ua);  // S_a / rho
+            rho_bar += lt[a] * (Fr * inv_tau + Sr);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int ed = L::c(a, d);
+                if (ed != 0) {
+                    s_eE_e[d] += ed * lw * eE;
+                    s_k2_e[d] += ed * lw * k2;
+                }
+                s_k2_a[d] += lw * k2 * exb[d] * p.cs_inv;
+            }
+        }
+    }
+    gtau *= inv_tau * inv_tau;
+    // dF/dv summed against lt w: rho [Bp s_e + 2 Cp s_eue + 2 s_k2 v]
+    float dF[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dF[d] = rho * (p.Bp * s_e[d] + 2.f * p.Cp * s_eue[d] + 2.f * s_k2 * ue[d]);
+    float u_bar[3], gBc[3];
+    if (FORCE == 0) {
+        const float ue_bar[3] = {dF[0] * inv_tau, dF[1] * inv_tau, dF[2] * inv_tau};
+        gtau += ue_bar[0] * acc_f[0] + ue_bar[1] * acc_f[1] + ue_bar[2] * acc_f[2];
+        float t1[3], t2[3];
+        cross3(ue_bar, u, t1);    // d(u x B)/dB transposed
+        cross3(p.B, ue_bar, t2);  // d(u x B)/du transposed
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            gEc[d] = p.tau * ue_bar[d];
+            gBc[d] = p.tau * t1[d];
+            u_bar[d] = ue_bar[d] + p.tau * t2[d];
+        }
+    } else {
+        // S_a depends on u through (e.u)(e.E) and u.a_a, and on E, B through a_a:
+        //   sum_a lt_a dS_a/du = rho [2 Cp s_eE_e + 2 (s_k2 E + s_k2_a)]
+        //   sum_a lt_a dS_a/da = dF (at v = u)                  -> dL/dE
+        //   dL/dB = sum_a (abar_a x e_a) / c_s = (2 rho / c_s) u x (sum lt w k2 e)
+        float bxk[3];
+        cross3(u, s_k2_e, bxk);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            u_bar[d] = dF[d] * inv_tau + rho * (2.f * p.Cp * s_eE_e[d] + 2.f * (s_k2 * E[d] + s_k2_a[d]));
+            gEc[d] = dF[d];
+            gBc[d] = 2.f * rho * p.cs_inv * bxk[d];
+        }
+    }
+    rho_bar -= (u_bar[0] * u[0] + u_bar[1] * u[1] + u_bar[2] * u[2]) * inv_rho;
+    const float ub[3] = {u_bar[0] * inv_rho * p.cs_inv, u_bar[1] * inv_rho * p.cs_inv,
+                         u_bar[2] * inv_rho * p.cs_inv};
+    float wjs[3] = {0.f, 0.f, 0.f};
+    if (WIN) {
+#pragma unroll
+        for (int d = 0; d < L::D; ++d) wjs[d] = wj[d] * p.cs_inv;
+        acc[4] += (double)wr * (double)rho + (double)wj[0] * (double)j[0] + (double)wj[1] * (double)j[1] +
+                  (double)wj[2] * (double)j[2];
+    }
+    const float omm = 1.0f - p.omega;
+#pragma unroll
+    for (int b = 0; b < L::Q; ++b) {
+        float v = omm * lt[b] + rho_bar + edot<L>(b, ub);
+        if (WIN) v += wr + edot<L>(b, wjs);
+        lam[b] = v;
+    }
+    acc[0] += gBc[0];
+    acc[1] += gBc[1];
+    acc[2] += gBc[2];
+    acc[3] += gtau;
+}
+
+// The link-buffer copies of a fluid cell's lam_t: slot (y, b) = lam_bbar(y)
+// for every outgoing direction b into a solid cell.
+template <class L>
+__device__ __forceinline__ void store_lam_links(float* __restrict__ lamG, uint32_t o, uint32_t lb, const float* lam) {
+#pragma unroll
+    for (int b = 1; b < L::Q; ++b)
+        if ((o >> b) & 1u) lamG[link_slot(lb, o, b)] = lam[opposite(b)];
+}
+
+__device__ __forceinline__ float* link_part(float* lam, const KParams& p) {
+    return reinterpret_cast<float*>(reinterpret_cast<char*>(lam) + p.lgofs);
+}
+__device__ __forceinline__ const float* link_part(const float* lam, const KParams& p) {
+    return reinterpret_cast<const float*>(reinterpret_cast<const char*>(lam) + p.lgofs);
 }
 
 // ---------------------------------------------------------------------------
@@ -90,24 +281,27 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_seed(const typename S::T* __
                 acc[4] = (double)wr * (double)(p.rho0 + drho) + (double)wj[0] * jx + (double)wj[1] * jy +
                          (double)wj[2] * jz;
             }
+            float lm[L::Q];
 #pragma unroll
             for (int a = 0; a < L::Q; ++a) {
-                const float g = wr + edot<L>(a, wj);
-                lam[(int64_t)a * p.N + c.cell] = g;
+                lm[a] = wr + edot<L>(a, wj);
+                lam[(int64_t)a * p.N + c.cell] = lm[a];
             }
+            const uint32_t o = outgoing<L::Q>(m);
+            if (o) store_lam_links<L>(link_part(lam, p), o, __ldg(p.lbase + c.cell), lm);
         }
     }
-    block_accumulate(acc, slots);
+    block_accumulate(acc, slots, (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
-// One reverse step.
+// One reverse step, general kernel: one thread per cell, direct global loads.
 // ---------------------------------------------------------------------------
 template <class L, class S, int FORCE, bool EF, bool WIN>
 __global__ void __launch_bounds__(kBlock) k_adjoint_step(
-    const typename S::T* __restrict__ P,       // stored buffer of the forward replay at step t
-    const float* __restrict__ lam_in,          // lam_{t+1}
-    float* __restrict__ lam_out,               // lam_t
+    const typename S::T* __restrict__ P,  // stored state of the forward replay at step t
+    const float* __restrict__ lam_in,     // lam_{t+1}
+    float* __restrict__ lam_out,          // lam_t
     const uint32_t* __restrict__ nbr, const float* __restrict__ Ef, const float* __restrict__ w_rho,
     const float* __restrict__ w_j, double* __restrict__ gE, double* __restrict__ slots, KParams p) {
     Cell c;
@@ -118,177 +312,221 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(
 #pragma unroll
             for (int a = 0; a < L::Q; ++a) lam_out[(int64_t)a * p.N + c.cell] = 0.f;
         } else {
-            // f_t(y): pull of the stored buffer; lamt(y): gather from downstream,
-            // lamt_a(y) = lam_a(y + e_a), or lam_abar(y) when y + e_a is solid
-            // (y + e_a = y - e_abar: bit abar of the link mask)
+            // f_t(y): pull of the stored state; lamt(y): gather from downstream
             float h[L::Q], lt[L::Q];
             dev::pull<L, S>(P, p, m, c, h);
+            const uint32_t o = outgoing<L::Q>(m);
+            const uint32_t lb = m ? __ldg(p.lbase + c.cell) : 0u;
+            const float* lamG_in = link_part(lam_in, p);
 #pragma unroll
             for (int a = 0; a < L::Q; ++a) {
                 h[a] *= p.inv_scale;
-                int64_t lidx;
-                if (a == 0)
-                    lidx = c.cell;
+                if (a != 0 && ((o >> a) & 1u))
+                    lt[a] = __ldg(lamG_in + link_slot(lb, o, a));
                 else
-                    lidx = ((m >> opposite(a)) & 1u) ? (int64_t)opposite(a) * p.N + c.cell
-                                                     : (int64_t)a * p.N + dev::shifted<L>(c, a, +1);
-                lt[a] = __ldg(lam_in + lidx);
+                    lt[a] = __ldg(lam_in + (int64_t)a * p.N + (a == 0 ? c.cell : dev::shifted<L>(c, a, +1)));
             }
-            // forward quantities
-            float drho = 0.f, j[3] = {0.f, 0.f, 0.f};
+            float E[3], wr, wj[3], lam[L::Q], gEc[3];
+            load_E<L, EF>(Ef, p, c.cell, E);
+            load_weights<L, WIN>(w_rho, w_j, p, c.cell, wr, wj);
+            adjoint_cell<L, FORCE, WIN>(h, lt, E, p, wr, wj, lam, gEc, acc);
 #pragma unroll
-            for (int a = 0; a < L::Q; ++a) {
-                drho += h[a];
-                j[0] += L::c(a, 0) * h[a];
-                j[1] += L::c(a, 1) * h[a];
-                j[2] += L::c(a, 2) * h[a];
-            }
-            j[0] *= p.cs_inv;
-            j[1] *= p.cs_inv;
-            j[2] = (L::D == 3) ? j[2] * p.cs_inv : 0.f;
-            const float rho = p.rho0 + drho;
-            const float inv_rho = 1.0f / rho;
-            const float u[3] = {j[0] * inv_rho, j[1] * inv_rho, j[2] * inv_rho};
-            float E[3];
-            if (EF) {
-                E[0] = __ldg(Ef + c.cell);
-                E[1] = __ldg(Ef + p.N + c.cell);
-                E[2] = (L::D == 3) ? __ldg(Ef + 2 * p.N + c.cell) : 0.f;
-            } else {
-                E[0] = p.E[0];
-                E[1] = p.E[1];
-                E[2] = p.E[2];
-            }
-            float acc_f[3], ue[3];
-            if (FORCE == 0) {
-                float uxb[3];
-                cross3(u, p.B, uxb);
-                acc_f[0] = E[0] + uxb[0];
-                acc_f[1] = E[1] + uxb[1];
-                acc_f[2] = (L::D == 3) ? E[2] + uxb[2] : 0.f;
-                ue[0] = u[0] + p.tau * acc_f[0];
-                ue[1] = u[1] + p.tau * acc_f[1];
-                ue[2] = u[2] + p.tau * acc_f[2];
-            } else {
-                ue[0] = u[0];
-                ue[1] = u[1];
-                ue[2] = u[2];
-            }
-            const float u2 = ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2];
-            const float Adr = p.A * drho;
-            const float inv_tau = p.omega;
-
-            float rho_bar = 0.f;
-            float gtau = 0.f;
-            // sums over a of lt_a w_a X for the vector derivatives
-            float s_e[3] = {0.f, 0.f, 0.f};   // sum lt w e
-            float s_eue[3] = {0.f, 0.f, 0.f}; // sum lt w (e.ue) e
-            float s_k2 = 0.f;                 // sum lt w k2
-            float s_eE_e[3] = {0.f, 0.f, 0.f};  // sum lt w (e.E) e        (term mode)
-            float s_k2_e[3] = {0.f, 0.f, 0.f};  // sum lt w k2 e           (term mode)
-            float s_k2_a[3] = {0.f, 0.f, 0.f};  // sum lt w k2 (e x B)/c_s (term mode)
-#pragma unroll
-            for (int a = 0; a < L::Q; ++a) {
-                const float eu = edot<L>(a, ue);
-                const float k2 = p.k2[a];
-                const float Fr = p.w[a] * (p.A + p.Bp * eu + p.Cp * eu * eu + k2 * u2);  // F_a / rho
-                const float heq = p.w[a] * (Adr + rho * (p.Bp * eu + p.Cp * eu * eu + k2 * u2));
-                const float lw = lt[a] * p.w[a];
-                gtau += lt[a] * (h[a] - heq);
-                s_k2 += lw * k2;
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const int ed = L::c(a, d);
-                    if (ed != 0) {
-                        s_e[d] += ed * lw;
-                        s_eue[d] += ed * lw * eu;
-                    }
-                }
-                if (FORCE == 0) {
-                    rho_bar += lt[a] * Fr * inv_tau;
-                } else {
-                    const float eE = edot<L>(a, E);
-                    float exb[3] = {0.f, 0.f, 0.f};
-                    const float e3[3] = {(float)L::c(a, 0), (float)L::c(a, 1), (float)L::c(a, 2)};  // e_a
-                    cross3(e3, p.B, exb);
-                    const float ua = u[0] * E[0] + u[1] * E[1] + u[2] * E[2] +
-                                     (u[0] * exb[0] + u[1] * exb[1] + u[2] * exb[2]) * p.cs_inv;
-                    const float Sr = p.w[a] * (p.Bp * eE + 2.f * p.Cp * eu * eE + 2.f * k2 * ua);  // S_a / rho
-                    rho_bar += lt[a] * (Fr * inv_tau + Sr);
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        const int ed = L::c(a, d);
-                        if (ed != 0) {
-                            s_eE_e[d] += ed * lw * eE;
-                            s_k2_e[d] += ed * lw * k2;
-                        }
-                        s_k2_a[d] += lw * k2 * exb[d] * p.cs_inv;
-                    }
-                }
-            }
-            gtau *= inv_tau * inv_tau;
-            // dF/dv summed against lt w: rho [Bp s_e + 2 Cp s_eue + 2 s_k2 v]
-            float dF[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) dF[d] = rho * (p.Bp * s_e[d] + 2.f * p.Cp * s_eue[d] + 2.f * s_k2 * ue[d]);
-            float u_bar[3];
-            float gEc[3], gBc[3];
-            if (FORCE == 0) {
-                float ue_bar[3] = {dF[0] * inv_tau, dF[1] * inv_tau, dF[2] * inv_tau};
-                gtau += ue_bar[0] * acc_f[0] + ue_bar[1] * acc_f[1] + ue_bar[2] * acc_f[2];
-                float t1[3], t2[3];
-                cross3(ue_bar, u, t1);      // d(u x B)/dB transposed
-                cross3(p.B, ue_bar, t2);    // d(u x B)/du transposed
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    gEc[d] = p.tau * ue_bar[d];
-                    gBc[d] = p.tau * t1[d];
-                    u_bar[d] = ue_bar[d] + p.tau * t2[d];
-                }
-            } else {
-                // S_a depends on u through (e.u)(e.E) and u.a_a, and on E, B through a_a
-                float bxk[3];
-                // sum_a lt_a dS_a/du = rho [2 Cp s_eE_e + 2 (s_k2 E + s_k2_a)]
-                // sum_a lt_a dS_a/da summed over a = dF (at v = u) -> dL/dE
-                // dL/dB = sum_a (abar_a x e_a)/c_s with abar_a = lt w rho [Bp e + 2Cp (e.u) e + 2 k2 u]
-                //       = (2 rho / c_s) u x (sum lt w k2 e)
-                cross3(u, s_k2_e, bxk);
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    u_bar[d] = dF[d] * inv_tau + rho * (2.f * p.Cp * s_eE_e[d] + 2.f * (s_k2 * E[d] + s_k2_a[d]));
-                    gEc[d] = dF[d];
-                    gBc[d] = 2.f * rho * p.cs_inv * bxk[d];
-                }
-            }
-            rho_bar -= (u_bar[0] * u[0] + u_bar[1] * u[1] + u_bar[2] * u[2]) * inv_rho;
-            float ub[3] = {u_bar[0] * inv_rho * p.cs_inv, u_bar[1] * inv_rho * p.cs_inv,
-                           u_bar[2] * inv_rho * p.cs_inv};
-            float wr = 0.f, wj[3] = {0.f, 0.f, 0.f};
-            if (WIN) {
-                wr = w_rho ? __ldg(w_rho + c.cell) : 0.f;
-#pragma unroll
-                for (int d = 0; d < L::D; ++d) wj[d] = w_j ? __ldg(w_j + (int64_t)d * p.N + c.cell) * p.cs_inv : 0.f;
-                acc[4] = (double)wr * (double)rho + (double)wj[0] * (double)j[0] / p.cs_inv +
-                         (double)wj[1] * (double)j[1] / p.cs_inv + (double)wj[2] * (double)j[2] / p.cs_inv;
-            }
-            const float omm = 1.0f - p.omega;
-#pragma unroll
-            for (int b = 0; b < L::Q; ++b) {
-                float v = omm * lt[b] + rho_bar + edot<L>(b, ub);
-                if (WIN) v += wr + edot<L>(b, wj);
-                lam_out[(int64_t)b * p.N + c.cell] = v;
-            }
+            for (int b = 0; b < L::Q; ++b) lam_out[(int64_t)b * p.N + c.cell] = lam[b];
+            if (o) store_lam_links<L>(link_part(lam_out, p), o, lb, lam);
             if (gE) {
 #pragma unroll
                 for (int d = 0; d < L::D; ++d) gE[(int64_t)d * p.N + c.cell] += (double)gEc[d];
             }
-            acc[0] = gBc[0];
-            acc[1] = gBc[1];
-            acc[2] = gBc[2];
-            acc[3] = gtau;
         }
     }
-    block_accumulate(acc, slots);
+    block_accumulate(acc, slots, (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Row-staged reverse step (persistent; block b takes rows b, b + G, ...).
+// One stage holds, for the row (y, z):
+//   - the Q pull rows of the forward state P_t: direction a from row
+//     (y - e_ay, z - e_az), read at x - e_ax;
+//   - the row's link masks and first link slots;
+//   - its window of P_t's link buffer (bounced pulls);
+//   - the Q gather rows of lam_{t+1}: direction a from row
+//     (y + e_ay, z + e_az), read at x + e_ax;
+//   - its window of lam_{t+1}'s link buffer (bounced gathers).
+// Stages are filled by cp.async while earlier rows compute; fluid cells are
+// compacted; lam_t goes through shared-memory output rows (zero for solid
+// cells) and is written with 16-byte vector stores.  dL/dB, dL/dtau and the
+// loss stay in registers until the block's single reduction at the end.
+// ---------------------------------------------------------------------------
+template <class L, class S>
+struct AdjLayout {
+    int nx, gcapP, gcapL;
+    __device__ __host__ int prow() const { return L::Q * nx * S::kBytes; }
+    __device__ __host__ int lrow() const { return L::Q * nx * 4; }
+    __device__ __host__ int bytes() const { return prow() + 8 * nx + gcapP + lrow() + gcapL; }
+};
+
+// Rows of every direction, elements of `esize` bytes: direction a from row
+// (y + s e_ay, z + s e_az), periodic; one warp per direction at a time.
+template <class L>
+__device__ __forceinline__ void stage_dir_rows(unsigned char* dst, const unsigned char* base, int esize, int s, int y,
+                                               int z, const KParams& p) {
+    const unsigned long long kPy = dev::packed_y<L>(), kPz = dev::packed_z<L>();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int row_bytes = p.nx * esize, chunks = row_bytes >> 4;
+    for (int a = warp; a < L::Q; a += nwarps) {
+        const int ey = (int)((kPy >> (2 * a)) & 3ull) - 1, ez = (int)((kPz >> (2 * a)) & 3ull) - 1;
+        int ys = y + s * ey, zs = z + s * ez;
+        ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
+        zs = zs < 0 ? zs + p.nz : (zs >= p.nz ? zs - p.nz : zs);
+        const unsigned char* src = base + ((int64_t)a * p.N + ((int64_t)zs * p.ny + ys) * p.nx) * esize;
+        unsigned char* d = dst + a * row_bytes;
+        for (int k = lane; k < chunks; k += 32) dev::cp_async16(d + 16 * k, src + 16 * k);
+    }
+}
+
+// Link slots [g0, g1) of elements of `esize` bytes, as a 16-byte aligned window
+// whose first element index goes to *gstart.
+__device__ __forceinline__ void stage_window(unsigned char* dst, const unsigned char* base, int esize, uint32_t g0,
+                                             uint32_t g1, uint32_t* gstart) {
+    const uint64_t b0 = ((uint64_t)g0 * esize) & ~15ull;
+    const uint64_t b1 = ((uint64_t)g1 * esize + 15ull) & ~15ull;
+    for (int k = threadIdx.x; k < (int)((b1 - b0) >> 4); k += blockDim.x)
+        dev::cp_async16(dst + 16 * k, base + b0 + 16 * (uint64_t)k);
+    if (threadIdx.x == 0) *gstart = (uint32_t)(b0 / esize);
+}
+
+template <class L, class S, int FORCE, bool EF, bool WIN, int STAGES>
+__global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __restrict__ P,
+                                                      const float* __restrict__ lam_in, float* __restrict__ lam_out,
+                                                      const uint32_t* __restrict__ nbr, const float* __restrict__ Ef,
+                                                      const float* __restrict__ w_rho, const float* __restrict__ w_j,
+                                                      double* __restrict__ gE, double* __restrict__ slots, int gcapP,
+                                                      int gcapL, KParams p) {
+    using T = typename S::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = p.nx;
+    const AdjLayout<L, S> lay{nx, gcapP, gcapL};
+    const int sbytes = lay.bytes();
+    float* outrow = reinterpret_cast<float*>(smem_raw + STAGES * sbytes);
+    uint32_t* flist = reinterpret_cast<uint32_t*>(outrow + L::Q * nx);
+    __shared__ int fcount[2];  // interior, boundary fluid cells of the row
+    __shared__ uint32_t gsP[STAGES], gsL[STAGES];
+    const unsigned char* Pb = reinterpret_cast<const unsigned char*>(P);
+    const unsigned char* Lb = reinterpret_cast<const unsigned char*>(lam_in);
+    float* lamG_out = link_part(lam_out, p);
+    const int R = p.ny * p.nz;
+    const int G = gridDim.x;
+    const int lchunks = (L::Q * nx * 4) >> 4;
+    for (int k = threadIdx.x; k < lchunks; k += blockDim.x)
+        reinterpret_cast<uint4*>(outrow)[k] = make_uint4(0u, 0u, 0u, 0u);
+    if (threadIdx.x == 0) fcount[0] = fcount[1] = 0;
+    auto range = [&](int row, uint32_t& g0, uint32_t& g1) {
+        g0 = g1 = 0u;
+        if (row < R) {
+            g0 = __ldg(p.rowG + row);
+            g1 = __ldg(p.rowG + row + 1);
+        }
+    };
+    auto stage = [&](int slot, int row, uint32_t g0, uint32_t g1) {
+        unsigned char* st = smem_raw + slot * sbytes;
+        const int y = row % p.ny, z = row / p.ny;
+        stage_dir_rows<L>(st, Pb, S::kBytes, -1, y, z, p);
+        unsigned char* mb = st + lay.prow();
+        const int wchunks = nx >> 2;
+        for (int k = threadIdx.x; k < 2 * wchunks; k += blockDim.x) {
+            if (k < wchunks)
+                dev::cp_async16(mb + 16 * k, nbr + (int64_t)row * nx + 4 * k);
+            else
+                dev::cp_async16(mb + 4 * nx + 16 * (k - wchunks), p.lbase + (int64_t)row * nx + 4 * (k - wchunks));
+        }
+        stage_window(mb + 8 * nx, Pb + p.gofs, S::kBytes, g0, g1, &gsP[slot]);
+        unsigned char* lr = mb + 8 * nx + gcapP;
+        stage_dir_rows<L>(lr, Lb, 4, +1, y, z, p);
+        stage_window(lr + lay.lrow(), Lb + p.lgofs, 4, g0, g1, &gsL[slot]);
+    };
+#pragma unroll
+    for (int k = 0; k < STAGES - 1; ++k) {
+        const int rk = blockIdx.x + k * G;
+        uint32_t g0, g1;
+        range(rk, g0, g1);
+        if (rk < R) stage(k, rk, g0, g1);
+        dev::cp_async_commit();
+    }
+    uint32_t ng0, ng1;
+    range(blockIdx.x + (STAGES - 1) * G, ng0, ng1);
+    __syncthreads();
+    double acc[kSlots] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    int it = 0;
+    for (int r = blockIdx.x; r < R; r += G, ++it) {
+        const int rn = r + (STAGES - 1) * G;
+        if (rn < R) stage((it + STAGES - 1) % STAGES, rn, ng0, ng1);
+        dev::cp_async_commit();
+        range(rn + G, ng0, ng1);
+        dev::cp_async_wait<STAGES - 1>();
+        __syncthreads();
+        const int cs = it % STAGES;
+        const unsigned char* st = smem_raw + cs * sbytes;
+        const T* prow = reinterpret_cast<const T*>(st);
+        const uint32_t* mrow = reinterpret_cast<const uint32_t*>(st + lay.prow());
+        const uint32_t* brow = mrow + nx;
+        const T* plink = reinterpret_cast<const T*>(st + lay.prow() + 8 * nx);
+        const float* lrow = reinterpret_cast<const float*>(st + lay.prow() + 8 * nx + gcapP);
+        const float* llink = lrow + L::Q * nx;
+        const uint32_t gP = gsP[cs], gL = gsL[cs];
+        const uint32_t rowbase = (uint32_t)r * (uint32_t)nx;
+        const int ni = dev::compact_row(mrow, nx, flist, fcount);
+        const int nf = ni + fcount[1];
+        for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+            const int x = (int)flist[i < ni ? i : nx - nf + i];
+            const uint32_t m = mrow[x];
+            const uint32_t cell = rowbase + (uint32_t)x;
+            const int xm = x == 0 ? nx - 1 : x - 1;
+            const int xp = x == nx - 1 ? 0 : x + 1;
+            float h[L::Q], lt[L::Q];
+#pragma unroll
+            for (int a = 0; a < L::Q; ++a) {
+                const int ex = L::c(a, 0);
+                h[a] = S::cvt(prow[a * nx + (ex > 0 ? xm : (ex < 0 ? xp : x))]);
+                lt[a] = lrow[a * nx + (ex > 0 ? xp : (ex < 0 ? xm : x))];
+            }
+            uint32_t o = 0u, lb = 0u;
+            if (m != 0u) {
+                o = outgoing<L::Q>(m);
+                lb = brow[x];
+#pragma unroll
+                for (int a = 1; a < L::Q; ++a) {
+                    if ((m >> a) & 1u) h[a] = S::cvt(plink[link_slot(lb, o, opposite(a)) - gP]);
+                    if ((o >> a) & 1u) lt[a] = llink[link_slot(lb, o, a) - gL];
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < L::Q; ++a) h[a] *= p.inv_scale;
+            float E[3], wr, wj[3], lam[L::Q], gEc[3];
+            load_E<L, EF>(Ef, p, cell, E);
+            load_weights<L, WIN>(w_rho, w_j, p, cell, wr, wj);
+            adjoint_cell<L, FORCE, WIN>(h, lt, E, p, wr, wj, lam, gEc, acc);
+#pragma unroll
+            for (int b = 0; b < L::Q; ++b) outrow[b * nx + x] = lam[b];
+            if (o) store_lam_links<L>(lamG_out, o, lb, lam);
+            if (gE) {
+#pragma unroll
+                for (int d = 0; d < L::D; ++d) gE[(int64_t)d * p.N + cell] += (double)gEc[d];
+            }
+        }
+        __syncthreads();
+        // lam_t rows out (16-byte stores), re-zeroing the output rows
+        const int qchunks = nx >> 2;
+        for (int k = threadIdx.x; k < lchunks; k += blockDim.x) {
+            const int a = k / qchunks, off = k - a * qchunks;
+            uint4* src = reinterpret_cast<uint4*>(outrow + a * nx) + off;
+            *reinterpret_cast<uint4*>(lam_out + (int64_t)a * p.N + rowbase + 4 * off) = *src;
+            *src = make_uint4(0u, 0u, 0u, 0u);
+        }
+        if (threadIdx.x == 0) fcount[0] = fcount[1] = 0;
+        __syncthreads();
+    }
+    dev::cp_async_wait<0>();
+    block_accumulate(acc, slots, blockIdx.x);
 }
 
 Launch grid_of(const KParams& p) {
@@ -310,6 +548,56 @@ int dispatch_storage(int storage, F&& f) {
     if (storage == LBM_F16_DEV) return f(StoreF16{});
     if (storage == LBM_BF16_DEV) return f(StoreBF16{});
     return f(StoreF32{});
+}
+
+// ---------------------------------------------------------------------------
+// Launch policy of the reverse step: the row-staged kernel when a row of one
+// direction of the state is a multiple of 16 bytes, nx >= 32, nx % 4 == 0 and
+// the stages fit the shared-memory budget; otherwise the general kernel.
+// ---------------------------------------------------------------------------
+constexpr int kAdjStages = 2;
+constexpr int kAdjThreads = 256;
+constexpr size_t kAdjSmemBudget = 200 * 1024;
+
+template <class L, class S, int FORCE, bool EF, bool WIN>
+bool launch_rows(const void* P, const float* lam_in, float* lam_out, const uint32_t* nbr, const float* Ef,
+                 const float* w_rho, const float* w_j, double* gE, double* slots, int64_t slot_blocks,
+                 const KParams& p, cudaStream_t s) {
+    if ((p.nx * S::kBytes) % 16 != 0 || p.nx % 4 != 0 || p.nx < 32) return false;
+    const int gcapP = (int)((((size_t)p.max_row_links * S::kBytes + 15) & ~(size_t)15) + 32);
+    const int gcapL = (int)((((size_t)p.max_row_links * 4 + 15) & ~(size_t)15) + 32);
+    const size_t stage = (size_t)AdjLayout<L, S>{p.nx, gcapP, gcapL}.bytes();
+    const size_t smem = kAdjStages * stage + (size_t)L::Q * p.nx * 4 + 4 * (size_t)p.nx;
+    if (smem > kAdjSmemBudget) return false;
+    const int threads = p.nx >= kAdjThreads ? kAdjThreads : ((p.nx + 31) / 32) * 32;
+    auto kern = k_adjoint_rows<L, S, FORCE, EF, WIN, kAdjStages>;
+    // persistent grid: co-resident blocks per SM (occupancy API) x SMs,
+    // cached per instantiation and shared-memory size
+    static std::mutex mu;
+    static size_t last_smem = 0;
+    static int last_threads = 0, last_blocks = 0;
+    int blocks;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (smem != last_smem || threads != last_threads) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+            last_smem = smem;
+            last_threads = threads;
+            last_blocks = per_sm > 0 ? per_sm * sms : 0;
+        }
+        blocks = last_blocks;
+    }
+    const int rows = p.ny * p.nz;
+    if (blocks > rows) blocks = rows;
+    if (blocks <= 0 || blocks > slot_blocks) return false;
+    kern<<<blocks, threads, smem, s>>>((const typename S::T*)P, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE, slots,
+                                       gcapP, gcapL, p);
+    return true;
 }
 
 }  // namespace
@@ -339,13 +627,19 @@ int launch_adjoint_step(int vel, int storage, int force, bool efield, bool in_wi
                         const float* w_rho, const float* w_j, double* gE, double* slots, const KParams& p,
                         cudaStream_t s) {
     Launch l = grid_of(p);
+    const int64_t slot_blocks = (int64_t)l.grid.x * l.grid.y;
     return dispatch_lattice(vel, [&](auto lat) {
         using L = decltype(lat);
         return dispatch_storage(storage, [&](auto st) {
             using S = decltype(st);
             const auto* Pt = (const typename S::T*)P;
-#define LBM_ADJ(F, EFV, W) \
-    k_adjoint_step<L, S, F, EFV, W><<<l.grid, l.block, 0, s>>>(Pt, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE, slots, p)
+#define LBM_ADJ(F, EFV, W)                                                                                    \
+    do {                                                                                                      \
+        if (!launch_rows<L, S, F, EFV, W>(P, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE, slots, slot_blocks, p, \
+                                          s))                                                                 \
+            k_adjoint_step<L, S, F, EFV, W>                                                                   \
+                <<<l.grid, l.block, 0, s>>>(Pt, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE, slots, p);          \
+    } while (0)
             if (force == LBM_FORCE_SHIFT) {
                 if (efield) {
                     if (in_window) LBM_ADJ(0, true, true); else LBM_ADJ(0, true, false);

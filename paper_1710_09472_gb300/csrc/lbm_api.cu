@@ -178,6 +178,7 @@ lbm::KParams lbm::make_params(const lbm_ctx* c) {
     p.lbase = c->lbase;
     p.rowG = c->rowG;
     p.max_row_links = c->max_row_links;
+    p.lgofs = 0;
     return p;
 }
 
@@ -714,14 +715,19 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
     if (K > T) K = T;
     const int64_t nseg = (T + K - 1) / K;
     const size_t pop_bytes = c->state_bytes;  // populations + link buffer
+    // adjoint field: lam in population layout, then its link buffer (one FP32
+    // per bounce-back link) at a 256-byte aligned offset
     const size_t lam_bytes = sizeof(float) * (size_t)c->Q * (size_t)c->N;
+    const size_t lgofs = (lam_bytes + 255) & ~(size_t)255;
+    const size_t lam_alloc = lgofs + ((sizeof(float) * (size_t)c->n_links + 16 + 255) & ~(size_t)255);
     KParams p = make_params(c);
+    p.lgofs = lgofs;
     const int64_t nslot = lbm::adjoint_slot_count(p);
 
     // --- memory: nseg checkpoints + (K - 1) replay slots + 2 adjoint fields ---
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    const size_t need = (size_t)(nseg + K - 1) * pop_bytes + 2 * lam_bytes + sizeof(double) * (nslot + 8) +
+    const size_t need = (size_t)(nseg + K - 1) * pop_bytes + 2 * lam_alloc + sizeof(double) * (nslot + 8) +
                         sizeof(float) * (size_t)c->N * (1 + c->D);
     if (need > free_b)
         return fail(c, LBM_ERR_OOM, "lbm_adjoint: needs %.2f GB of device memory, %.2f GB free; choose "
@@ -752,8 +758,8 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
     } while (0)
     for (int64_t s = 0; s < nseg; ++s) ADJ_CHECK(cudaMalloc(&ckpt[s], pop_bytes));
     for (int64_t k = 1; k < K; ++k) ADJ_CHECK(cudaMalloc(&seg[k], pop_bytes));
-    ADJ_CHECK(cudaMalloc((void**)&lam[0], lam_bytes));
-    ADJ_CHECK(cudaMalloc((void**)&lam[1], lam_bytes));
+    ADJ_CHECK(cudaMalloc((void**)&lam[0], lam_alloc));
+    ADJ_CHECK(cudaMalloc((void**)&lam[1], lam_alloc));
     ADJ_CHECK(cudaMalloc((void**)&slots, sizeof(double) * nslot));
     ADJ_CHECK(cudaMalloc((void**)&red, sizeof(double) * 8));
     ADJ_CHECK(cudaMemsetAsync(slots, 0, sizeof(double) * nslot, c->stream));

@@ -96,5 +96,62 @@ __device__ __forceinline__ void pull(const typename S::T* __restrict__ P, const 
     }
 }
 
+// 16-byte asynchronous global -> shared copies (cp.async, L2 only).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// e_ay + 1 and e_az + 1 of every direction, 2 bits each, in two 64-bit words
+// (19 directions need 38 bits per word); the unrolled loops fold to constants.
+template <class L>
+__device__ __forceinline__ unsigned long long packed_y() {
+    unsigned long long v = 0;
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) v |= (unsigned long long)(L::c(a, 1) + 1) << (2 * a);
+    return v;
+}
+template <class L>
+__device__ __forceinline__ unsigned long long packed_z() {
+    unsigned long long v = 0;
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) v |= (unsigned long long)(L::c(a, 2) + 1) << (2 * a);
+    return v;
+}
+
+// Compacts the fluid cells of a staged row (link masks mrow[0..nx)) into
+// flist: cells without solid neighbours (mask 0) from the front, cells with
+// bounce-back links from the back (flist[nx - 1], flist[nx - 2], ...), so that
+// a warp taking consecutive entries mostly sees one kind and skips the link
+// code.  counts[0..1] must be zero on entry and receive the two numbers; the
+// call ends with a block barrier and returns counts[0].  blockDim.x must be a
+// multiple of 32.
+__device__ __forceinline__ int compact_row(const uint32_t* mrow, int nx, uint32_t* flist, int* counts) {
+    const unsigned lane = threadIdx.x & 31u, below = (1u << lane) - 1u;
+    for (int x0 = 0; x0 < nx; x0 += blockDim.x) {
+        const int x = x0 + (int)threadIdx.x;
+        const uint32_t m = x < nx ? mrow[x] : kSolidBit;
+        const bool inner = m == 0u;
+        const bool bnd = m != 0u && !(m & kSolidBit);
+        const unsigned bi = __ballot_sync(0xffffffffu, inner), bb = __ballot_sync(0xffffffffu, bnd);
+        int base_i = 0, base_b = 0;
+        if (lane == 0) {
+            if (bi) base_i = atomicAdd(&counts[0], __popc(bi));
+            if (bb) base_b = atomicAdd(&counts[1], __popc(bb));
+        }
+        base_i = __shfl_sync(0xffffffffu, base_i, 0);
+        base_b = __shfl_sync(0xffffffffu, base_b, 0);
+        if (inner) flist[base_i + __popc(bi & below)] = (uint32_t)x;
+        if (bnd) flist[nx - 1 - (base_b + __popc(bb & below))] = (uint32_t)x;
+    }
+    __syncthreads();
+    return counts[0];
+}
+
 }  // namespace dev
 }  // namespace lbm

@@ -147,6 +147,8 @@ struct KParams {
     const uint32_t* lbase;
     const uint32_t* rowG;
     int max_row_links;
+    // byte offset of the link buffer inside an adjoint field (reverse sweep)
+    uint64_t lgofs;
 };
 
 struct Launch {

@@ -333,7 +333,8 @@ __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict
 //    into a ring of STAGES row sets with 16-byte asynchronous copies
 //    (cp.async.cg, L1 bypass), STAGES - 1 rows ahead of the row being computed;
 //  - the row's fluid cells are compacted into a list, so the collision runs on
-//    full warps (solid cells do no work);
+//    full warps (solid cells do no work); cells with bounce-back links are
+//    listed after the others, so most warps skip the link code;
 //  - f_a(x) is read from the ring at x - e_ax (periodic wrap in x is a
 //    shared-memory index); a bounced link reads P_abar(x) from global memory;
 //  - results go into a shared-memory output row set (zero for solid cells),
@@ -440,7 +441,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
     const int sbytes = lay.bytes();
     T* outrow = reinterpret_cast<T*>(smem_raw + STAGES * sbytes);
     uint32_t* flist = reinterpret_cast<uint32_t*>(outrow + L::Q * nx);  // x of the row's fluid cells
-    __shared__ int fcount;
+    __shared__ int fcount[2];  // interior, boundary fluid cells of the row
     __shared__ uint32_t gstart[STAGES];
     T* Gout = reinterpret_cast<T*>(reinterpret_cast<char*>(Pout) + p.gofs);
     const int R = p.ny * p.nz;
@@ -449,7 +450,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
     const int chunks = L::Q << cpr_shift;
     for (int k = threadIdx.x; k < chunks; k += blockDim.x)
         reinterpret_cast<uint4*>(outrow)[k] = make_uint4(0u, 0u, 0u, 0u);
-    if (threadIdx.x == 0) fcount = 0;
+    if (threadIdx.x == 0) fcount[0] = fcount[1] = 0;
     auto range = [&](int row, uint32_t& g0, uint32_t& g1) {
         g0 = g1 = 0u;
         if (row < R) {
@@ -484,30 +485,20 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
         const T* lbuf = lay.links(st);
         const uint32_t g_base = gstart[it % STAGES];
         const uint32_t rowbase = (uint32_t)r * (uint32_t)nx;
-        // compact the row's fluid cells (warp ballots, one shared atomic per warp)
-        for (int x0 = 0; x0 < nx; x0 += blockDim.x) {
-            const int x = x0 + threadIdx.x;
-            const bool fluid = x < nx && !(mrow[x] & kSolidBit);
-            const unsigned ball = __ballot_sync(0xffffffffu, fluid);
-            int base = 0;
-            if ((threadIdx.x & 31) == 0 && ball) base = atomicAdd(&fcount, __popc(ball));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (fluid) flist[base + __popc(ball & ((1u << (threadIdx.x & 31)) - 1u))] = (uint32_t)x;
-        }
-        __syncthreads();  // list complete
-        const int nf = fcount;
+        const int ni = dev::compact_row(mrow, nx, flist, fcount);
+        const int nf = ni + fcount[1];
         Cell c;
         c.y = r % p.ny;
         c.z = r / p.ny;
         for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-            const int x = (int)flist[i];
+            const int x = (int)flist[i < ni ? i : nx - nf + i];
             const uint32_t m = mrow[x];
             c.x = x;
             c.cell = rowbase + (uint32_t)x;
             const int xm = x == 0 ? nx - 1 : x - 1;
             const int xp = x == nx - 1 ? 0 : x + 1;
             const uint32_t o = outgoing<L::Q>(m);
-            const uint32_t lb = brow[x];
+            const uint32_t lb = m ? brow[x] : 0u;
             float h[L::Q];
 #pragma unroll
             for (int a = 0; a < L::Q; ++a) {
@@ -547,7 +538,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
             *reinterpret_cast<uint4*>(dst) = *src;
             *src = make_uint4(0u, 0u, 0u, 0u);
         }
-        if (threadIdx.x == 0) fcount = 0;
+        if (threadIdx.x == 0) fcount[0] = fcount[1] = 0;
         __syncthreads();  // list, counter and stage slot free for reuse
     }
     cp_async_wait<0>();

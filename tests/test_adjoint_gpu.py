@@ -21,13 +21,18 @@ def _built():
     build()
 
 
-def _case(vel):
+# nx a multiple of 4 (and of 16 bytes per row) takes the row-staged reverse
+# kernel; a ragged nx takes the general one.
+SHAPES = {("D2V9", "staged"): (14, 40), ("D2V9", "general"): (14, 38),
+          ("D3V19", "staged"): (6, 7, 36), ("D3V19", "general"): (6, 7, 35)}
+
+
+def _case(vel, layout="staged"):
+    shape = SHAPES[(vel, layout)]
     if vel == "D2V9":
-        shape = (14, 40)
         mask, _ = wl.boolean_obstacles(shape, 2.5, 0.8, seed=81)
         B = (0.0, 0.0, 2e-2)
     else:
-        shape = (6, 7, 36)
         mask, _ = wl.boolean_obstacles(shape, 1.5, 0.8, seed=82)
         B = (1e-2, -2e-2, 3e-2)
     D = len(shape)
@@ -52,17 +57,7 @@ def _gpu_sim(vel, shape, mask, B, Ef, rho0, u0, tau, force, storage="f32"):
     return sim
 
 
-@pytest.mark.parametrize("vel", ["D2V9", "D3V19"])
-@pytest.mark.parametrize("force", ["term", "shift"])
-def test_adjoint_matches_oracle(vel, force):
-    shape, mask, B, Ef, rho0, u0, wr, wj = _case(vel)
-    tau, T, tb = 0.75, 14, 6
-    sim = _gpu_sim(vel, shape, mask, B, Ef, rho0, u0, tau, force)
-    D, Q, N = sim.D, sim.Q, sim.N
-    dE = torch.empty(D * N, dtype=torch.float64, device="cuda")
-    lam0 = torch.empty(Q * N, dtype=torch.float32, device="cuda")
-    res = sim.adjoint(tb, T, torch.from_numpy(wr.reshape(-1)).cuda(), torch.from_numpy(wj.reshape(-1)).cuda(),
-                      checkpoint_every=4, dL_dE=dE, dL_df0=lam0)
+def _compare(sim, res, dE, lam0, vel, shape, mask, B, Ef, rho0, u0, wr, wj, tau, T, tb, force):
     m = oracle.Model(vel, "fd", THETA, 1.0, tau=tau, B=B, force=force)
     f0 = m.init_equilibrium(shape, mask, rho0.astype(np.float64), u0.astype(np.float64))
     states = m.trajectory(shape, mask, f0, T, Ef.astype(np.float64))
@@ -75,6 +70,47 @@ def test_adjoint_matches_oracle(vel, force):
     for c in comps:
         assert abs(res["dL_dB"][c] - ref["gB"][c]) < 1e-4 * max(abs(ref["gB"][c]), 1e-2 * np.abs(ref["gB"]).max())
     assert abs(res["dL_dtau"] / ref["gtau"] - 1) < 1e-4
+
+
+@pytest.mark.parametrize("vel", ["D2V9", "D3V19"])
+@pytest.mark.parametrize("force", ["term", "shift"])
+@pytest.mark.parametrize("layout", ["staged", "general"])
+def test_adjoint_matches_oracle(vel, force, layout):
+    shape, mask, B, Ef, rho0, u0, wr, wj = _case(vel, layout)
+    tau, T, tb = 0.75, 14, 6
+    sim = _gpu_sim(vel, shape, mask, B, Ef, rho0, u0, tau, force)
+    D, Q, N = sim.D, sim.Q, sim.N
+    dE = torch.empty(D * N, dtype=torch.float64, device="cuda")
+    lam0 = torch.empty(Q * N, dtype=torch.float32, device="cuda")
+    res = sim.adjoint(tb, T, torch.from_numpy(wr.reshape(-1)).cuda(), torch.from_numpy(wj.reshape(-1)).cuda(),
+                      checkpoint_every=4, dL_dE=dE, dL_df0=lam0)
+    _compare(sim, res, dE, lam0, vel, shape, mask, B, Ef, rho0, u0, wr, wj, tau, T, tb, force)
+    sim.close()
+
+
+@pytest.mark.parametrize("force", ["term", "shift"])
+def test_adjoint_many_rows_porous_3d(force):
+    """More rows (20 x 24 = 480) than a persistent grid has blocks, so each
+    block of the row-staged reverse kernel cycles its stage ring; porous
+    geometry with many bounce-back links per row."""
+    shape = (20, 24, 32)
+    mask, _ = wl.boolean_obstacles(shape, 2.0, 0.75, seed=97)
+    B = (2e-2, -1e-2, 3e-2)
+    D, N = 3, mask.size
+    Ef = np.zeros((D,) + shape, dtype=np.float32)
+    Ef[0] = (1e-3 + 2e-4 * wl.normal(98, N)).reshape(shape)
+    Ef[2] = (3e-4 * wl.normal(99, N)).reshape(shape)
+    rho0 = (1.0 + 0.02 * wl.uniform01(100, N)).reshape(shape).astype(np.float32)
+    u0 = (0.01 * wl.normal(101, D * N)).reshape((D,) + shape).astype(np.float32)
+    wr = wl.normal(102, N).reshape(shape).astype(np.float32)
+    wj = wl.normal(103, D * N).reshape((D,) + shape).astype(np.float32)
+    tau, T, tb = 0.8, 9, 3
+    sim = _gpu_sim("D3V19", shape, mask, B, Ef, rho0, u0, tau, force)
+    dE = torch.empty(D * N, dtype=torch.float64, device="cuda")
+    lam0 = torch.empty(sim.Q * N, dtype=torch.float32, device="cuda")
+    res = sim.adjoint(tb, T, torch.from_numpy(wr.reshape(-1)).cuda(), torch.from_numpy(wj.reshape(-1)).cuda(),
+                      checkpoint_every=3, dL_dE=dE, dL_df0=lam0)
+    _compare(sim, res, dE, lam0, "D3V19", shape, mask, B, Ef, rho0, u0, wr, wj, tau, T, tb, force)
     sim.close()
 
 
