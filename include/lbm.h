@@ -60,7 +60,11 @@ typedef enum {
     LBM_ERR_CUDA = 3,             /* a CUDA runtime call failed; see lbm_last_error */
     LBM_ERR_OOM = 4,              /* device or host allocation failed */
     LBM_ERR_NONFINITE = 5,        /* a NaN/Inf appeared in a reduction */
-    LBM_ERR_TIMEOUT = 6,          /* reserved: no call waits on the device without a bound */
+    LBM_ERR_TIMEOUT = 6,          /* a kernel's bounded wait on its own asynchronous copies ran
+                                     out (about 1 s); reported by the next synchronising call
+                                     (lbm_moments with totals or host outputs, lbm_get_populations,
+                                     lbm_window_totals, lbm_adjoint, lbm_save_state); the state
+                                     is then invalid */
     LBM_ERR_STATE = 7             /* call out of order (e.g. step before init) */
 } lbm_status;
 

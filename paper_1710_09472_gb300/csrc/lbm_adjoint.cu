@@ -36,7 +36,8 @@ using dev::cross3;
 using dev::edot;
 using dev::kBlock;
 using dev::warp_sum;
-constexpr int kSlots = 5;  // gB[3], gtau, loss
+constexpr int kSlots = 5;         // gB[3], gtau, loss
+constexpr int kAdjMaxChunks = 64;  // nx <= 2048 for the row-staged reverse step
 
 // Adds the block's sums of acc[kSlots] into slots[block * kSlots + k].
 __device__ __forceinline__ void block_accumulate(double* acc, double* __restrict__ slots, int64_t block) {
@@ -347,79 +348,112 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(
 // One stage holds, for the row (y, z):
 //   - the Q pull rows of the forward state P_t: direction a from row
 //     (y - e_ay, z - e_az), read at x - e_ax;
-//   - the row's link masks and first link slots;
+//   - the row's link masks;
 //   - its window of P_t's link buffer (bounced pulls);
 //   - the Q gather rows of lam_{t+1}: direction a from row
 //     (y + e_ay, z + e_az), read at x + e_ax;
-//   - its window of lam_{t+1}'s link buffer (bounced gathers).
-// Stages are filled by cp.async while earlier rows compute; fluid cells are
-// compacted; lam_t goes through shared-memory output rows (zero for solid
-// cells) and is written with 16-byte vector stores.  dL/dB, dL/dtau and the
-// loss stay in registers until the block's single reduction at the end.
+//   - its windows of lam_{t+1}'s link buffer (bounced gathers) and of the
+//     link descriptors;
+// all by bulk asynchronous copies issued by warp 0, completing on the
+// stage's mbarrier (bounded waits, as in the forward's row-staged kernel).
+// One pass over the row's links patches both bounced reads into the staged
+// rows (the solid neighbour's slot, read by that cell alone), so cells read
+// their rows without link logic; fluid cells are compacted; lam_t goes
+// through shared-memory output rows (zeros for solid cells) that leave by
+// bulk stores, and one pass over the links copies lam_bbar(x) into the row's
+// range of the new link buffer.  dL/dB, dL/dtau and the loss stay in
+// registers until the block's single reduction at the end.
 // ---------------------------------------------------------------------------
 template <class L, class S>
 struct AdjLayout {
-    int nx, gcapP, gcapL;
+    int nx, gcapP, gcapL;  // gcapL also bounds the descriptor window (4-byte elements)
     __device__ __host__ int prow() const { return L::Q * nx * S::kBytes; }
     __device__ __host__ int lrow() const { return L::Q * nx * 4; }
-    __device__ __host__ int bytes() const { return prow() + 8 * nx + gcapP + lrow() + gcapL; }
+    __device__ __host__ int bytes() const { return prow() + 4 * nx + gcapP + lrow() + 2 * gcapL; }
+    __device__ unsigned char* masks(unsigned char* st) const { return st + prow(); }
+    __device__ unsigned char* plinks(unsigned char* st) const { return st + prow() + 4 * nx; }
+    __device__ unsigned char* lrows(unsigned char* st) const { return st + prow() + 4 * nx + gcapP; }
+    __device__ unsigned char* llinks(unsigned char* st) const { return lrows(st) + lrow(); }
+    __device__ unsigned char* descs(unsigned char* st) const { return llinks(st) + gcapL; }
 };
 
-// Rows of every direction, elements of `esize` bytes: direction a from row
-// (y + s e_ay, z + s e_az), periodic; one warp per direction at a time.
-template <class L>
-__device__ __forceinline__ void stage_dir_rows(unsigned char* dst, const unsigned char* base, int esize, int s, int y,
-                                               int z, const KParams& p) {
-    const unsigned long long kPy = dev::packed_y<L>(), kPz = dev::packed_z<L>();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int row_bytes = p.nx * esize, chunks = row_bytes >> 4;
-    for (int a = warp; a < L::Q; a += nwarps) {
-        const int ey = (int)((kPy >> (2 * a)) & 3ull) - 1, ez = (int)((kPz >> (2 * a)) & 3ull) - 1;
-        int ys = y + s * ey, zs = z + s * ez;
-        ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
-        zs = zs < 0 ? zs + p.nz : (zs >= p.nz ? zs - p.nz : zs);
-        const unsigned char* src = base + ((int64_t)a * p.N + ((int64_t)zs * p.ny + ys) * p.nx) * esize;
-        unsigned char* d = dst + a * row_bytes;
-        for (int k = lane; k < chunks; k += 32) dev::cp_async16(d + 16 * k, src + 16 * k);
+// Issued by warp 0: the bulk copies of row `row` into stage `st` (lane 0 arms
+// the barrier with the byte count; lane a copies pull row a and gather row a;
+// four more lanes take the masks and the three windows).
+template <class L, class S>
+__device__ __forceinline__ void adj_stage(unsigned char* st, const AdjLayout<L, S>& lay, uint64_t* bar,
+                                          const typename S::T* P, const float* lam, const uint32_t* nbr, int row,
+                                          uint32_t g0, uint32_t g1, uint32_t* ws, const KParams& p) {
+    static_assert(L::Q + 4 <= 32, "one lane per direction");
+    const int lane = threadIdx.x & 31;
+    const uint32_t prb = (uint32_t)p.nx * S::kBytes, lrb = (uint32_t)p.nx * 4u;
+    uint64_t pb0, pb1, lb0, lb1;
+    dev::window_bytes(g0, g1, S::kBytes, pb0, pb1);
+    dev::window_bytes(g0, g1, 4, lb0, lb1);
+    if (lane == 0) {
+        // window starts first: the arrive releases them to the waiting threads
+        ws[0] = (uint32_t)(pb0 / S::kBytes);
+        ws[1] = (uint32_t)(lb0 / 4);  // the lam-link and descriptor windows start at the same element
+        dev::mbar_expect_tx(bar, L::Q * (prb + lrb) + 4u * (uint32_t)p.nx + (uint32_t)(pb1 - pb0) +
+                                     2u * (uint32_t)(lb1 - lb0));
     }
-}
-
-// Link slots [g0, g1) of elements of `esize` bytes, as a 16-byte aligned window
-// whose first element index goes to *gstart.
-__device__ __forceinline__ void stage_window(unsigned char* dst, const unsigned char* base, int esize, uint32_t g0,
-                                             uint32_t g1, uint32_t* gstart) {
-    const uint64_t b0 = ((uint64_t)g0 * esize) & ~15ull;
-    const uint64_t b1 = ((uint64_t)g1 * esize + 15ull) & ~15ull;
-    for (int k = threadIdx.x; k < (int)((b1 - b0) >> 4); k += blockDim.x)
-        dev::cp_async16(dst + 16 * k, base + b0 + 16 * (uint64_t)k);
-    if (threadIdx.x == 0) *gstart = (uint32_t)(b0 / esize);
+    __syncwarp();
+    if (lane < L::Q) {
+        const unsigned long long kPy = dev::packed_y<L>(), kPz = dev::packed_z<L>();
+        const int a = lane;
+        const int ey = (int)((kPy >> (2 * a)) & 3ull) - 1, ez = (int)((kPz >> (2 * a)) & 3ull) - 1;
+        const int y = row % p.ny, z = row / p.ny;
+        // pull row (y - e_ay, z - e_az) of P_t, gather row (y + e_ay, z + e_az) of lam_{t+1}
+        int ysP = y - ey, zsP = z - ez, ysL = y + ey, zsL = z + ez;
+        ysP = ysP < 0 ? ysP + p.ny : (ysP >= p.ny ? ysP - p.ny : ysP);
+        zsP = zsP < 0 ? zsP + p.nz : (zsP >= p.nz ? zsP - p.nz : zsP);
+        ysL = ysL < 0 ? ysL + p.ny : (ysL >= p.ny ? ysL - p.ny : ysL);
+        zsL = zsL < 0 ? zsL + p.nz : (zsL >= p.nz ? zsL - p.nz : zsL);
+        dev::bulk_load(st + a * prb, P + (int64_t)a * p.N + ((int64_t)zsP * p.ny + ysP) * p.nx, prb, bar);
+        dev::bulk_load(lay.lrows(st) + a * lrb, lam + (int64_t)a * p.N + ((int64_t)zsL * p.ny + ysL) * p.nx, lrb,
+                       bar);
+    } else if (lane == L::Q) {
+        dev::bulk_load(lay.masks(st), nbr + (int64_t)row * p.nx, 4u * (uint32_t)p.nx, bar);
+    } else if (lane == L::Q + 1) {
+        if (pb1 > pb0)
+            dev::bulk_load(lay.plinks(st), reinterpret_cast<const unsigned char*>(P) + p.gofs + pb0,
+                           (uint32_t)(pb1 - pb0), bar);
+    } else if (lane == L::Q + 2) {
+        if (lb1 > lb0)
+            dev::bulk_load(lay.llinks(st), reinterpret_cast<const unsigned char*>(lam) + p.lgofs + lb0,
+                           (uint32_t)(lb1 - lb0), bar);
+    } else if (lane == L::Q + 3) {
+        if (lb1 > lb0)
+            dev::bulk_load(lay.descs(st), reinterpret_cast<const unsigned char*>(p.ldesc) + lb0,
+                           (uint32_t)(lb1 - lb0), bar);
+    }
 }
 
 template <class L, class S, int FORCE, bool EF, bool WIN, int STAGES>
 __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __restrict__ P,
-                                                      const float* __restrict__ lam_in, float* __restrict__ lam_out,
-                                                      const uint32_t* __restrict__ nbr, const float* __restrict__ Ef,
-                                                      const float* __restrict__ w_rho, const float* __restrict__ w_j,
-                                                      double* __restrict__ gE, double* __restrict__ slots, int gcapP,
-                                                      int gcapL, KParams p) {
+                                                         const float* __restrict__ lam_in,
+                                                         float* __restrict__ lam_out,
+                                                         const uint32_t* __restrict__ nbr,
+                                                         const float* __restrict__ Ef,
+                                                         const float* __restrict__ w_rho,
+                                                         const float* __restrict__ w_j, double* __restrict__ gE,
+                                                         double* __restrict__ slots, int gcapP, int gcapL, KParams p) {
     using T = typename S::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int nx = p.nx;
     const AdjLayout<L, S> lay{nx, gcapP, gcapL};
     const int sbytes = lay.bytes();
     float* outrow = reinterpret_cast<float*>(smem_raw + STAGES * sbytes);
     uint32_t* flist = reinterpret_cast<uint32_t*>(outrow + L::Q * nx);
-    __shared__ int fcount[2];  // interior, boundary fluid cells of the row
-    __shared__ uint32_t gsP[STAGES], gsL[STAGES];
-    const unsigned char* Pb = reinterpret_cast<const unsigned char*>(P);
-    const unsigned char* Lb = reinterpret_cast<const unsigned char*>(lam_in);
+    __shared__ __align__(8) uint64_t bar[STAGES];
+    __shared__ int wcnt[kAdjMaxChunks];  // fluid cells per 32-cell chunk of the row
+    __shared__ int nfluid;
+    __shared__ uint32_t wstart[STAGES][2];
     float* lamG_out = link_part(lam_out, p);
     const int R = p.ny * p.nz;
     const int G = gridDim.x;
-    const int lchunks = (L::Q * nx * 4) >> 4;
-    for (int k = threadIdx.x; k < lchunks; k += blockDim.x)
-        reinterpret_cast<uint4*>(outrow)[k] = make_uint4(0u, 0u, 0u, 0u);
-    if (threadIdx.x == 0) fcount[0] = fcount[1] = 0;
+    const bool leader = threadIdx.x == 0;
+    const bool warp0 = threadIdx.x < 32;
     auto range = [&](int row, uint32_t& g0, uint32_t& g1) {
         g0 = g1 = 0u;
         if (row < R) {
@@ -427,105 +461,102 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
             g1 = __ldg(p.rowG + row + 1);
         }
     };
-    auto stage = [&](int slot, int row, uint32_t g0, uint32_t g1) {
-        unsigned char* st = smem_raw + slot * sbytes;
-        const int y = row % p.ny, z = row / p.ny;
-        stage_dir_rows<L>(st, Pb, S::kBytes, -1, y, z, p);
-        unsigned char* mb = st + lay.prow();
-        const int wchunks = nx >> 2;
-        for (int k = threadIdx.x; k < 2 * wchunks; k += blockDim.x) {
-            if (k < wchunks)
-                dev::cp_async16(mb + 16 * k, nbr + (int64_t)row * nx + 4 * k);
-            else
-                dev::cp_async16(mb + 4 * nx + 16 * (k - wchunks), p.lbase + (int64_t)row * nx + 4 * (k - wchunks));
-        }
-        stage_window(mb + 8 * nx, Pb + p.gofs, S::kBytes, g0, g1, &gsP[slot]);
-        unsigned char* lr = mb + 8 * nx + gcapP;
-        stage_dir_rows<L>(lr, Lb, 4, +1, y, z, p);
-        stage_window(lr + lay.lrow(), Lb + p.lgofs, 4, g0, g1, &gsL[slot]);
-    };
+    if (leader) {
 #pragma unroll
-    for (int k = 0; k < STAGES - 1; ++k) {
-        const int rk = blockIdx.x + k * G;
-        uint32_t g0, g1;
-        range(rk, g0, g1);
-        if (rk < R) stage(k, rk, g0, g1);
-        dev::cp_async_commit();
+        for (int k = 0; k < STAGES; ++k) dev::mbar_init(&bar[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    uint32_t ng0, ng1;
-    range(blockIdx.x + (STAGES - 1) * G, ng0, ng1);
     __syncthreads();
+    if (warp0) {
+#pragma unroll
+        for (int k = 0; k < STAGES - 1; ++k) {
+            const int rk = blockIdx.x + k * G;
+            if (rk < R) {
+                uint32_t g0, g1;
+                range(rk, g0, g1);
+                adj_stage<L, S>(smem_raw + k * sbytes, lay, &bar[k], P, lam_in, nbr, rk, g0, g1, wstart[k], p);
+            }
+        }
+    }
     double acc[kSlots] = {0.0, 0.0, 0.0, 0.0, 0.0};
     int it = 0;
+    bool ok = true;  // false once a wait has run out: no further waits
     for (int r = blockIdx.x; r < R; r += G, ++it) {
-        const int rn = r + (STAGES - 1) * G;
-        if (rn < R) stage((it + STAGES - 1) % STAGES, rn, ng0, ng1);
-        dev::cp_async_commit();
-        range(rn + G, ng0, ng1);
-        dev::cp_async_wait<STAGES - 1>();
-        __syncthreads();
         const int cs = it % STAGES;
-        const unsigned char* st = smem_raw + cs * sbytes;
-        const T* prow = reinterpret_cast<const T*>(st);
-        const uint32_t* mrow = reinterpret_cast<const uint32_t*>(st + lay.prow());
-        const uint32_t* brow = mrow + nx;
-        const T* plink = reinterpret_cast<const T*>(st + lay.prow() + 8 * nx);
-        const float* lrow = reinterpret_cast<const float*>(st + lay.prow() + 8 * nx + gcapP);
-        const float* llink = lrow + L::Q * nx;
-        const uint32_t gP = gsP[cs], gL = gsL[cs];
+        uint32_t g0, g1;
+        range(r, g0, g1);
+        if (ok && !dev::mbar_wait(&bar[cs], (uint32_t)(it / STAGES) & 1u)) {
+            ok = false;
+            if (p.status) atomicExch(p.status, 2);
+        }
+        unsigned char* st = smem_raw + cs * sbytes;
+        T* prow = reinterpret_cast<T*>(st);
+        float* lrow = reinterpret_cast<float*>(lay.lrows(st));
+        const uint32_t* desc = reinterpret_cast<const uint32_t*>(lay.descs(st));
+        const uint32_t d0 = wstart[cs][1];
+        // ascending-x compaction: each thread's FP64 sums then see the same
+        // cells in the same order on every run
+        dev::compact_fluid_ordered(reinterpret_cast<const uint32_t*>(lay.masks(st)), nx, flist, wcnt, &nfluid);
+        dev::patch_links<L, true>(prow, nx, reinterpret_cast<const T*>(lay.plinks(st)), wstart[cs][0], g0, g1, desc,
+                                  d0);
+        dev::patch_links<L, false>(lrow, nx, reinterpret_cast<const float*>(lay.llinks(st)), d0, g0, g1, desc, d0);
+        if (warp0) dev::bulk_wait_read();  // the previous row's bulk stores have read the output rows
+        __syncthreads();  // list complete, bounced values in place, output rows free
+        if (warp0) {
+            // refill the stage of the previous row (every thread is past its reads of it)
+            const int rn = r + (STAGES - 1) * G;
+            if (rn < R) {
+                const int sn = (it + STAGES - 1) % STAGES;
+                uint32_t n0, n1;
+                range(rn, n0, n1);
+                adj_stage<L, S>(smem_raw + sn * sbytes, lay, &bar[sn], P, lam_in, nbr, rn, n0, n1, wstart[sn], p);
+            }
+        }
+        const int nf = nfluid;
         const uint32_t rowbase = (uint32_t)r * (uint32_t)nx;
-        const int ni = dev::compact_row(mrow, nx, flist, fcount);
-        const int nf = ni + fcount[1];
-        for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-            const int x = (int)flist[i < ni ? i : nx - nf + i];
-            const uint32_t m = mrow[x];
-            const uint32_t cell = rowbase + (uint32_t)x;
-            const int xm = x == 0 ? nx - 1 : x - 1;
-            const int xp = x == nx - 1 ? 0 : x + 1;
-            float h[L::Q], lt[L::Q];
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const int x = (int)flist[i];
+            if (i < nf) {
+                const uint32_t cell = rowbase + (uint32_t)x;
+                const int xm = x == 0 ? nx - 1 : x - 1;
+                const int xp = x == nx - 1 ? 0 : x + 1;
+                float h[L::Q], lt[L::Q];
 #pragma unroll
-            for (int a = 0; a < L::Q; ++a) {
-                const int ex = L::c(a, 0);
-                h[a] = S::cvt(prow[a * nx + (ex > 0 ? xm : (ex < 0 ? xp : x))]);
-                lt[a] = lrow[a * nx + (ex > 0 ? xp : (ex < 0 ? xm : x))];
-            }
-            uint32_t o = 0u, lb = 0u;
-            if (m != 0u) {
-                o = outgoing<L::Q>(m);
-                lb = brow[x];
-#pragma unroll
-                for (int a = 1; a < L::Q; ++a) {
-                    if ((m >> a) & 1u) h[a] = S::cvt(plink[link_slot(lb, o, opposite(a)) - gP]);
-                    if ((o >> a) & 1u) lt[a] = llink[link_slot(lb, o, a) - gL];
+                for (int a = 0; a < L::Q; ++a) {
+                    const int ex = L::c(a, 0);
+                    h[a] = S::cvt(prow[a * nx + (ex > 0 ? xm : (ex < 0 ? xp : x))]) * p.inv_scale;
+                    lt[a] = lrow[a * nx + (ex > 0 ? xp : (ex < 0 ? xm : x))];
                 }
-            }
+                float E[3], wr, wj[3], lam[L::Q], gEc[3];
+                load_E<L, EF>(Ef, p, cell, E);
+                load_weights<L, WIN>(w_rho, w_j, p, cell, wr, wj);
+                adjoint_cell<L, FORCE, WIN>(h, lt, E, p, wr, wj, lam, gEc, acc);
 #pragma unroll
-            for (int a = 0; a < L::Q; ++a) h[a] *= p.inv_scale;
-            float E[3], wr, wj[3], lam[L::Q], gEc[3];
-            load_E<L, EF>(Ef, p, cell, E);
-            load_weights<L, WIN>(w_rho, w_j, p, cell, wr, wj);
-            adjoint_cell<L, FORCE, WIN>(h, lt, E, p, wr, wj, lam, gEc, acc);
+                for (int b = 0; b < L::Q; ++b) outrow[b * nx + x] = lam[b];
+                if (gE) {
 #pragma unroll
-            for (int b = 0; b < L::Q; ++b) outrow[b * nx + x] = lam[b];
-            if (o) store_lam_links<L>(lamG_out, o, lb, lam);
-            if (gE) {
+                    for (int d = 0; d < L::D; ++d) gE[(int64_t)d * p.N + cell] += (double)gEc[d];
+                }
+            } else {
 #pragma unroll
-                for (int d = 0; d < L::D; ++d) gE[(int64_t)d * p.N + cell] += (double)gEc[d];
+                for (int b = 0; b < L::Q; ++b) outrow[b * nx + x] = 0.f;
             }
         }
-        __syncthreads();
-        // lam_t rows out (16-byte stores), re-zeroing the output rows
-        const int qchunks = nx >> 2;
-        for (int k = threadIdx.x; k < lchunks; k += blockDim.x) {
-            const int a = k / qchunks, off = k - a * qchunks;
-            uint4* src = reinterpret_cast<uint4*>(outrow + a * nx) + off;
-            *reinterpret_cast<uint4*>(lam_out + (int64_t)a * p.N + rowbase + 4 * off) = *src;
-            *src = make_uint4(0u, 0u, 0u, 0u);
+        dev::fence_proxy_async();
+        __syncthreads();  // output rows complete
+        if (threadIdx.x < L::Q) {
+            // lane a of warp 0: the bulk store of direction a, in its own group
+            const int a = threadIdx.x;
+            dev::bulk_store(lam_out + (int64_t)a * p.N + rowbase, outrow + a * nx, (uint32_t)nx * 4u);
+            dev::bulk_commit();
         }
-        if (threadIdx.x == 0) fcount[0] = fcount[1] = 0;
-        __syncthreads();
+        // link copies of lam_t: slot k of (x, b) takes lam_bbar(x)
+        for (uint32_t k = g0 + threadIdx.x; k < g1; k += blockDim.x) {
+            const uint32_t d = desc[k - d0];
+            lamG_out[k] = outrow[opposite((int)(d >> 24)) * nx + (int)(d & 0xFFFFFFu)];
+        }
     }
-    dev::cp_async_wait<0>();
+    if (warp0) dev::bulk_wait_all();
     block_accumulate(acc, slots, blockIdx.x);
 }
 
@@ -563,9 +594,9 @@ template <class L, class S, int FORCE, bool EF, bool WIN>
 bool launch_rows(const void* P, const float* lam_in, float* lam_out, const uint32_t* nbr, const float* Ef,
                  const float* w_rho, const float* w_j, double* gE, double* slots, int64_t slot_blocks,
                  const KParams& p, cudaStream_t s) {
-    if ((p.nx * S::kBytes) % 16 != 0 || p.nx % 4 != 0 || p.nx < 32) return false;
-    const int gcapP = (int)((((size_t)p.max_row_links * S::kBytes + 15) & ~(size_t)15) + 32);
-    const int gcapL = (int)((((size_t)p.max_row_links * 4 + 15) & ~(size_t)15) + 32);
+    if ((p.nx * S::kBytes) % 16 != 0 || p.nx % 4 != 0 || p.nx < 32 || p.nx > 32 * kAdjMaxChunks) return false;
+    const int gcapP = dev::window_cap(p.max_row_links, S::kBytes);
+    const int gcapL = dev::window_cap(p.max_row_links, 4);
     const size_t stage = (size_t)AdjLayout<L, S>{p.nx, gcapP, gcapL}.bytes();
     const size_t smem = kAdjStages * stage + (size_t)L::Q * p.nx * 4 + 4 * (size_t)p.nx;
     if (smem > kAdjSmemBudget) return false;

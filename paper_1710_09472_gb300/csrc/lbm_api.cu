@@ -128,6 +128,16 @@ lbm_status cuda_check(lbm_ctx* c, cudaError_t e, const char* what) {
         if (_st != LBM_OK) return _st;                        \
     } while (0)
 
+// After a stream synchronisation: a kernel whose bounded wait ran out has
+// written a nonzero code into the mapped status word; report it once.
+lbm_status device_status(lbm_ctx* c) {
+    volatile int* w = c->status_host;
+    if (!w || *w == 0) return LBM_OK;
+    const int code = *w;
+    *w = 0;
+    return fail(c, LBM_ERR_TIMEOUT, "a device-side wait ran out (code %d); the state is invalid", code);
+}
+
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -177,8 +187,10 @@ lbm::KParams lbm::make_params(const lbm_ctx* c) {
     p.gofs = c->gofs;
     p.lbase = c->lbase;
     p.rowG = c->rowG;
+    p.ldesc = c->ldesc;
     p.max_row_links = c->max_row_links;
     p.lgofs = 0;
+    p.status = c->status_dev;
     return p;
 }
 
@@ -249,6 +261,13 @@ lbm_status build_links_and_state(lbm_ctx* c) {
     int mx = 0;
     for (int64_t r = 0; r < R; ++r) mx = std::max(mx, (int)(rowG[r + 1] - rowG[r]));
     c->max_row_links = mx;
+    // link descriptors (x | b << 24), one per slot
+    cudaFree(c->ldesc);
+    c->ldesc = nullptr;
+    LBM_CUDA(c, cudaMalloc((void**)&c->ldesc, sizeof(uint32_t) * ((size_t)c->n_links + 4)));
+    p.ldesc = c->ldesc;
+    c->launches += lbm::launch_build_link_desc(c->lat.vel, c->nbr, c->lbase, c->ldesc, p, c->stream);
+    LBM_CUDA(c, cudaGetLastError());
     const size_t eb = pop_elem_bytes(c->storage);
     const size_t pbytes = (size_t)c->Q * (size_t)c->N * eb;
     c->gofs = (pbytes + 255) & ~(size_t)255;
@@ -395,7 +414,11 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_lattice* lat, const int64_t dims[
         (st = cuda_check(c, cudaMalloc((void**)&c->count_dev, sizeof(unsigned long long)), "cudaMalloc count")) !=
             LBM_OK ||
         (st = cuda_check(c, cudaMallocHost((void**)&c->totals_host, sizeof(double) * 4), "cudaMallocHost")) !=
-            LBM_OK) {
+            LBM_OK ||
+        (st = cuda_check(c, cudaHostAlloc((void**)&c->status_host, sizeof(int), cudaHostAllocMapped),
+                         "cudaHostAlloc status")) != LBM_OK ||
+        (st = cuda_check(c, cudaHostGetDevicePointer((void**)&c->status_dev, c->status_host, 0),
+                         "status device pointer")) != LBM_OK) {
         lbm_destroy(c);
         return st;
     }
@@ -424,6 +447,7 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->nbr);
     cudaFree(c->lbase);
     cudaFree(c->rowG);
+    cudaFree(c->ldesc);
     cudaFree(c->mask_dev);
     cudaFree(c->Efield);
     cudaFree(c->partials);
@@ -431,6 +455,7 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->count_dev);
     cudaFree(c->stage);
     if (c->totals_host) cudaFreeHost(c->totals_host);
+    if (c->status_host) cudaFreeHost(c->status_host);
     delete c;
 }
 
@@ -583,6 +608,10 @@ lbm_status lbm_moments(lbm_ctx* c, float* rho, float* j, double* total_rho, doub
     if (j_host)
         LBM_CUDA(c, cudaMemcpyAsync(j, j_d, sizeof(float) * nN * c->D, cudaMemcpyDeviceToHost, c->stream));
     if (want_totals || rho_host || j_host) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (want_totals || rho_host || j_host) {
+        lbm_status _ds = device_status(c);
+        if (_ds != LBM_OK) return _ds;
+    }
     if (want_totals) {
         for (int k = 0; k < 4; ++k)
             if (!std::isfinite(c->totals_host[k])) return fail(c, LBM_ERR_NONFINITE, "non-finite total moment");
@@ -611,6 +640,10 @@ lbm_status lbm_get_populations(lbm_ctx* c, float* f, int deviation) {
     if (host) {
         LBM_CUDA(c, cudaMemcpyAsync(f, fd, bytes, cudaMemcpyDeviceToHost, c->stream));
         LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+        {
+            lbm_status _ds = device_status(c);
+            if (_ds != LBM_OK) return _ds;
+        }
     }
     return LBM_OK;
 }
@@ -636,6 +669,10 @@ lbm_status lbm_save_state(lbm_ctx* c, void* host_buf, size_t cap, size_t* used) 
     unsigned char* dst = (unsigned char*)host_buf + sizeof(StateHeader);
     LBM_CUDA(c, cudaMemcpyAsync(dst, c->pop[c->cur], payload, cudaMemcpyDeviceToHost, c->stream));
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    {
+        lbm_status _ds = device_status(c);
+        if (_ds != LBM_OK) return _ds;
+    }
     h.crc = checksum(dst, payload);
     std::memcpy(host_buf, &h, sizeof h);
     return LBM_OK;
@@ -655,6 +692,7 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t len) {
     if (checksum(src, payload) != h.crc) return fail(c, LBM_ERR_INVALID_ARG, "lbm_load_state: checksum mismatch");
     LBM_CUDA(c, cudaMemcpyAsync(c->pop[c->cur], src, payload, cudaMemcpyHostToDevice, c->stream));
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    *(volatile int*)c->status_host = 0;  // the state that a timed-out wait left is replaced
     c->steps = h.steps;
     c->has_state = true;
     return LBM_OK;
@@ -689,6 +727,10 @@ lbm_status lbm_window_totals(lbm_ctx* c, int64_t t_begin, int64_t t_end, double 
     LBM_CUDA(c, cudaGetLastError());
     LBM_CUDA(c, cudaMemcpyAsync(c->totals_host, c->totals_dev, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream));
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    {
+        lbm_status _ds = device_status(c);
+        if (_ds != LBM_OK) return _ds;
+    }
     for (int k = 0; k < 4; ++k) {
         if (!std::isfinite(c->totals_host[k])) return fail(c, LBM_ERR_NONFINITE, "non-finite window total");
         out[k] = c->totals_host[k];
@@ -823,6 +865,10 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
     ADJ_CHECK(cudaStreamSynchronize(c->stream));
     release();
 #undef ADJ_CHECK
+    {
+        lbm_status _ds = device_status(c);
+        if (_ds != LBM_OK) return _ds;
+    }
     c->steps += T;
     for (int k = 0; k < 5; ++k)
         if (!std::isfinite(host[k])) return fail(c, LBM_ERR_NONFINITE, "lbm_adjoint: non-finite gradient or loss");

@@ -124,33 +124,170 @@ __device__ __forceinline__ unsigned long long packed_z() {
     return v;
 }
 
-// Compacts the fluid cells of a staged row (link masks mrow[0..nx)) into
-// flist: cells without solid neighbours (mask 0) from the front, cells with
-// bounce-back links from the back (flist[nx - 1], flist[nx - 2], ...), so that
-// a warp taking consecutive entries mostly sees one kind and skips the link
-// code.  counts[0..1] must be zero on entry and receive the two numbers; the
-// call ends with a block barrier and returns counts[0].  blockDim.x must be a
-// multiple of 32.
-__device__ __forceinline__ int compact_row(const uint32_t* mrow, int nx, uint32_t* flist, int* counts) {
+template <class L>
+__device__ __forceinline__ unsigned long long packed_x() {
+    unsigned long long v = 0;
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) v |= (unsigned long long)(L::c(a, 0) + 1) << (2 * a);
+    return v;
+}
+
+// Compacts a staged row (link masks mrow[0..nx)) into flist: fluid cells from
+// the front, solid cells from the back, so that warps taking consecutive
+// entries mostly see one kind.  counts[0..1] must be zero on entry and
+// receive the numbers of fluid and solid cells; the caller synchronises the
+// block before reading them.  blockDim.x must be a multiple of 32.
+__device__ __forceinline__ void compact_fluid(const uint32_t* mrow, int nx, uint32_t* flist, int* counts) {
     const unsigned lane = threadIdx.x & 31u, below = (1u << lane) - 1u;
     for (int x0 = 0; x0 < nx; x0 += blockDim.x) {
         const int x = x0 + (int)threadIdx.x;
-        const uint32_t m = x < nx ? mrow[x] : kSolidBit;
-        const bool inner = m == 0u;
-        const bool bnd = m != 0u && !(m & kSolidBit);
-        const unsigned bi = __ballot_sync(0xffffffffu, inner), bb = __ballot_sync(0xffffffffu, bnd);
-        int base_i = 0, base_b = 0;
+        const bool in = x < nx;
+        const bool fluid = in && !(mrow[x] & kSolidBit);
+        const unsigned bf = __ballot_sync(0xffffffffu, fluid), bs = __ballot_sync(0xffffffffu, in && !fluid);
+        int base_f = 0, base_s = 0;
         if (lane == 0) {
-            if (bi) base_i = atomicAdd(&counts[0], __popc(bi));
-            if (bb) base_b = atomicAdd(&counts[1], __popc(bb));
+            if (bf) base_f = atomicAdd(&counts[0], __popc(bf));
+            if (bs) base_s = atomicAdd(&counts[1], __popc(bs));
         }
-        base_i = __shfl_sync(0xffffffffu, base_i, 0);
-        base_b = __shfl_sync(0xffffffffu, base_b, 0);
-        if (inner) flist[base_i + __popc(bi & below)] = (uint32_t)x;
-        if (bnd) flist[nx - 1 - (base_b + __popc(bb & below))] = (uint32_t)x;
+        base_f = __shfl_sync(0xffffffffu, base_f, 0);
+        base_s = __shfl_sync(0xffffffffu, base_s, 0);
+        if (fluid) flist[base_f + __popc(bf & below)] = (uint32_t)x;
+        if (in && !fluid) flist[nx - 1 - (base_s + __popc(bs & below))] = (uint32_t)x;
+    }
+}
+
+// As compact_fluid, but in ascending x within each kind, so the list (and any
+// per-thread accumulation over it) is the same on every run.  wcnt holds
+// ceil(nx / 32) ints; the fluid count goes to *nfluid.  Contains one block
+// barrier; the caller synchronises again before reading *nfluid.
+__device__ __forceinline__ void compact_fluid_ordered(const uint32_t* mrow, int nx, uint32_t* flist, int* wcnt,
+                                                      int* nfluid) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    const int nch = (nx + 31) >> 5;
+    for (int c = warp; c < nch; c += nw) {
+        const int x = c * 32 + lane;
+        const unsigned b = __ballot_sync(0xffffffffu, x < nx && !(mrow[x] & kSolidBit));
+        if (lane == 0) wcnt[c] = __popc(b);
     }
     __syncthreads();
-    return counts[0];
+    for (int c = warp; c < nch; c += nw) {
+        int before = 0;
+        for (int k = lane; k < c; k += 32) before += wcnt[k];
+        before = __reduce_add_sync(0xffffffffu, before);  // fluid cells with x < 32 c
+        const int x = c * 32 + lane;
+        const bool in = x < nx;
+        const bool fluid = in && !(mrow[x] & kSolidBit);
+        const unsigned bf = __ballot_sync(0xffffffffu, fluid), bs = __ballot_sync(0xffffffffu, in && !fluid);
+        if (fluid) flist[before + __popc(bf & below)] = (uint32_t)x;
+        if (in && !fluid) flist[nx - 1 - ((c * 32 - before) + __popc(bs & below))] = (uint32_t)x;
+        if (c == nch - 1 && lane == 0) *nfluid = before + __popc(bf);
+    }
+}
+
+// Bounce-back patch of a staged row set.  Link k of the row is a fluid cell x
+// with an outgoing direction b into a solid cell, descriptor x | b << 24.  The
+// solid neighbour x + e_b is read by exactly one cell of the row for each
+// direction: by x itself, in the pull of direction bbar (which reads
+// x - e_bbar = x + e_b) and in the adjoint gather of direction b (which reads
+// x + e_b).  So the halfway bounce-back value win[k - w0] is written into that
+// staged slot, rows[d * nx + (x + e_bx mod nx)] with d = bbar (PULL) or b
+// (gather), and the cells then read their rows without any link logic.
+// The descriptors come from the staged window desc (first element d0).
+template <class L, bool PULL, class T>
+__device__ __forceinline__ void patch_links(T* rows, int nx, const T* win, uint32_t w0, uint32_t g0, uint32_t g1,
+                                            const uint32_t* desc, uint32_t d0) {
+    const unsigned long long kPx = packed_x<L>();
+    for (uint32_t k = g0 + threadIdx.x; k < g1; k += blockDim.x) {
+        const uint32_t d = desc[k - d0];
+        const int x = (int)(d & 0xFFFFFFu), b = (int)(d >> 24);
+        int xs = x + (int)((kPx >> (2 * b)) & 3ull) - 1;
+        xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+        rows[(PULL ? opposite(b) : b) * nx + xs] = win[k - w0];
+    }
+}
+
+// Stages elements [g0, g1) of an array of `esize`-byte elements as a 16-byte
+// aligned window (cp.async); the window's first element index goes to *start
+// (written by thread 0).  The window spans at most
+// round_up16((g1 - g0) * esize) + 16 bytes.
+__device__ __forceinline__ void stage_window(unsigned char* dst, const unsigned char* base, int esize, uint32_t g0,
+                                             uint32_t g1, uint32_t* start) {
+    const uint64_t b0 = ((uint64_t)g0 * esize) & ~15ull;
+    const uint64_t b1 = ((uint64_t)g1 * esize + 15ull) & ~15ull;
+    for (int k = threadIdx.x; k < (int)((b1 - b0) >> 4); k += blockDim.x)
+        cp_async16(dst + 16 * k, base + b0 + 16 * (uint64_t)k);
+    if (threadIdx.x == 0) *start = (uint32_t)(b0 / esize);
+}
+
+// Bytes reserved for a staged window of up to n elements of esize bytes.
+__host__ __device__ __forceinline__ int window_cap(int n, int esize) {
+    return (int)((((size_t)n * esize + 15) & ~(size_t)15) + 32);
+}
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (the non-tensor form of the Blackwell TMA engine)
+// and mbarriers.  A stage is filled by one thread: mbarrier.arrive.expect_tx
+// with the stage's byte count, then one cp.async.bulk per contiguous piece,
+// each completing its bytes on the stage's mbarrier.  Output rows leave
+// shared memory with cp.async.bulk stores (bulk groups).  Addresses and
+// sizes are multiples of 16 bytes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// One potentially blocking test: the thread may be suspended in hardware
+// until the phase completes or a system-dependent time limit passes.
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the phase of the given parity to complete; gives up and returns
+// false after 2^31 SM clock cycles (about one second).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity))
+        if (clock64() - t0 > (1ll << 31)) return false;
+    return true;
+}
+// global -> shared, completing `bytes` on the mbarrier
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// shared -> global, in the current bulk group
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// the sources of all committed bulk stores have been read
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+// all committed bulk stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+// orders this thread's generic-proxy shared-memory accesses before later
+// async-proxy (bulk copy) accesses
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// Bytes [b0, b1) of the 16-byte aligned window covering elements [g0, g1).
+__device__ __forceinline__ void window_bytes(uint32_t g0, uint32_t g1, int esize, uint64_t& b0, uint64_t& b1) {
+    b0 = ((uint64_t)g0 * esize) & ~15ull;
+    b1 = ((uint64_t)g1 * esize + 15ull) & ~15ull;
 }
 
 }  // namespace dev

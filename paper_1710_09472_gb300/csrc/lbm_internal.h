@@ -146,9 +146,15 @@ struct KParams {
     uint64_t gofs;
     const uint32_t* lbase;
     const uint32_t* rowG;
+    // per link slot k: x | b << 24, the x coordinate of its fluid cell and
+    // its outgoing direction b (the row-staged kernels' link passes)
+    const uint32_t* ldesc;
     int max_row_links;
     // byte offset of the link buffer inside an adjoint field (reverse sweep)
     uint64_t lgofs;
+    // host-mapped status word: a kernel whose bounded wait ran out writes a
+    // nonzero code here (read by the next synchronising API call)
+    int* status;
 };
 
 struct Launch {
@@ -160,6 +166,9 @@ int launch_build_neighbors(int vel, const uint8_t* mask, uint32_t* nbr, unsigned
                            const KParams& p, cudaStream_t s);
 // Link buffer layout: lbase[cell] (exclusive prefix of outgoing-link counts),
 // rowG[0..ny*nz]; needs a temporary of *temp_bytes (queried with temp == NULL).
+// Per-link descriptors ldesc[k] = x | b << 24 (needs lbase).
+int launch_build_link_desc(int vel, const uint32_t* nbr, const uint32_t* lbase, uint32_t* ldesc, const KParams& p,
+                           cudaStream_t s);
 int launch_build_links(int vel, const uint32_t* nbr, uint32_t* lbase, uint32_t* rowG, void* temp,
                        size_t* temp_bytes, const KParams& p, cudaStream_t s);
 int launch_init(int vel, int storage, void* pop, const uint32_t* nbr, const float* rho, const float* u,
@@ -222,6 +231,7 @@ struct lbm_ctx {
     uint32_t* nbr = nullptr;
     uint32_t* lbase = nullptr;     // per-cell first slot in the link buffer
     uint32_t* rowG = nullptr;      // per-row first slot (ny * nz + 1)
+    uint32_t* ldesc = nullptr;     // per link slot: x | b << 24
     int64_t n_links = 0;           // outgoing links into solid cells
     int max_row_links = 0;
     size_t state_bytes = 0;        // populations + link buffer
@@ -234,6 +244,8 @@ struct lbm_ctx {
     double* totals_dev = nullptr;
     double* totals_host = nullptr;  // pinned, 4 doubles
     unsigned long long* count_dev = nullptr;
+    int* status_host = nullptr;    // mapped pinned word written by kernels on a wait timeout
+    int* status_dev = nullptr;     // its device address
     float* stage = nullptr;  // device staging for host-pointer arguments
     size_t stage_bytes = 0;
     bool geometry_counted = false;

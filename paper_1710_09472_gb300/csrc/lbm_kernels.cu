@@ -110,6 +110,23 @@ __global__ void __launch_bounds__(kBlock) k_link_counts(const uint32_t* __restri
     cnt[c.cell] = (m & kSolidBit) ? 0u : (uint32_t)__popc(outgoing<L::Q>(m));
 }
 
+// Descriptor of every link slot: the x coordinate of its fluid cell and its
+// outgoing direction b, ldesc[slot] = x | b << 24.
+template <class L>
+__global__ void __launch_bounds__(kBlock) k_link_desc(const uint32_t* __restrict__ nbr,
+                                                      const uint32_t* __restrict__ lbase,
+                                                      uint32_t* __restrict__ ldesc, KParams p) {
+    Cell c;
+    if (!dev::cell_of_thread(p, c)) return;
+    const uint32_t m = nbr[c.cell];
+    if ((m & kSolidBit) || m == 0u) return;
+    const uint32_t o = outgoing<L::Q>(m);
+    const uint32_t base = lbase[c.cell];
+#pragma unroll
+    for (int b = 1; b < L::Q; ++b)
+        if ((o >> b) & 1u) ldesc[link_slot(base, o, b)] = (uint32_t)c.x | ((uint32_t)b << 24);
+}
+
 template <class L>
 __global__ void k_row_starts(const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ lbase,
                              uint32_t* __restrict__ rowG, KParams p) {
@@ -309,6 +326,16 @@ int launch_build_links(int vel, const uint32_t* nbr, uint32_t* lbase, uint32_t* 
         return 1;
     });
     return 3;
+}
+
+int launch_build_link_desc(int vel, const uint32_t* nbr, const uint32_t* lbase, uint32_t* ldesc, const KParams& p,
+                           cudaStream_t s) {
+    Launch l = grid_of(p);
+    return dispatch_lattice(vel, [&](auto lat) {
+        using L = decltype(lat);
+        k_link_desc<L><<<l.grid, l.block, 0, s>>>(nbr, lbase, ldesc, p);
+        return 1;
+    });
 }
 
 int launch_init(int vel, int storage, void* pop, const uint32_t* nbr, const float* rho, const float* u,

@@ -327,130 +327,115 @@ __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict
 
 // ---------------------------------------------------------------------------
 // Row-staged step kernel (used when a whole x-row of one direction is a
-// power-of-two number of 16-byte chunks and the rings fit shared memory).  A
+// whole number of 16-byte chunks and the stages fit shared memory).  A
 // persistent block walks rows r = blockIdx.x, blockIdx.x + gridDim.x, ...:
-//  - the Q source rows P_a(y - e_ay, z - e_az, :) of the row are copied whole
-//    into a ring of STAGES row sets with 16-byte asynchronous copies
-//    (cp.async.cg, L1 bypass), STAGES - 1 rows ahead of the row being computed;
+//  - the Q source rows P_a(y - e_ay, z - e_az, :) of the row, its link masks
+//    and its ranges of the link buffer and of the link descriptors arrive by
+//    bulk asynchronous copies (warp 0 issues one copy per contiguous piece,
+//    completing on the stage's mbarrier) into a ring of STAGES stages,
+//    STAGES - 1 rows ahead of the row being computed;
+//  - one pass over the row's links writes each bounced value f*_b(x) into the
+//    staged slot that the pull of direction bbar at x reads (the slot of the
+//    solid neighbour), so the cells pull without link logic;
 //  - the row's fluid cells are compacted into a list, so the collision runs on
-//    full warps (solid cells do no work); cells with bounce-back links are
-//    listed after the others, so most warps skip the link code;
+//    full warps; solid cells only write zeros;
 //  - f_a(x) is read from the ring at x - e_ax (periodic wrap in x is a
-//    shared-memory index); a bounced link reads P_abar(x) from global memory;
-//  - results go into a shared-memory output row set (zero for solid cells),
-//    which is then written with 16-byte vector stores: whole sectors, fully
-//    coalesced, no scattered stores.
+//    shared-memory index); results go into a shared-memory output row set
+//    that leaves by bulk stores (one per direction);
+//  - one pass over the row's links copies the outgoing values f*_b(x) from
+//    the output rows into the row's contiguous range of the link buffer.
+// Two block barriers per row; a stage is refilled after the first barrier of
+// the row that follows its own.  Every wait on an mbarrier is bounded; one that
+// runs out writes a code to p.status and the kernel carries on (its results
+// are then invalid, but it ends and no access leaves its buffers).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// e_ay + 1 and e_az + 1 of every direction, 2 bits each, in two 64-bit words
-// (19 directions need 38 bits per word); the unrolled loops fold to constants.
-template <class L>
-__device__ __forceinline__ unsigned long long packed_y() {
-    unsigned long long v = 0;
-#pragma unroll
-    for (int a = 0; a < L::Q; ++a) v |= (unsigned long long)(L::c(a, 1) + 1) << (2 * a);
-    return v;
-}
-template <class L>
-__device__ __forceinline__ unsigned long long packed_z() {
-    unsigned long long v = 0;
-#pragma unroll
-    for (int a = 0; a < L::Q; ++a) v |= (unsigned long long)(L::c(a, 2) + 1) << (2 * a);
-    return v;
-}
 
 // Shared-memory layout of one stage: Q source rows (Q nx elements), the row's
-// link masks (nx words), its first link slots (nx words), and its range of the
-// link buffer (gcap bytes, 16-byte aligned window).
+// link masks (nx words), its range of the link buffer (gcap bytes) and of
+// the link descriptors (dcap bytes), both as 16-byte aligned windows.
 template <class L, class S>
 struct StageLayout {
-    int nx, gcap;
-    __device__ __forceinline__ int bytes() const { return L::Q * nx * S::kBytes + 8 * nx + gcap; }
+    int nx, gcap, dcap;
+    __device__ __forceinline__ int bytes() const { return L::Q * nx * S::kBytes + 4 * nx + gcap + dcap; }
     __device__ __forceinline__ typename S::T* rows(unsigned char* st) const {
         return reinterpret_cast<typename S::T*>(st);
     }
     __device__ __forceinline__ uint32_t* masks(unsigned char* st) const {
         return reinterpret_cast<uint32_t*>(st + L::Q * nx * S::kBytes);
     }
-    __device__ __forceinline__ uint32_t* bases(unsigned char* st) const { return masks(st) + nx; }
     __device__ __forceinline__ typename S::T* links(unsigned char* st) const {
-        return reinterpret_cast<typename S::T*>(st + L::Q * nx * S::kBytes + 8 * nx);
+        return reinterpret_cast<typename S::T*>(st + L::Q * nx * S::kBytes + 4 * nx);
+    }
+    __device__ __forceinline__ uint32_t* descs(unsigned char* st) const {
+        return reinterpret_cast<uint32_t*>(st + L::Q * nx * S::kBytes + 4 * nx + gcap);
     }
 };
 
+// Issued by warp 0: the bulk copies of row `row` into stage `st`, all
+// completing on `bar` (lane 0 arms the barrier with the byte count, then lane
+// a copies source row a; the last lanes take the masks and the windows).  The
+// window starts go to *gstart and *dstart before the barrier is armed.
 template <class L, class S>
-__device__ __forceinline__ void stage_row(unsigned char* st, const StageLayout<L, S>& lay,
+__device__ __forceinline__ void stage_row(unsigned char* st, const StageLayout<L, S>& lay, uint64_t* bar,
                                           const typename S::T* __restrict__ Pin, const uint32_t* __restrict__ nbr,
-                                          int row, uint32_t g0, uint32_t g1, int cpr_shift, uint32_t* gstart,
+                                          int row, uint32_t g0, uint32_t g1, uint32_t* gstart, uint32_t* dstart,
                                           const KParams& p) {
-    using T = typename S::T;
-    constexpr int kElem16 = 16 / S::kBytes;
-    static_assert(L::Q <= 32, "direction codes must fit 64 bits");
-    const unsigned long long kPy = packed_y<L>(), kPz = packed_z<L>();
-    const int cpr = 1 << cpr_shift;  // 16-byte chunks per population row
-    const int y = row % p.ny, z = row / p.ny;
-    T* rows = lay.rows(st);
-    const int total = L::Q << cpr_shift;
-    for (int k = threadIdx.x; k < total; k += blockDim.x) {
-        const int a = k >> cpr_shift, off = k & (cpr - 1);
-        const int ey = (int)((kPy >> (2 * a)) & 3ull) - 1, ez = (int)((kPz >> (2 * a)) & 3ull) - 1;
-        // source row of direction a: (y - e_ay, z - e_az) with periodic wrap
-        int ys = y - ey, zs = z - ez;
+    static_assert(L::Q + 3 <= 32, "one lane per copy");
+    const int lane = threadIdx.x & 31;
+    const uint32_t row_bytes = (uint32_t)p.nx * S::kBytes;
+    uint64_t gb0, gb1, db0, db1;
+    dev::window_bytes(g0, g1, S::kBytes, gb0, gb1);
+    dev::window_bytes(g0, g1, 4, db0, db1);
+    if (lane == 0) {
+        *gstart = (uint32_t)(gb0 / S::kBytes);
+        *dstart = (uint32_t)(db0 / 4);
+        dev::mbar_expect_tx(bar, L::Q * row_bytes + 4u * (uint32_t)p.nx + (uint32_t)(gb1 - gb0) +
+                                     (uint32_t)(db1 - db0));
+    }
+    __syncwarp();
+    if (lane < L::Q) {
+        // source row of direction a = lane: (y - e_ay, z - e_az), periodic
+        const unsigned long long kPy = dev::packed_y<L>(), kPz = dev::packed_z<L>();
+        const int a = lane;
+        const int y = row % p.ny, z = row / p.ny;
+        int ys = y - ((int)((kPy >> (2 * a)) & 3ull) - 1), zs = z - ((int)((kPz >> (2 * a)) & 3ull) - 1);
         ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
         zs = zs < 0 ? zs + p.nz : (zs >= p.nz ? zs - p.nz : zs);
-        const int64_t src = (int64_t)a * p.N + ((int64_t)zs * p.ny + ys) * p.nx + (int64_t)off * kElem16;
-        cp_async16(rows + a * p.nx + off * kElem16, Pin + src);
+        dev::bulk_load(lay.rows(st) + a * p.nx, Pin + (int64_t)a * p.N + ((int64_t)zs * p.ny + ys) * p.nx, row_bytes,
+                       bar);
+    } else if (lane == L::Q) {
+        dev::bulk_load(lay.masks(st), nbr + (int64_t)row * p.nx, 4u * (uint32_t)p.nx, bar);
+    } else if (lane == L::Q + 1) {
+        if (gb1 > gb0)
+            dev::bulk_load(lay.links(st), reinterpret_cast<const unsigned char*>(Pin) + p.gofs + gb0,
+                           (uint32_t)(gb1 - gb0), bar);
+    } else if (lane == L::Q + 2) {
+        if (db1 > db0)
+            dev::bulk_load(lay.descs(st), reinterpret_cast<const unsigned char*>(p.ldesc) + db0,
+                           (uint32_t)(db1 - db0), bar);
     }
-    // link masks and first link slots of the row (nx words each)
-    const int wchunks = p.nx >> 2;
-    const uint32_t* mrow = nbr + (int64_t)row * p.nx;
-    const uint32_t* brow = p.lbase + (int64_t)row * p.nx;
-    for (int k = threadIdx.x; k < 2 * wchunks; k += blockDim.x) {
-        if (k < wchunks)
-            cp_async16(lay.masks(st) + 4 * k, mrow + 4 * k);
-        else
-            cp_async16(lay.bases(st) + 4 * (k - wchunks), brow + 4 * (k - wchunks));
-    }
-    // the row's links [g0, g1), in a 16-byte aligned window
-    const uint64_t b0 = ((uint64_t)g0 * S::kBytes) & ~15ull;
-    const uint64_t b1 = ((uint64_t)g1 * S::kBytes + 15ull) & ~15ull;
-    const unsigned char* G = reinterpret_cast<const unsigned char*>(Pin) + p.gofs;
-    for (int k = threadIdx.x; k < (int)((b1 - b0) >> 4); k += blockDim.x)
-        cp_async16(reinterpret_cast<unsigned char*>(lay.links(st)) + 16 * k, G + b0 + 16 * (uint64_t)k);
-    if (threadIdx.x == 0) *gstart = (uint32_t)(b0 / S::kBytes);
 }
 
 template <class L, class S, int FORCE, bool EF, bool SR, int STAGES>
 __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restrict__ Pin,
                                                    typename S::T* __restrict__ Pout, const uint32_t* __restrict__ nbr,
-                                                   const float* __restrict__ Ef, int cpr_shift, int gcap, KParams p) {
+                                                   const float* __restrict__ Ef, int gcap, int dcap, KParams p) {
     using T = typename S::T;
-    constexpr int kElem16 = 16 / S::kBytes;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int nx = p.nx;
-    const StageLayout<L, S> lay{nx, gcap};
+    const StageLayout<L, S> lay{nx, gcap, dcap};
     const int sbytes = lay.bytes();
     T* outrow = reinterpret_cast<T*>(smem_raw + STAGES * sbytes);
-    uint32_t* flist = reinterpret_cast<uint32_t*>(outrow + L::Q * nx);  // x of the row's fluid cells
-    __shared__ int fcount[2];  // interior, boundary fluid cells of the row
-    __shared__ uint32_t gstart[STAGES];
+    uint32_t* flist = reinterpret_cast<uint32_t*>(outrow + L::Q * nx);  // fluid x from the front, solid from the back
+    __shared__ __align__(8) uint64_t bar[STAGES];
+    __shared__ int counts[2][2];  // [row parity][fluid, solid]
+    __shared__ uint32_t gstart[STAGES], dstart[STAGES];
     T* Gout = reinterpret_cast<T*>(reinterpret_cast<char*>(Pout) + p.gofs);
+    const uint32_t row_bytes = (uint32_t)nx * S::kBytes;
     const int R = p.ny * p.nz;
     const int G = gridDim.x;
-    const int cpr = 1 << cpr_shift;
-    const int chunks = L::Q << cpr_shift;
-    for (int k = threadIdx.x; k < chunks; k += blockDim.x)
-        reinterpret_cast<uint4*>(outrow)[k] = make_uint4(0u, 0u, 0u, 0u);
-    if (threadIdx.x == 0) fcount[0] = fcount[1] = 0;
+    const bool leader = threadIdx.x == 0;
+    const bool warp0 = threadIdx.x < 32;
     auto range = [&](int row, uint32_t& g0, uint32_t& g1) {
         g0 = g1 = 0u;
         if (row < R) {
@@ -458,90 +443,97 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
             g1 = __ldg(p.rowG + row + 1);
         }
     };
+    if (leader) {
+        counts[0][0] = counts[0][1] = counts[1][0] = counts[1][1] = 0;
 #pragma unroll
-    for (int k = 0; k < STAGES - 1; ++k) {
-        const int rk = blockIdx.x + k * G;
-        uint32_t g0, g1;
-        range(rk, g0, g1);
-        if (rk < R) stage_row<L, S>(smem_raw + k * sbytes, lay, Pin, nbr, rk, g0, g1, cpr_shift, &gstart[k], p);
-        cp_async_commit();
+        for (int k = 0; k < STAGES; ++k) dev::mbar_init(&bar[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    uint32_t ng0, ng1;  // link range of the next row to stage, loaded one iteration ahead
-    range(blockIdx.x + (STAGES - 1) * G, ng0, ng1);
     __syncthreads();
-    int it = 0;
-    for (int r = blockIdx.x; r < R; r += G, ++it) {
-        const int rn = r + (STAGES - 1) * G;
-        const int sn = (it + STAGES - 1) % STAGES;
-        if (rn < R) stage_row<L, S>(smem_raw + sn * sbytes, lay, Pin, nbr, rn, ng0, ng1, cpr_shift, &gstart[sn], p);
-        cp_async_commit();
-        range(rn + G, ng0, ng1);
-        cp_async_wait<STAGES - 1>();
-        __syncthreads();  // this row's stage has landed
-        unsigned char* st = smem_raw + (it % STAGES) * sbytes;
-        const T* buf = lay.rows(st);
-        const uint32_t* mrow = lay.masks(st);
-        const uint32_t* brow = lay.bases(st);
-        const T* lbuf = lay.links(st);
-        const uint32_t g_base = gstart[it % STAGES];
-        const uint32_t rowbase = (uint32_t)r * (uint32_t)nx;
-        const int ni = dev::compact_row(mrow, nx, flist, fcount);
-        const int nf = ni + fcount[1];
-        Cell c;
-        c.y = r % p.ny;
-        c.z = r / p.ny;
-        for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-            const int x = (int)flist[i < ni ? i : nx - nf + i];
-            const uint32_t m = mrow[x];
-            c.x = x;
-            c.cell = rowbase + (uint32_t)x;
-            const int xm = x == 0 ? nx - 1 : x - 1;
-            const int xp = x == nx - 1 ? 0 : x + 1;
-            const uint32_t o = outgoing<L::Q>(m);
-            const uint32_t lb = m ? brow[x] : 0u;
-            float h[L::Q];
+    if (warp0) {
 #pragma unroll
-            for (int a = 0; a < L::Q; ++a) {
-                const int ex = L::c(a, 0);
-                const int xs = ex > 0 ? xm : (ex < 0 ? xp : x);
-                h[a] = S::cvt(buf[a * nx + xs]);
-            }
-            if (m != 0u) {  // bounced links: f_a(x) = f*_abar(x) from the link buffer
-#pragma unroll
-                for (int a = 1; a < L::Q; ++a)
-                    if ((m >> a) & 1u) h[a] = S::cvt(lbuf[link_slot(lb, o, opposite(a)) - g_base]);
-            }
-            float E[3];
-            load_E<L>(Ef, EF, p, c.cell, E);
-            float out[L::Q];
-            collide_any<L, S, FORCE>(h, E, p, out);
-            Rng rng(c.cell, p);
-            uint32_t rnd[L::Q];
-#pragma unroll
-            for (int a = 0; a < L::Q; ++a) {
-                rnd[a] = SR ? rng.next() : 0u;
-                store_val<S, SR>(outrow + a * nx + x, out[a], rnd[a]);
-            }
-            if (o != 0u) {  // links into solid cells also store into their slots
-#pragma unroll
-                for (int a = 1; a < L::Q; ++a)
-                    if ((o >> a) & 1u) store_val<S, SR>(Gout + link_slot(lb, o, a), out[a], rnd[a]);
+        for (int k = 0; k < STAGES - 1; ++k) {
+            const int rk = blockIdx.x + k * G;
+            if (rk < R) {
+                uint32_t g0, g1;
+                range(rk, g0, g1);
+                stage_row<L, S>(smem_raw + k * sbytes, lay, &bar[k], Pin, nbr, rk, g0, g1, &gstart[k], &dstart[k], p);
             }
         }
-        __syncthreads();  // output rows complete
-        // write the output rows with 16-byte vector stores; each chunk is
-        // zeroed again by the thread that read it (solid cells stay 0)
-        for (int k = threadIdx.x; k < chunks; k += blockDim.x) {
-            const int a = k >> cpr_shift, off = k & (cpr - 1);
-            uint4* src = reinterpret_cast<uint4*>(outrow + a * nx) + off;
-            T* dst = Pout + (int64_t)a * p.N + rowbase + (int64_t)off * kElem16;
-            *reinterpret_cast<uint4*>(dst) = *src;
-            *src = make_uint4(0u, 0u, 0u, 0u);
-        }
-        if (threadIdx.x == 0) fcount[0] = fcount[1] = 0;
-        __syncthreads();  // list, counter and stage slot free for reuse
     }
-    cp_async_wait<0>();
+    int it = 0;
+    bool ok = true;  // false once a wait has run out: no further waits
+    for (int r = blockIdx.x; r < R; r += G, ++it) {
+        const int cs = it % STAGES;
+        uint32_t g0, g1;  // this row's links
+        range(r, g0, g1);
+        if (ok && !dev::mbar_wait(&bar[cs], (uint32_t)(it / STAGES) & 1u)) {
+            ok = false;
+            if (p.status) atomicExch(p.status, 1);
+        }
+        unsigned char* st = smem_raw + cs * sbytes;
+        T* buf = lay.rows(st);
+        const uint32_t* desc = lay.descs(st);
+        const uint32_t d0 = dstart[cs];
+        int* cnt = counts[it & 1];
+        dev::compact_fluid(lay.masks(st), nx, flist, cnt);
+        dev::patch_links<L, true>(buf, nx, lay.links(st), gstart[cs], g0, g1, desc, d0);
+        if (warp0) dev::bulk_wait_read();  // the previous row's bulk stores have read the output rows
+        if (leader) counts[(it + 1) & 1][0] = counts[(it + 1) & 1][1] = 0;
+        __syncthreads();  // list complete, bounced values in place, output rows free
+        if (warp0) {
+            // refill the stage of the previous row: every thread is past its
+            // last reads of it (the link pass that follows the output)
+            const int rn = r + (STAGES - 1) * G;
+            if (rn < R) {
+                const int sn = (it + STAGES - 1) % STAGES;
+                uint32_t n0, n1;
+                range(rn, n0, n1);
+                stage_row<L, S>(smem_raw + sn * sbytes, lay, &bar[sn], Pin, nbr, rn, n0, n1, &gstart[sn], &dstart[sn],
+                                p);
+            }
+        }
+        const int nf = cnt[0];
+        const uint32_t rowbase = (uint32_t)r * (uint32_t)nx;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const int x = (int)flist[i];
+            if (i < nf) {
+                const uint32_t cell = rowbase + (uint32_t)x;
+                const int xm = x == 0 ? nx - 1 : x - 1;
+                const int xp = x == nx - 1 ? 0 : x + 1;
+                float h[L::Q];
+#pragma unroll
+                for (int a = 0; a < L::Q; ++a) {
+                    const int ex = L::c(a, 0);
+                    h[a] = S::cvt(buf[a * nx + (ex > 0 ? xm : (ex < 0 ? xp : x))]);
+                }
+                float E[3];
+                load_E<L>(Ef, EF, p, cell, E);
+                float out[L::Q];
+                collide_any<L, S, FORCE>(h, E, p, out);
+                Rng rng(cell, p);
+#pragma unroll
+                for (int a = 0; a < L::Q; ++a) store_val<S, SR>(outrow + a * nx + x, out[a], SR ? rng.next() : 0u);
+            } else {
+#pragma unroll
+                for (int a = 0; a < L::Q; ++a) S::put(outrow + a * nx + x, 0.f);
+            }
+        }
+        dev::fence_proxy_async();  // this thread's shared-memory writes before the bulk copies
+        __syncthreads();           // output rows complete; the stage is free for its refill
+        if (threadIdx.x < L::Q) {
+            // lane a of warp 0: the bulk store of direction a, in its own group
+            const int a = threadIdx.x;
+            dev::bulk_store(Pout + (int64_t)a * p.N + rowbase, outrow + a * nx, row_bytes);
+            dev::bulk_commit();
+        }
+        // outgoing links: slot k of (x, b) takes f*_b(x)
+        for (uint32_t k = g0 + threadIdx.x; k < g1; k += blockDim.x) {
+            const uint32_t d = desc[k - d0];
+            Gout[k] = outrow[(int)(d >> 24) * nx + (int)(d & 0xFFFFFFu)];
+        }
+    }
+    if (warp0) dev::bulk_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -583,20 +575,17 @@ int launch_one(const void* fin, void* fout, const uint32_t* nbr, const float* Ef
     const T* in = (const T*)fin;
     T* out = (T*)fout;
     const size_t row_bytes = (size_t)p.nx * S::kBytes;
-    const int gcap = (int)((((size_t)p.max_row_links * S::kBytes + 15) & ~(size_t)15) + 32);
-    const size_t stage_bytes = (size_t)L::Q * row_bytes + 8 * (size_t)p.nx + gcap;
+    const int gcap = dev::window_cap(p.max_row_links, S::kBytes);
+    const int dcap = dev::window_cap(p.max_row_links, 4);
+    const size_t stage_bytes = (size_t)L::Q * row_bytes + 4 * (size_t)p.nx + gcap + dcap;
     const size_t smem = (size_t)kStages * stage_bytes + (size_t)L::Q * row_bytes + 4 * (size_t)p.nx;
-    const size_t cpr = row_bytes / 16;
-    int cpr_shift = 0;
-    while ((size_t(1) << cpr_shift) < cpr) ++cpr_shift;
-    if (row_bytes % 16 == 0 && (size_t(1) << cpr_shift) == cpr && smem <= kSmemBudget && p.nx >= 32 &&
-        p.nx % 4 == 0) {
+    if (row_bytes % 16 == 0 && smem <= kSmemBudget && p.nx >= 32 && p.nx % 4 == 0) {
         const int threads = p.nx >= kRowThreads ? kRowThreads : ((p.nx + 31) / 32) * 32;
         auto kern = k_step_rows<L, S, FORCE, EF, SR, kStages>;
         const int blocks = persistent_grid(kern, threads, smem);
         if (blocks > 0) {
             const int rows = p.ny * p.nz;
-            kern<<<blocks < rows ? blocks : rows, threads, smem, s>>>(in, out, nbr, Ef, cpr_shift, gcap, p);
+            kern<<<blocks < rows ? blocks : rows, threads, smem, s>>>(in, out, nbr, Ef, gcap, dcap, p);
             return 1;
         }
     }
