@@ -184,6 +184,16 @@ lbm_status lbm_get_populations(lbm_ctx* ctx, float* f, int deviation);
  * Synchronises.  Errors: INVALID_ARG, STATE, CUDA, NONFINITE. */
 lbm_status lbm_window_totals(lbm_ctx* ctx, int64_t t_begin, int64_t t_end, double out[4]);
 
+/* Failure-path self-check (the paper has no counterpart).  Launches one block
+ * that waits on an mbarrier that nothing completes, using the same bounded
+ * wait as the row-staged kernels but a limit of `clocks` SM cycles
+ * (1 <= clocks <= 2^31).  The wait runs out, the block writes its code into
+ * the context's status word and returns, and this call (which synchronises)
+ * returns LBM_ERR_TIMEOUT, just as a real timeout would be reported.  The
+ * context stays usable.  Errors: INVALID_ARG, CUDA; an earlier unreported
+ * timeout is returned first. */
+lbm_status lbm_selftest_wait_timeout(lbm_ctx* ctx, int64_t clocks);
+
 /* Reverse-mode gradient of a linear functional of the trajectory that starts
  * at the current state f_0 (this is an addition to the paper's method: a
  * hand-written adjoint of the Sec. 9.1 step, with the Sec. 7 forcing):

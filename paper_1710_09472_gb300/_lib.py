@@ -47,6 +47,7 @@ SIGNATURES = {
     "lbm_last_error": (ctypes.c_char_p, [_vp]),
     "lbm_status_string": (ctypes.c_char_p, [_i]),
     "lbm_launch_count": (_i64, [_vp]),
+    "lbm_selftest_wait_timeout": (_i, [_vp, _i64]),
 }
 
 

@@ -738,6 +738,21 @@ lbm_status lbm_window_totals(lbm_ctx* c, int64_t t_begin, int64_t t_end, double 
     return LBM_OK;
 }
 
+lbm_status lbm_selftest_wait_timeout(lbm_ctx* c, int64_t clocks) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (clocks < 1 || clocks > (1ll << 31))
+        return fail(c, LBM_ERR_INVALID_ARG, "lbm_selftest_wait_timeout: need 1 <= clocks <= 2^31");
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    {
+        lbm_status _ds = device_status(c);  // an earlier timeout is reported first
+        if (_ds != LBM_OK) return _ds;
+    }
+    c->launches += lbm::launch_wait_probe(c->status_dev, (long long)clocks, c->stream);
+    LBM_CUDA(c, cudaGetLastError());
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return device_status(c);
+}
+
 lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t t_begin, int64_t t_end,
                        int64_t checkpoint_every, double* dL_dE, double dL_dB[3], double* dL_dtau, double* loss,
                        float* dL_df0) {

@@ -254,12 +254,12 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 // Waits for the phase of the given parity to complete; gives up and returns
-// false after 2^31 SM clock cycles (about one second).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// false after `limit` SM clock cycles (default 2^31, about one second).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = 1ll << 31) {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try(bar, parity))
-        if (clock64() - t0 > (1ll << 31)) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 // global -> shared, completing `bytes` on the mbarrier

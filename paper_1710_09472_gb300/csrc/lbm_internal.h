@@ -166,6 +166,8 @@ int launch_build_neighbors(int vel, const uint8_t* mask, uint32_t* nbr, unsigned
                            const KParams& p, cudaStream_t s);
 // Link buffer layout: lbase[cell] (exclusive prefix of outgoing-link counts),
 // rowG[0..ny*nz]; needs a temporary of *temp_bytes (queried with temp == NULL).
+// Bounded-wait probe (writes code 3 into *status when its wait runs out).
+int launch_wait_probe(int* status, long long limit, cudaStream_t s);
 // Per-link descriptors ldesc[k] = x | b << 24 (needs lbase).
 int launch_build_link_desc(int vel, const uint32_t* nbr, const uint32_t* lbase, uint32_t* ldesc, const KParams& p,
                            cudaStream_t s);

@@ -328,6 +328,25 @@ int launch_build_links(int vel, const uint32_t* nbr, uint32_t* lbase, uint32_t* 
     return 3;
 }
 
+// Failure-path probe: one block waits, with the staged kernels' bounded
+// wait, on an mbarrier that nothing completes; the wait runs out after
+// `limit` clocks and the block writes code 3 into the status word.
+__global__ void k_wait_probe(int* status, long long limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        dev::mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    const bool done = dev::mbar_wait(&bar, 0u, limit);
+    if (!done && threadIdx.x == 0 && status) atomicExch(status, 3);
+}
+
+int launch_wait_probe(int* status, long long limit, cudaStream_t s) {
+    k_wait_probe<<<1, 32, 0, s>>>(status, limit);
+    return 1;
+}
+
 int launch_build_link_desc(int vel, const uint32_t* nbr, const uint32_t* lbase, uint32_t* ldesc, const KParams& p,
                            cudaStream_t s) {
     Launch l = grid_of(p);

@@ -331,8 +331,8 @@ __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict
 // persistent block walks rows r = blockIdx.x, blockIdx.x + gridDim.x, ...:
 //  - the Q source rows P_a(y - e_ay, z - e_az, :) of the row, its link masks
 //    and its ranges of the link buffer and of the link descriptors arrive by
-//    bulk asynchronous copies (warp 0 issues one copy per contiguous piece,
-//    completing on the stage's mbarrier) into a ring of STAGES stages,
+//    bulk asynchronous copies (one thread issues one copy per contiguous
+//    piece, completing on the stage's mbarrier) into a ring of STAGES stages,
 //    STAGES - 1 rows ahead of the row being computed;
 //  - one pass over the row's links writes each bounced value f*_b(x) into the
 //    staged slot that the pull of direction bbar at x reads (the slot of the
@@ -371,49 +371,42 @@ struct StageLayout {
     }
 };
 
-// Issued by warp 0: the bulk copies of row `row` into stage `st`, all
-// completing on `bar` (lane 0 arms the barrier with the byte count, then lane
-// a copies source row a; the last lanes take the masks and the windows).  The
-// window starts go to *gstart and *dstart before the barrier is armed.
+// Issued by one thread (lane 0 of warp 0; the other lanes return): the bulk
+// copies of row `row` into stage `st`, all completing on `bar`.  The window
+// starts go to *gstart and *dstart before the barrier is armed, so the arrive
+// releases them to the waiting threads.  (Spreading the copies over the
+// lanes of warp 0 measured slower.)
 template <class L, class S>
 __device__ __forceinline__ void stage_row(unsigned char* st, const StageLayout<L, S>& lay, uint64_t* bar,
                                           const typename S::T* __restrict__ Pin, const uint32_t* __restrict__ nbr,
                                           int row, uint32_t g0, uint32_t g1, uint32_t* gstart, uint32_t* dstart,
                                           const KParams& p) {
-    static_assert(L::Q + 3 <= 32, "one lane per copy");
-    const int lane = threadIdx.x & 31;
+    if ((threadIdx.x & 31) != 0) return;
     const uint32_t row_bytes = (uint32_t)p.nx * S::kBytes;
     uint64_t gb0, gb1, db0, db1;
     dev::window_bytes(g0, g1, S::kBytes, gb0, gb1);
     dev::window_bytes(g0, g1, 4, db0, db1);
-    if (lane == 0) {
-        *gstart = (uint32_t)(gb0 / S::kBytes);
-        *dstart = (uint32_t)(db0 / 4);
-        dev::mbar_expect_tx(bar, L::Q * row_bytes + 4u * (uint32_t)p.nx + (uint32_t)(gb1 - gb0) +
-                                     (uint32_t)(db1 - db0));
-    }
-    __syncwarp();
-    if (lane < L::Q) {
-        // source row of direction a = lane: (y - e_ay, z - e_az), periodic
-        const unsigned long long kPy = dev::packed_y<L>(), kPz = dev::packed_z<L>();
-        const int a = lane;
-        const int y = row % p.ny, z = row / p.ny;
-        int ys = y - ((int)((kPy >> (2 * a)) & 3ull) - 1), zs = z - ((int)((kPz >> (2 * a)) & 3ull) - 1);
-        ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
-        zs = zs < 0 ? zs + p.nz : (zs >= p.nz ? zs - p.nz : zs);
+    *gstart = (uint32_t)(gb0 / S::kBytes);
+    *dstart = (uint32_t)(db0 / 4);
+    dev::mbar_expect_tx(bar, L::Q * row_bytes + 4u * (uint32_t)p.nx + (uint32_t)(gb1 - gb0) + (uint32_t)(db1 - db0));
+    const int y = row % p.ny, z = row / p.ny;
+    const int yp = y == p.ny - 1 ? 0 : y + 1, ym = y == 0 ? p.ny - 1 : y - 1;
+    const int zp = z == p.nz - 1 ? 0 : z + 1, zm = z == 0 ? p.nz - 1 : z - 1;
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) {
+        // source row of direction a: (y - e_ay, z - e_az), periodic
+        const int ys = L::c(a, 1) > 0 ? ym : (L::c(a, 1) < 0 ? yp : y);
+        const int zs = L::c(a, 2) > 0 ? zm : (L::c(a, 2) < 0 ? zp : z);
         dev::bulk_load(lay.rows(st) + a * p.nx, Pin + (int64_t)a * p.N + ((int64_t)zs * p.ny + ys) * p.nx, row_bytes,
                        bar);
-    } else if (lane == L::Q) {
-        dev::bulk_load(lay.masks(st), nbr + (int64_t)row * p.nx, 4u * (uint32_t)p.nx, bar);
-    } else if (lane == L::Q + 1) {
-        if (gb1 > gb0)
-            dev::bulk_load(lay.links(st), reinterpret_cast<const unsigned char*>(Pin) + p.gofs + gb0,
-                           (uint32_t)(gb1 - gb0), bar);
-    } else if (lane == L::Q + 2) {
-        if (db1 > db0)
-            dev::bulk_load(lay.descs(st), reinterpret_cast<const unsigned char*>(p.ldesc) + db0,
-                           (uint32_t)(db1 - db0), bar);
     }
+    dev::bulk_load(lay.masks(st), nbr + (int64_t)row * p.nx, 4u * (uint32_t)p.nx, bar);
+    if (gb1 > gb0)
+        dev::bulk_load(lay.links(st), reinterpret_cast<const unsigned char*>(Pin) + p.gofs + gb0,
+                       (uint32_t)(gb1 - gb0), bar);
+    if (db1 > db0)
+        dev::bulk_load(lay.descs(st), reinterpret_cast<const unsigned char*>(p.ldesc) + db0, (uint32_t)(db1 - db0),
+                       bar);
 }
 
 template <class L, class S, int FORCE, bool EF, bool SR, int STAGES>
@@ -543,7 +536,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
 // number of co-resident blocks (occupancy API) times the SM count, capped by
 // the number of rows.
 // ---------------------------------------------------------------------------
-constexpr int kStages = 3;
+constexpr int kStages = 2;
 constexpr int kRowThreads = 256;
 constexpr size_t kSmemBudget = 160 * 1024;
 

@@ -166,6 +166,11 @@ class LBM:
             return tr.value, np.array(list(tj))
         return None
 
+    def selftest_wait_timeout(self, clocks: int = 1 << 20) -> int:
+        """Run the bounded-wait probe (lbm_selftest_wait_timeout) and return its
+        raw status; LBM_ERR_TIMEOUT is the expected answer."""
+        return int(_lib.load().lbm_selftest_wait_timeout(self._h, int(clocks)))
+
     def moment_totals_static(self, out):
         """FP64 totals into `out` (a float64 device tensor of 4) without any
         device allocation (lbm_moment_totals_static)."""

@@ -365,3 +365,25 @@ def test_save_load_roundtrip_and_errors():
         LBM("D2V9", (8, 8, 2), 0.8)  # a 2D lattice needs nz = 1
     with pytest.raises(LBMError):
         LBM("D2V9", (8, 8), 0.4)
+
+
+def test_bounded_wait_runs_out_and_reports_timeout():
+    """The bounded mbarrier wait of the row-staged kernels, run on a barrier
+    that nothing completes (limit 2^20 clocks, about 0.5 ms): the block gives
+    up, the next synchronising call reports LBM_ERR_TIMEOUT, and the context
+    keeps working."""
+    from paper_1710_09472_gb300._lib import STATUS
+    from paper_1710_09472_gb300.lbm import LBM
+
+    sim = LBM("D3V19", (32, 6, 5), 0.8, E=(1e-4, 0, 0), storage="f16")
+    sim.init_equilibrium()
+    sim.step(3)
+    before = sim.populations()
+    assert STATUS[sim.selftest_wait_timeout(1 << 20)] == "LBM_ERR_TIMEOUT"
+    assert STATUS[sim.selftest_wait_timeout(1 << 10)] == "LBM_ERR_TIMEOUT"
+    assert np.array_equal(sim.populations(), before)  # reported once, state untouched
+    sim.step(2)
+    tot, _ = sim.moments()
+    assert np.isfinite(tot)
+    assert STATUS[sim.selftest_wait_timeout(0)] == "LBM_ERR_INVALID_ARG"
+    sim.close()
