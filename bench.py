@@ -32,11 +32,12 @@ def workload_name(n: int) -> str:
     return (f"porous-3d-{n}^3 D3V19 FD(theta=1/270,mu=1) spheres r=6 porosity=0.7 seed=1, "
             "tau=0.8 E_x=1e-6 B_z=1e-3 force=term")
 
-# DRAM traffic per launch of the step kernel from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by storage, with the
-# hash of the kernel source it was taken on; reported as null once the
-# source has changed.
-NCU_TRAFFIC = {"f16": (1478718976, "94ce989d984b2b3a")}  # profiles/step_d3v19_f16_porous256.md
+# DRAM traffic per launch of the step kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum) from an ncu capture of a 160^3 launch of the same
+# sphere recipe, scaled to 256^3 by the fluid cells processed; keyed by
+# storage, with the hash of the kernel source it was taken on, and reported
+# as null once the source has changed.
+NCU_TRAFFIC = {"f16": (1257417027, "ce97c9b9b12f4dea")}
 
 FALLBACK_HBM_GBS = 6800.0
 

@@ -86,20 +86,64 @@ __device__ __forceinline__ void load_weights(const float* __restrict__ w_rho, co
     }
 }
 
+// First direction of the shell |e|^2 = s (0 rest, 1 axis, 2 diagonal); the
+// weight w_a and the coefficient k2_a depend on the shell only.
+template <class L>
+__host__ __device__ constexpr int shell_rep(int s) {
+    int r = 0;
+    for (int a = L::Q - 1; a >= 0; --a)
+        if (dev::esq<L>(a) == s) r = a;
+    return r;
+}
+
 // The reverse step at one fluid cell.  h: unscaled deviations of f_t at the
 // cell; lt: lamt; E: the field there; wr, wj: its loss weights (used when WIN).
 // Writes lam = lam_t at the cell and gEc = its dL/dE term; adds
 // {dL/dB, dL/dtau, loss} into acc[0..4].
+//
+// Every sum over directions that the chain rule needs is a moment of
+// mu_a = lt_a w_a: with the forcing-free part F_a = rho w_a [A + Bp (e.v) +
+// Cp (e.v)^2 + k2_a v^2] and the term S_a = rho w_a [Bp (e.E) + 2 Cp (e.u)(e.E)
+// + 2 k2_a (u.E + u.(e x B)/c_s)] of the forward step,
+//   sum lt F   = rho [A M0 + Bp M1.v + Cp v.M2.v + v^2 K0],
+//   d/dv       = rho [Bp M1 + 2 Cp M2 v + 2 K0 v],
+//   sum lt S   = rho [Bp M1.E + 2 Cp u.M2.E + 2 K0 u.E + 2 u.(K1 x B)/c_s],
+// with M0 = sum mu, M1 = sum mu e, M2 = sum mu e e^T, K0 = sum mu k2,
+// K1 = sum mu k2 e.  Since w_a and k2_a are constant on each shell, the
+// per-direction work is only the unweighted shell moments of lt.
 template <class L, int FORCE, bool WIN>
 __device__ __forceinline__ void adjoint_cell(const float* h, const float* lt, const float* E, const KParams& p,
                                              float wr, const float* wj, float* lam, float* gEc, double* acc) {
-    float drho = 0.f, j[3] = {0.f, 0.f, 0.f};
+    constexpr int kAx = shell_rep<L>(1), kDg = shell_rep<L>(2);
+    // forward moments of f_t
+    float drho = 0.f, j[3] = {0.f, 0.f, 0.f}, lth = 0.f;
+    // shell moments of lt: axis (1) and diagonal (2); the rest shell adds to M0 only
+    float L0a = 0.f, L0d = 0.f, L1a[3] = {0.f, 0.f, 0.f}, L1d[3] = {0.f, 0.f, 0.f};
+    float L2a[3] = {0.f, 0.f, 0.f};                     // axis shell: diagonal of sum lt e e^T
+    float L2d[3] = {0.f, 0.f, 0.f}, L2o[3] = {0.f, 0.f, 0.f};  // diagonal shell: diagonal; (xy, xz, yz)
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
+        const int ex = L::c(a, 0), ey = L::c(a, 1), ez = L::c(a, 2);
         drho += h[a];
-        j[0] += L::c(a, 0) * h[a];
-        j[1] += L::c(a, 1) * h[a];
-        j[2] += L::c(a, 2) * h[a];
+        j[0] += ex * h[a];
+        j[1] += ey * h[a];
+        j[2] += ez * h[a];
+        lth = fmaf(lt[a], h[a], lth);
+        const int sh = dev::esq<L>(a);
+        if (sh == 1) {
+            L0a += lt[a];
+            if (ex) { L1a[0] += ex * lt[a]; L2a[0] += lt[a]; }
+            if (ey) { L1a[1] += ey * lt[a]; L2a[1] += lt[a]; }
+            if (ez) { L1a[2] += ez * lt[a]; L2a[2] += lt[a]; }
+        } else if (sh == 2) {
+            L0d += lt[a];
+            if (ex) { L1d[0] += ex * lt[a]; L2d[0] += lt[a]; }
+            if (ey) { L1d[1] += ey * lt[a]; L2d[1] += lt[a]; }
+            if (ez) { L1d[2] += ez * lt[a]; L2d[2] += lt[a]; }
+            if (ex * ey) L2o[0] += ex * ey * lt[a];
+            if (ex * ez) L2o[1] += ex * ez * lt[a];
+            if (ey * ez) L2o[2] += ey * ez * lt[a];
+        }
     }
     j[0] *= p.cs_inv;
     j[1] *= p.cs_inv;
@@ -107,6 +151,25 @@ __device__ __forceinline__ void adjoint_cell(const float* h, const float* lt, co
     const float rho = p.rho0 + drho;
     const float inv_rho = 1.0f / rho;
     const float u[3] = {j[0] * inv_rho, j[1] * inv_rho, j[2] * inv_rho};
+    // weighted moments
+    const float w0 = p.w[0], w1 = p.w[kAx], w2 = p.w[kDg];
+    const float k1 = p.k2[kAx], k2d = p.k2[kDg];
+    const float M0 = w0 * lt[0] + w1 * L0a + w2 * L0d;
+    const float K0 = w0 * p.k2[0] * lt[0] + w1 * k1 * L0a + w2 * k2d * L0d;
+    float M1[3], K1[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        M1[d] = w1 * L1a[d] + w2 * L1d[d];
+        K1[d] = w1 * k1 * L1a[d] + w2 * k2d * L1d[d];
+    }
+    // M2 = w1 diag(L2a) + w2 [L2d on the diagonal, L2o off it]
+    const float Mxx = w1 * L2a[0] + w2 * L2d[0], Myy = w1 * L2a[1] + w2 * L2d[1], Mzz = w1 * L2a[2] + w2 * L2d[2];
+    const float Mxy = w2 * L2o[0], Mxz = w2 * L2o[1], Myz = w2 * L2o[2];
+    auto m2v = [&](const float* v, float* out) {
+        out[0] = Mxx * v[0] + Mxy * v[1] + Mxz * v[2];
+        out[1] = Mxy * v[0] + Myy * v[1] + Myz * v[2];
+        out[2] = Mxz * v[0] + Myz * v[1] + Mzz * v[2];
+    };
     float acc_f[3], ue[3];
     if (FORCE == 0) {
         float uxb[3];
@@ -123,64 +186,22 @@ __device__ __forceinline__ void adjoint_cell(const float* h, const float* lt, co
         ue[2] = u[2];
     }
     const float u2 = ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2];
-    const float Adr = p.A * drho;
+    float M2v[3];
+    m2v(ue, M2v);
+    const float M1v = M1[0] * ue[0] + M1[1] * ue[1] + M1[2] * ue[2];
+    const float vM2v = M2v[0] * ue[0] + M2v[1] * ue[1] + M2v[2] * ue[2];
     const float inv_tau = p.omega;
-
-    float rho_bar = 0.f;
-    float gtau = 0.f;
-    // sums over a of lt_a w_a X for the vector derivatives
-    float s_e[3] = {0.f, 0.f, 0.f};     // sum lt w e
-    float s_eue[3] = {0.f, 0.f, 0.f};   // sum lt w (e.ue) e
-    float s_k2 = 0.f;                   // sum lt w k2
-    float s_eE_e[3] = {0.f, 0.f, 0.f};  // sum lt w (e.E) e        (term mode)
-    float s_k2_e[3] = {0.f, 0.f, 0.f};  // sum lt w k2 e           (term mode)
-    float s_k2_a[3] = {0.f, 0.f, 0.f};  // sum lt w k2 (e x B)/c_s (term mode)
-#pragma unroll
-    for (int a = 0; a < L::Q; ++a) {
-        const float eu = edot<L>(a, ue);
-        const float k2 = p.k2[a];
-        const float Fr = p.w[a] * (p.A + p.Bp * eu + p.Cp * eu * eu + k2 * u2);  // F_a / rho
-        const float heq = p.w[a] * (Adr + rho * (p.Bp * eu + p.Cp * eu * eu + k2 * u2));
-        const float lw = lt[a] * p.w[a];
-        gtau += lt[a] * (h[a] - heq);
-        s_k2 += lw * k2;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const int ed = L::c(a, d);
-            if (ed != 0) {
-                s_e[d] += ed * lw;
-                s_eue[d] += ed * lw * eu;
-            }
-        }
-        if (FORCE == 0) {
-            rho_bar += lt[a] * Fr * inv_tau;
-        } else {
-            const float eE = edot<L>(a, E);
-            float exb[3] = {0.f, 0.f, 0.f};
-            const float e3[3] = {(float)L::c(a, 0), (float)L::c(a, 1), (float)L::c(a, 2)};  // e_a
-            cross3(e3, p.B, exb);
-            const float ua = u[0] * E[0] + u[1] * E[1] + u[2] * E[2] +
-                             (u[0] * exb[0] + u[1] * exb[1] + u[2] * exb[2]) * p.cs_inv;
-            const float Sr = p.w[a] * (p.Bp * eE + 2.f * p.Cp * eu * eE + 2.f * k2 * ua);  // S_a / rho
-            rho_bar += lt[a] * (Fr * inv_tau + Sr);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const int ed = L::c(a, d);
-                if (ed != 0) {
-                    s_eE_e[d] += ed * lw * eE;
-                    s_k2_e[d] += ed * lw * k2;
-                }
-                s_k2_a[d] += lw * k2 * exb[d] * p.cs_inv;
-            }
-        }
-    }
-    gtau *= inv_tau * inv_tau;
-    // dF/dv summed against lt w: rho [Bp s_e + 2 Cp s_eue + 2 s_k2 v]
+    // sum_a lt_a F_a / rho and sum_a lt_a heq_a
+    const float ltF = p.A * M0 + p.Bp * M1v + p.Cp * vM2v + u2 * K0;
+    const float ltHeq = p.A * drho * M0 + rho * (p.Bp * M1v + p.Cp * vM2v + u2 * K0);
+    float gtau = (lth - ltHeq) * inv_tau * inv_tau;
+    // dF/dv summed against mu: rho [Bp M1 + 2 Cp M2 v + 2 K0 v]
     float dF[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) dF[d] = rho * (p.Bp * s_e[d] + 2.f * p.Cp * s_eue[d] + 2.f * s_k2 * ue[d]);
-    float u_bar[3], gBc[3];
+    for (int d = 0; d < 3; ++d) dF[d] = rho * (p.Bp * M1[d] + 2.f * p.Cp * M2v[d] + 2.f * K0 * ue[d]);
+    float rho_bar, u_bar[3], gBc[3];
     if (FORCE == 0) {
+        rho_bar = ltF * inv_tau;
         const float ue_bar[3] = {dF[0] * inv_tau, dF[1] * inv_tau, dF[2] * inv_tau};
         gtau += ue_bar[0] * acc_f[0] + ue_bar[1] * acc_f[1] + ue_bar[2] * acc_f[2];
         float t1[3], t2[3];
@@ -193,17 +214,22 @@ __device__ __forceinline__ void adjoint_cell(const float* h, const float* lt, co
             u_bar[d] = ue_bar[d] + p.tau * t2[d];
         }
     } else {
-        // S_a depends on u through (e.u)(e.E) and u.a_a, and on E, B through a_a:
-        //   sum_a lt_a dS_a/du = rho [2 Cp s_eE_e + 2 (s_k2 E + s_k2_a)]
-        //   sum_a lt_a dS_a/da = dF (at v = u)                  -> dL/dE
-        //   dL/dB = sum_a (abar_a x e_a) / c_s = (2 rho / c_s) u x (sum lt w k2 e)
-        float bxk[3];
-        cross3(u, s_k2_e, bxk);
+        float M2E[3], K1xB[3];
+        m2v(E, M2E);
+        cross3(K1, p.B, K1xB);
+        const float uE = u[0] * E[0] + u[1] * E[1] + u[2] * E[2];
+        const float ltS = p.Bp * (M1[0] * E[0] + M1[1] * E[1] + M1[2] * E[2]) +
+                          2.f * p.Cp * (u[0] * M2E[0] + u[1] * M2E[1] + u[2] * M2E[2]) +
+                          2.f * (K0 * uE + (u[0] * K1xB[0] + u[1] * K1xB[1] + u[2] * K1xB[2]) * p.cs_inv);
+        rho_bar = ltF * inv_tau + ltS;
+        // d(sum lt S)/du = rho [2 Cp M2 E + 2 K0 E + 2 (K1 x B)/c_s]; d/dE = dF; d/dB = (2 rho / c_s) u x K1
+        float uxK[3];
+        cross3(u, K1, uxK);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            u_bar[d] = dF[d] * inv_tau + rho * (2.f * p.Cp * s_eE_e[d] + 2.f * (s_k2 * E[d] + s_k2_a[d]));
+            u_bar[d] = dF[d] * inv_tau + rho * (2.f * p.Cp * M2E[d] + 2.f * (K0 * E[d] + K1xB[d] * p.cs_inv));
             gEc[d] = dF[d];
-            gBc[d] = 2.f * rho * p.cs_inv * bxk[d];
+            gBc[d] = 2.f * rho * p.cs_inv * uxK[d];
         }
     }
     rho_bar -= (u_bar[0] * u[0] + u_bar[1] * u[1] + u_bar[2] * u[2]) * inv_rho;
@@ -354,7 +380,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(
 //     (y + e_ay, z + e_az), read at x + e_ax;
 //   - its windows of lam_{t+1}'s link buffer (bounced gathers) and of the
 //     link descriptors;
-// all by bulk asynchronous copies issued by warp 0, completing on the
+// all by bulk asynchronous copies issued by one thread, completing on the
 // stage's mbarrier (bounded waits, as in the forward's row-staged kernel).
 // One pass over the row's links patches both bounced reads into the staged
 // rows (the solid neighbour's slot, read by that cell alone), so cells read
@@ -367,65 +393,73 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(
 template <class L, class S>
 struct AdjLayout {
     int nx, gcapP, gcapL;  // gcapL also bounds the descriptor window (4-byte elements)
+    int gerow, efrow;      // bytes of the staged dL/dE rows (FP64) and E rows (FP32), 0 when absent
     __device__ __host__ int prow() const { return L::Q * nx * S::kBytes; }
     __device__ __host__ int lrow() const { return L::Q * nx * 4; }
-    __device__ __host__ int bytes() const { return prow() + 4 * nx + gcapP + lrow() + 2 * gcapL; }
-    __device__ unsigned char* masks(unsigned char* st) const { return st + prow(); }
-    __device__ unsigned char* plinks(unsigned char* st) const { return st + prow() + 4 * nx; }
-    __device__ unsigned char* lrows(unsigned char* st) const { return st + prow() + 4 * nx + gcapP; }
+    __device__ __host__ int bytes() const { return gerow + prow() + 4 * nx + gcapP + lrow() + 2 * gcapL + efrow; }
+    __device__ unsigned char* gerows(unsigned char* st) const { return st; }
+    __device__ unsigned char* prows(unsigned char* st) const { return st + gerow; }
+    __device__ unsigned char* masks(unsigned char* st) const { return st + gerow + prow(); }
+    __device__ unsigned char* plinks(unsigned char* st) const { return masks(st) + 4 * nx; }
+    __device__ unsigned char* lrows(unsigned char* st) const { return plinks(st) + gcapP; }
     __device__ unsigned char* llinks(unsigned char* st) const { return lrows(st) + lrow(); }
     __device__ unsigned char* descs(unsigned char* st) const { return llinks(st) + gcapL; }
+    __device__ unsigned char* efrows(unsigned char* st) const { return descs(st) + gcapL; }
 };
 
-// Issued by warp 0: the bulk copies of row `row` into stage `st` (lane 0 arms
-// the barrier with the byte count; lane a copies pull row a and gather row a;
-// four more lanes take the masks and the three windows).
+// Issued by one thread (lane 0 of warp 0; the other lanes return): the bulk
+// copies of row `row` into stage `st`, all completing on `bar`; the window
+// starts are written before the barrier is armed.  With gE, the row's dL/dE
+// (accumulated in place, stored back after the row); with Ef, its E.
 template <class L, class S>
 __device__ __forceinline__ void adj_stage(unsigned char* st, const AdjLayout<L, S>& lay, uint64_t* bar,
-                                          const typename S::T* P, const float* lam, const uint32_t* nbr, int row,
-                                          uint32_t g0, uint32_t g1, uint32_t* ws, const KParams& p) {
-    static_assert(L::Q + 4 <= 32, "one lane per direction");
-    const int lane = threadIdx.x & 31;
+                                          const typename S::T* P, const float* lam, const uint32_t* nbr,
+                                          const double* gE, const float* Ef, int row, uint32_t g0, uint32_t g1,
+                                          uint32_t* ws, const KParams& p) {
+    if ((threadIdx.x & 31) != 0) return;
     const uint32_t prb = (uint32_t)p.nx * S::kBytes, lrb = (uint32_t)p.nx * 4u;
     uint64_t pb0, pb1, lb0, lb1;
     dev::window_bytes(g0, g1, S::kBytes, pb0, pb1);
     dev::window_bytes(g0, g1, 4, lb0, lb1);
-    if (lane == 0) {
-        // window starts first: the arrive releases them to the waiting threads
-        ws[0] = (uint32_t)(pb0 / S::kBytes);
-        ws[1] = (uint32_t)(lb0 / 4);  // the lam-link and descriptor windows start at the same element
-        dev::mbar_expect_tx(bar, L::Q * (prb + lrb) + 4u * (uint32_t)p.nx + (uint32_t)(pb1 - pb0) +
-                                     2u * (uint32_t)(lb1 - lb0));
-    }
-    __syncwarp();
-    if (lane < L::Q) {
-        const unsigned long long kPy = dev::packed_y<L>(), kPz = dev::packed_z<L>();
-        const int a = lane;
-        const int ey = (int)((kPy >> (2 * a)) & 3ull) - 1, ez = (int)((kPz >> (2 * a)) & 3ull) - 1;
-        const int y = row % p.ny, z = row / p.ny;
+    ws[0] = (uint32_t)(pb0 / S::kBytes);
+    ws[1] = (uint32_t)(lb0 / 4);  // the lam-link and descriptor windows start at the same element
+    dev::mbar_expect_tx(bar, L::Q * (prb + lrb) + 4u * (uint32_t)p.nx + (uint32_t)(pb1 - pb0) +
+                                 2u * (uint32_t)(lb1 - lb0) + (uint32_t)lay.gerow + (uint32_t)lay.efrow);
+    const int y = row % p.ny, z = row / p.ny;
+    const int yp = y == p.ny - 1 ? 0 : y + 1, ym = y == 0 ? p.ny - 1 : y - 1;
+    const int zp = z == p.nz - 1 ? 0 : z + 1, zm = z == 0 ? p.nz - 1 : z - 1;
+    unsigned char* pr = lay.prows(st);
+    unsigned char* lr = lay.lrows(st);
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) {
+        const int ey = L::c(a, 1), ez = L::c(a, 2);
         // pull row (y - e_ay, z - e_az) of P_t, gather row (y + e_ay, z + e_az) of lam_{t+1}
-        int ysP = y - ey, zsP = z - ez, ysL = y + ey, zsL = z + ez;
-        ysP = ysP < 0 ? ysP + p.ny : (ysP >= p.ny ? ysP - p.ny : ysP);
-        zsP = zsP < 0 ? zsP + p.nz : (zsP >= p.nz ? zsP - p.nz : zsP);
-        ysL = ysL < 0 ? ysL + p.ny : (ysL >= p.ny ? ysL - p.ny : ysL);
-        zsL = zsL < 0 ? zsL + p.nz : (zsL >= p.nz ? zsL - p.nz : zsL);
-        dev::bulk_load(st + a * prb, P + (int64_t)a * p.N + ((int64_t)zsP * p.ny + ysP) * p.nx, prb, bar);
-        dev::bulk_load(lay.lrows(st) + a * lrb, lam + (int64_t)a * p.N + ((int64_t)zsL * p.ny + ysL) * p.nx, lrb,
+        const int ysP = ey > 0 ? ym : (ey < 0 ? yp : y), zsP = ez > 0 ? zm : (ez < 0 ? zp : z);
+        const int ysL = ey > 0 ? yp : (ey < 0 ? ym : y), zsL = ez > 0 ? zp : (ez < 0 ? zm : z);
+        dev::bulk_load(pr + a * prb, P + (int64_t)a * p.N + ((int64_t)zsP * p.ny + ysP) * p.nx, prb, bar);
+        dev::bulk_load(lr + a * lrb, lam + (int64_t)a * p.N + ((int64_t)zsL * p.ny + ysL) * p.nx, lrb, bar);
+    }
+    dev::bulk_load(lay.masks(st), nbr + (int64_t)row * p.nx, 4u * (uint32_t)p.nx, bar);
+    if (pb1 > pb0)
+        dev::bulk_load(lay.plinks(st), reinterpret_cast<const unsigned char*>(P) + p.gofs + pb0, (uint32_t)(pb1 - pb0),
                        bar);
-    } else if (lane == L::Q) {
-        dev::bulk_load(lay.masks(st), nbr + (int64_t)row * p.nx, 4u * (uint32_t)p.nx, bar);
-    } else if (lane == L::Q + 1) {
-        if (pb1 > pb0)
-            dev::bulk_load(lay.plinks(st), reinterpret_cast<const unsigned char*>(P) + p.gofs + pb0,
-                           (uint32_t)(pb1 - pb0), bar);
-    } else if (lane == L::Q + 2) {
-        if (lb1 > lb0)
-            dev::bulk_load(lay.llinks(st), reinterpret_cast<const unsigned char*>(lam) + p.lgofs + lb0,
-                           (uint32_t)(lb1 - lb0), bar);
-    } else if (lane == L::Q + 3) {
-        if (lb1 > lb0)
-            dev::bulk_load(lay.descs(st), reinterpret_cast<const unsigned char*>(p.ldesc) + lb0,
-                           (uint32_t)(lb1 - lb0), bar);
+    if (lb1 > lb0) {
+        dev::bulk_load(lay.llinks(st), reinterpret_cast<const unsigned char*>(lam) + p.lgofs + lb0,
+                       (uint32_t)(lb1 - lb0), bar);
+        dev::bulk_load(lay.descs(st), reinterpret_cast<const unsigned char*>(p.ldesc) + lb0, (uint32_t)(lb1 - lb0),
+                       bar);
+    }
+    if (lay.gerow) {
+#pragma unroll
+        for (int d = 0; d < L::D; ++d)
+            dev::bulk_load(lay.gerows(st) + d * p.nx * 8, gE + (int64_t)d * p.N + (int64_t)row * p.nx,
+                           (uint32_t)p.nx * 8u, bar);
+    }
+    if (lay.efrow) {
+#pragma unroll
+        for (int d = 0; d < L::D; ++d)
+            dev::bulk_load(lay.efrows(st) + d * p.nx * 4, Ef + (int64_t)d * p.N + (int64_t)row * p.nx,
+                           (uint32_t)p.nx * 4u, bar);
     }
 }
 
@@ -441,7 +475,7 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
     using T = typename S::T;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int nx = p.nx;
-    const AdjLayout<L, S> lay{nx, gcapP, gcapL};
+    const AdjLayout<L, S> lay{nx, gcapP, gcapL, gE ? L::D * nx * 8 : 0, EF ? L::D * nx * 4 : 0};
     const int sbytes = lay.bytes();
     float* outrow = reinterpret_cast<float*>(smem_raw + STAGES * sbytes);
     uint32_t* flist = reinterpret_cast<uint32_t*>(outrow + L::Q * nx);
@@ -474,7 +508,8 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
             if (rk < R) {
                 uint32_t g0, g1;
                 range(rk, g0, g1);
-                adj_stage<L, S>(smem_raw + k * sbytes, lay, &bar[k], P, lam_in, nbr, rk, g0, g1, wstart[k], p);
+                adj_stage<L, S>(smem_raw + k * sbytes, lay, &bar[k], P, lam_in, nbr, gE, Ef, rk, g0, g1, wstart[k],
+                                p);
             }
         }
     }
@@ -490,7 +525,9 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
             if (p.status) atomicExch(p.status, 2);
         }
         unsigned char* st = smem_raw + cs * sbytes;
-        T* prow = reinterpret_cast<T*>(st);
+        T* prow = reinterpret_cast<T*>(lay.prows(st));
+        double* ge_s = reinterpret_cast<double*>(lay.gerows(st));
+        const float* ef_s = reinterpret_cast<const float*>(lay.efrows(st));
         float* lrow = reinterpret_cast<float*>(lay.lrows(st));
         const uint32_t* desc = reinterpret_cast<const uint32_t*>(lay.descs(st));
         const uint32_t d0 = wstart[cs][1];
@@ -509,7 +546,8 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
                 const int sn = (it + STAGES - 1) % STAGES;
                 uint32_t n0, n1;
                 range(rn, n0, n1);
-                adj_stage<L, S>(smem_raw + sn * sbytes, lay, &bar[sn], P, lam_in, nbr, rn, n0, n1, wstart[sn], p);
+                adj_stage<L, S>(smem_raw + sn * sbytes, lay, &bar[sn], P, lam_in, nbr, gE, Ef, rn, n0, n1,
+                                wstart[sn], p);
             }
         }
         const int nf = nfluid;
@@ -528,14 +566,20 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
                     lt[a] = lrow[a * nx + (ex > 0 ? xp : (ex < 0 ? xm : x))];
                 }
                 float E[3], wr, wj[3], lam[L::Q], gEc[3];
-                load_E<L, EF>(Ef, p, cell, E);
+                if (EF) {
+                    E[0] = ef_s[x];
+                    E[1] = ef_s[nx + x];
+                    E[2] = (L::D == 3) ? ef_s[2 * nx + x] : 0.f;
+                } else {
+                    load_E<L, false>(Ef, p, cell, E);
+                }
                 load_weights<L, WIN>(w_rho, w_j, p, cell, wr, wj);
                 adjoint_cell<L, FORCE, WIN>(h, lt, E, p, wr, wj, lam, gEc, acc);
 #pragma unroll
                 for (int b = 0; b < L::Q; ++b) outrow[b * nx + x] = lam[b];
                 if (gE) {
 #pragma unroll
-                    for (int d = 0; d < L::D; ++d) gE[(int64_t)d * p.N + cell] += (double)gEc[d];
+                    for (int d = 0; d < L::D; ++d) ge_s[d * nx + x] += (double)gEc[d];
                 }
             } else {
 #pragma unroll
@@ -548,6 +592,12 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
             // lane a of warp 0: the bulk store of direction a, in its own group
             const int a = threadIdx.x;
             dev::bulk_store(lam_out + (int64_t)a * p.N + rowbase, outrow + a * nx, (uint32_t)nx * 4u);
+            dev::bulk_commit();
+        } else if (gE && threadIdx.x < L::Q + L::D) {
+            // lanes Q .. Q + D - 1: the row's updated dL/dE back from the stage
+            // (the stage is refilled only after these lanes' reads are done)
+            const int d = threadIdx.x - L::Q;
+            dev::bulk_store(gE + (int64_t)d * p.N + rowbase, ge_s + d * nx, (uint32_t)nx * 8u);
             dev::bulk_commit();
         }
         // link copies of lam_t: slot k of (x, b) takes lam_bbar(x)
@@ -595,9 +645,11 @@ bool launch_rows(const void* P, const float* lam_in, float* lam_out, const uint3
                  const float* w_rho, const float* w_j, double* gE, double* slots, int64_t slot_blocks,
                  const KParams& p, cudaStream_t s) {
     if ((p.nx * S::kBytes) % 16 != 0 || p.nx % 4 != 0 || p.nx < 32 || p.nx > 32 * kAdjMaxChunks) return false;
+    if (reinterpret_cast<uintptr_t>(gE) % 16 != 0) return false;  // dL/dE rows move by bulk copies
     const int gcapP = dev::window_cap(p.max_row_links, S::kBytes);
     const int gcapL = dev::window_cap(p.max_row_links, 4);
-    const size_t stage = (size_t)AdjLayout<L, S>{p.nx, gcapP, gcapL}.bytes();
+    const size_t stage =
+        (size_t)AdjLayout<L, S>{p.nx, gcapP, gcapL, gE ? L::D * p.nx * 8 : 0, EF ? L::D * p.nx * 4 : 0}.bytes();
     const size_t smem = kAdjStages * stage + (size_t)L::Q * p.nx * 4 + 4 * (size_t)p.nx;
     if (smem > kAdjSmemBudget) return false;
     const int threads = p.nx >= kAdjThreads ? kAdjThreads : ((p.nx + 31) / 32) * 32;
