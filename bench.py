@@ -293,9 +293,57 @@ def run_gpu(args, rank, world):
         "clocks": clocks,
         "kernel_source": src_hash,
     }
+    if args.adjoint_512 > 0:
+        result["adjoint_512"] = adjoint_512(args.adjoint_512, dev, stream)
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(mask)
     return result
+
+
+def adjoint_512(T: int, dev, stream):
+    """Forward + full adjoint on the 512^3 porous box (spheres r = 10, porosity
+    0.65, seed 5; E_x = 2e-6, B_z = 5e-4, tau 0.8, FP16-deviation storage):
+    loss = mean x-current after T steps, dL/dE(x) per cell, with the kept
+    forward states limited to what fits 180 GB of device memory together with
+    the adjoint fields, the context's own states and dL/dE (the binomial
+    schedule when the segment schedule does not fit)."""
+    import torch
+
+    from paper_1710_09472_gb300 import workloads as wl
+    from paper_1710_09472_gb300.lbm import LBM
+
+    n = 512
+    mask, count = wl.boolean_obstacles((n, n, n), 10.0, 0.65, 5)
+    sim = LBM("D3V19", (n, n, n), 0.8, E=(2e-6, 0.0, 0.0), B=(0.0, 0.0, 5e-4), storage="f16", force="term",
+              stream=stream)
+    sim.set_geometry(torch.from_numpy(mask.reshape(-1)).to(dev))
+    del mask
+    sim.init_equilibrium()
+    N = sim.N
+    n_fluid = sim.info()["n_fluid"]
+    wj = torch.zeros(3 * N, dtype=torch.float32, device=dev)
+    wj[:N] = 1.0 / n_fluid
+    dE = torch.empty(3 * N, dtype=torch.float64, device=dev)
+    state = sim.adjoint_stats()["state_bytes"]
+    # an adjoint field: FP32 lambda plus one FP32 per link (the state holds one FP16 per link)
+    lam_field = 4 * 19 * N + 2 * max(0, state - 2 * 19 * N) + 1024
+    fixed = 2 * lam_field + 2 * state + dE.numel() * 8 + wj.numel() * 4
+    budget = 180 * 10**9 - fixed
+    sim.set_memory_budget(budget)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = sim.adjoint(T - 1, T, None, wj, 0, dL_dE=dE)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    st = sim.adjoint_stats()
+    out = {"T": T, "seconds": round(dt, 2), "ms_per_step": round(dt * 1e3 / T, 3), "schedule": st["schedule"],
+           "states_kept": st["states"], "state_gb": round(state / 1e9, 3),
+           "device_gb_budgeted": round((st["states"] * state + fixed) / 1e9, 1),
+           "forward_steps": st["forward_steps"], "reverse_steps": st["reverse_steps"],
+           "dL_dtau": res["dL_dtau"], "dL_dBz": float(res["dL_dB"][2]), "spheres": count, "fluid_cells": n_fluid,
+           "dL_dE_sum_x": float(dE[:N].sum())}
+    sim.close()
+    return out
 
 
 def _oracle_sample(mask, box: int):
@@ -372,6 +420,8 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--adjoint-checkpoint", type=int, default=14)
     ap.add_argument("--n", type=int, default=256, help="box edge (256 is the benchmark; smaller for profiling)")
+    ap.add_argument("--adjoint-512", type=int, default=0,
+                    help="also run the 512^3 forward + full adjoint over this many steps within 180 GB (0 = off)")
     args = ap.parse_args()
     WORKLOAD["n"] = args.n
     if args.warmup < 3:

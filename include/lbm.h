@@ -184,6 +184,18 @@ lbm_status lbm_get_populations(lbm_ctx* ctx, float* f, int deviation);
  * Synchronises.  Errors: INVALID_ARG, STATE, CUDA, NONFINITE. */
 lbm_status lbm_window_totals(lbm_ctx* ctx, int64_t t_begin, int64_t t_end, double out[4]);
 
+/* Device bytes that an lbm_adjoint call with checkpoint_every = 0 may spend
+ * on kept forward states (0, the default: 95% of the free device memory left
+ * after the adjoint fields).  The adjoint fields and gradient scratch come on
+ * top.  Infrastructure for the checkpoint schedule; the paper has no
+ * counterpart.  Errors: INVALID_ARG. */
+lbm_status lbm_set_memory_budget(lbm_ctx* ctx, uint64_t bytes);
+
+/* Schedule of the last lbm_adjoint call and the size of one kept state:
+ * out = {0 segment / 1 binomial, state buffers held, forward steps run,
+ * reverse steps run, bytes per state buffer}.  Errors: INVALID_ARG. */
+lbm_status lbm_adjoint_stats(const lbm_ctx* ctx, int64_t out[5]);
+
 /* Failure-path self-check (the paper has no counterpart).  Launches one block
  * that waits on an mbarrier that nothing completes, using the same bounded
  * wait as the row-staged kernels but a limit of `clocks` SM cycles
@@ -199,11 +211,22 @@ lbm_status lbm_selftest_wait_timeout(lbm_ctx* ctx, int64_t clocks);
  * hand-written adjoint of the Sec. 9.1 step, with the Sec. 7 forcing):
  *   L = sum_{t_begin < t <= t_end} sum_x [w_rho(x) rho_t(x) + w_j(x) . j_t(x)],
  * where rho_t, j_t are the moments after t steps (lbm_moments convention).
- * The call runs t_end forward steps (leaving the context at step t_end, as
- * lbm_step would), keeping a copy of the state every checkpoint_every steps
- * (0 = about sqrt(t_end)), then sweeps backwards segment by segment: each
- * segment is replayed forward from its checkpoint storing every state, and
- * the reverse step kernel maps lam_{t+1} = dL/df_{t+1} to lam_t.
+ * The call leaves the context at step t_end, as lbm_step would.  The reverse
+ * step kernel maps lam_{t+1} = dL/df_{t+1} to lam_t and needs the forward
+ * state at t; checkpoint_every chooses how those states are kept:
+ *   K > 0 : segment schedule: t_end forward steps keeping a copy every K
+ *           steps, then each segment is replayed from its copy storing every
+ *           state (ceil(t_end / K) + K - 1 states; 2 t_end forward steps);
+ *   K = 0 : the segment schedule with K = ceil(sqrt(t_end)) when it fits the
+ *           memory budget (lbm_set_memory_budget), else the binomial schedule
+ *           with as many snapshots as fit;
+ *   K < 0 : binomial schedule with -K snapshots: the recursion of Griewank's
+ *           revolve (snapshots placed so that s snapshots and r sweeps cover
+ *           C(s + r, s) steps), holding -K + 2 states (the initial state and a
+ *           work buffer besides the snapshots).
+ * Forward states are recomputed bit for bit (the stochastic-rounding stream
+ * depends on the global step index only), so every schedule gives the same
+ * gradients.
  *   w_rho[N], w_j[D * N] : FP32 loss weights, host or device, NULL = 0.
  *   t_begin, t_end       : -1 <= t_begin < t_end, t_end >= 1.
  *   dL_dE   : [D * N] FP64 device, per-cell dL/dE(x) (overwritten), or NULL.
@@ -211,10 +234,10 @@ lbm_status lbm_selftest_wait_timeout(lbm_ctx* ctx, int64_t clocks);
  *   dL_dB   : 3 host doubles, dL/dB (2D: only the z component), or NULL.
  *   dL_dtau : host double, or NULL.   loss : host double (L itself), or NULL.
  *   dL_df0  : [Q * N] FP32 device, dL/df_0 (population layout), or NULL.
- * Device memory: (ceil(t_end / K) + K - 1) copies of the stored state
- * (populations + bounce-back link buffer) plus two FP32 adjoint fields (Q N
- * values + one per bounce-back link each), allocated for the call and
- * released before it returns.  Gradients accumulate in FP64; the sweep is deterministic.
+ * Device memory: the schedule's states (populations + bounce-back link
+ * buffer each) plus two FP32 adjoint fields (Q N values + one per bounce-back
+ * link each), allocated for the call and released before it returns.
+ * Gradients accumulate in FP64; the sweep is deterministic.
  * Synchronises.  Errors: INVALID_ARG, STATE, OOM (with the size needed), CUDA,
  * NONFINITE. */
 lbm_status lbm_adjoint(lbm_ctx* ctx, const float* w_rho, const float* w_j, int64_t t_begin, int64_t t_end,

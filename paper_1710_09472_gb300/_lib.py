@@ -48,6 +48,8 @@ SIGNATURES = {
     "lbm_status_string": (ctypes.c_char_p, [_i]),
     "lbm_launch_count": (_i64, [_vp]),
     "lbm_selftest_wait_timeout": (_i, [_vp, _i64]),
+    "lbm_set_memory_budget": (_i, [_vp, ctypes.c_uint64]),
+    "lbm_adjoint_stats": (_i, [_vp, _vp]),
 }
 
 

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <functional>
 #include <vector>
 
 #include "lbm_internal.h"
@@ -738,6 +739,19 @@ lbm_status lbm_window_totals(lbm_ctx* c, int64_t t_begin, int64_t t_end, double 
     return LBM_OK;
 }
 
+lbm_status lbm_set_memory_budget(lbm_ctx* c, uint64_t bytes) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    c->mem_budget = (size_t)bytes;
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_stats(const lbm_ctx* c, int64_t out[5]) {
+    if (!c || !out) return LBM_ERR_INVALID_ARG;
+    for (int k = 0; k < 4; ++k) out[k] = c->adj_stats[k];
+    out[4] = (int64_t)c->state_bytes;
+    return LBM_OK;
+}
+
 lbm_status lbm_selftest_wait_timeout(lbm_ctx* c, int64_t clocks) {
     if (!c) return LBM_ERR_INVALID_ARG;
     if (clocks < 1 || clocks > (1ll << 31))
@@ -760,11 +774,11 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
     if (!c->has_state) return fail(c, LBM_ERR_STATE, "lbm_adjoint before lbm_init_equilibrium");
     if (t_end < 1 || t_begin < -1 || t_begin >= t_end)
         return fail(c, LBM_ERR_INVALID_ARG, "lbm_adjoint: need -1 <= t_begin < t_end and t_end >= 1");
-    if (checkpoint_every < 0) return fail(c, LBM_ERR_INVALID_ARG, "lbm_adjoint: checkpoint_every < 0");
+
     if ((dL_dE && !is_device_ptr(dL_dE)) || (dL_df0 && !is_device_ptr(dL_df0)))
         return fail(c, LBM_ERR_INVALID_ARG, "lbm_adjoint: dL_dE and dL_df0 must be device pointers");
     const int64_t T = t_end;
-    int64_t K = checkpoint_every;
+    int64_t K = checkpoint_every < 0 ? 0 : checkpoint_every;
     if (K == 0) {
         K = 1;
         while (K * K < T) ++K;
@@ -781,15 +795,38 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
     p.lgofs = lgofs;
     const int64_t nslot = lbm::adjoint_slot_count(p);
 
-    // --- memory: nseg checkpoints + (K - 1) replay slots + 2 adjoint fields ---
+    // --- memory and schedule ---
+    // Fixed: two adjoint fields, the gradient slots, staged loss weights.
+    // States: the segment schedule (K > 0, or K = 0 when it fits) keeps
+    // ceil(T/K) checkpoints and K - 1 replay states; the binomial schedule
+    // keeps the initial state, one work buffer and s snapshots.
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    const size_t need = (size_t)(nseg + K - 1) * pop_bytes + 2 * lam_alloc + sizeof(double) * (nslot + 8) +
-                        sizeof(float) * (size_t)c->N * (1 + c->D);
-    if (need > free_b)
+    const size_t fixed = 2 * lam_alloc + sizeof(double) * (nslot + 8) + sizeof(float) * (size_t)c->N * (1 + c->D);
+    // bytes for the kept forward states: the budget, or 95% of what the fixed part leaves free
+    const size_t avail = free_b > fixed ? free_b - fixed : 0;
+    const size_t budget = c->mem_budget ? std::min(c->mem_budget, avail) : avail - avail / 20;
+    const int64_t states_fit = (int64_t)(budget / pop_bytes);
+    bool binomial = checkpoint_every < 0 || (checkpoint_every == 0 && nseg + K - 1 > states_fit);
+    int64_t nsnap = 0;  // binomial: snapshots besides the initial state and the work buffer
+    if (checkpoint_every < 0) {
+        nsnap = std::min<int64_t>(-checkpoint_every, T);
+        if ((size_t)(nsnap + 2) * pop_bytes + fixed > free_b)
+            return fail(c, LBM_ERR_OOM, "lbm_adjoint: %lld snapshots need %.2f GB, %.2f GB free", (long long)nsnap,
+                        ((size_t)(nsnap + 2) * pop_bytes + fixed) / 1e9, free_b / 1e9);
+    } else if (binomial) {
+        nsnap = std::min<int64_t>(states_fit - 2, T);
+        if (nsnap < 0)
+            return fail(c, LBM_ERR_OOM, "lbm_adjoint: the budget of %.2f GB holds fewer than 2 states of %.2f GB",
+                        budget / 1e9, pop_bytes / 1e9);
+    } else if ((size_t)(nseg + K - 1) * pop_bytes + fixed > free_b) {
         return fail(c, LBM_ERR_OOM, "lbm_adjoint: needs %.2f GB of device memory, %.2f GB free; choose "
-                    "checkpoint_every near sqrt(t_end)", need / 1e9, free_b / 1e9);
-    std::vector<void*> ckpt(nseg, nullptr), seg(K, nullptr);
+                    "checkpoint_every near sqrt(t_end), or 0 for a schedule sized to the memory budget",
+                    ((size_t)(nseg + K - 1) * pop_bytes + fixed) / 1e9, free_b / 1e9);
+    }
+    std::vector<void*> ckpt(binomial ? 0 : nseg, nullptr), seg(binomial ? 0 : K, nullptr), snaps;
+    void* base = nullptr;   // binomial: the state at t = 0
+    void* work1 = nullptr;  // binomial: second work buffer
     float* lam[2] = {nullptr, nullptr};
     double* slots = nullptr;
     double* red = nullptr;
@@ -799,6 +836,9 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
         cudaStreamSynchronize(c->stream);
         for (void* q : ckpt) cudaFree(q);
         for (size_t k = 1; k < seg.size(); ++k) cudaFree(seg[k]);
+        for (void* q : snaps) cudaFree(q);
+        cudaFree(base);
+        cudaFree(work1);
         cudaFree(lam[0]);
         cudaFree(lam[1]);
         cudaFree(slots);
@@ -813,8 +853,15 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
             return st;                                         \
         }                                                      \
     } while (0)
-    for (int64_t s = 0; s < nseg; ++s) ADJ_CHECK(cudaMalloc(&ckpt[s], pop_bytes));
-    for (int64_t k = 1; k < K; ++k) ADJ_CHECK(cudaMalloc(&seg[k], pop_bytes));
+    if (binomial) {
+        ADJ_CHECK(cudaMalloc(&base, pop_bytes));
+        ADJ_CHECK(cudaMalloc(&work1, pop_bytes));
+        snaps.assign((size_t)nsnap, nullptr);
+        for (auto& q : snaps) ADJ_CHECK(cudaMalloc(&q, pop_bytes));
+    } else {
+        for (int64_t s = 0; s < nseg; ++s) ADJ_CHECK(cudaMalloc(&ckpt[s], pop_bytes));
+        for (int64_t k = 1; k < K; ++k) ADJ_CHECK(cudaMalloc(&seg[k], pop_bytes));
+    }
     ADJ_CHECK(cudaMalloc((void**)&lam[0], lam_alloc));
     ADJ_CHECK(cudaMalloc((void**)&lam[1], lam_alloc));
     ADJ_CHECK(cudaMalloc((void**)&slots, sizeof(double) * nslot));
@@ -840,39 +887,124 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
     const int vel = c->lat.vel, sto = c->storage, force = c->lat.force;
     const bool ef = c->use_Efield, sr = c->stochastic;
     const int64_t step0 = c->steps;
-    // --- forward with checkpoints every K steps ---
-    for (int64_t t = 0; t < T; ++t) {
-        if (t % K == 0)
-            ADJ_CHECK(cudaMemcpyAsync(ckpt[t / K], c->pop[c->cur], pop_bytes, cudaMemcpyDeviceToDevice, c->stream));
-        p.step = (uint32_t)(step0 + t);
-        c->launches += lbm::launch_step(vel, sto, force, ef, sr, c->pop[c->cur], c->pop[c->cur ^ 1], c->nbr,
-                                        c->Efield, p, c->stream);
-        c->cur ^= 1;
-    }
-    ADJ_CHECK(cudaGetLastError());
-    // --- seed lam_T at the final state ---
     int li = 0;
-    c->launches += lbm::launch_adjoint_seed(vel, sto, c->pop[c->cur], c->nbr, wr_d, wj_d, lam[li], slots,
-                                            T > t_begin && T <= t_end, p, c->stream);
-    // --- reverse sweep, one segment at a time ---
-    for (int64_t s = nseg - 1; s >= 0; --s) {
-        const int64_t t0 = s * K, t1 = std::min(t0 + K, T);
-        seg[0] = ckpt[s];
-        for (int64_t t = t0; t < t1 - 1; ++t)
-        {
-            p.step = (uint32_t)(step0 + t);
-            c->launches += lbm::launch_step(vel, sto, force, ef, sr, seg[t - t0], seg[t - t0 + 1], c->nbr, c->Efield,
-                                            p, c->stream);
-        }
-        for (int64_t t = t1 - 1; t >= t0; --t) {
-            const bool win = t > t_begin && t <= t_end;
-            c->launches += lbm::launch_adjoint_step(vel, sto, force, ef, win, seg[t - t0], lam[li], lam[li ^ 1],
-                                                    c->nbr, c->Efield, wr_d, wj_d, dL_dE, slots, p, c->stream);
-            li ^= 1;
+    int64_t fwd_steps = 0;
+    // one forward step of global index step0 + t, in -> out
+    auto fstep = [&](int64_t t, const void* in, void* out) {
+        p.step = (uint32_t)(step0 + t);
+        c->launches += lbm::launch_step(vel, sto, force, ef, sr, in, out, c->nbr, c->Efield, p, c->stream);
+        ++fwd_steps;
+    };
+    // one reverse step at t from the state at t: lam_{t+1} -> lam_t
+    auto rstep = [&](int64_t t, const void* state) {
+        const bool win = t > t_begin && t <= t_end;
+        c->launches += lbm::launch_adjoint_step(vel, sto, force, ef, win, state, lam[li], lam[li ^ 1], c->nbr,
+                                                c->Efield, wr_d, wj_d, dL_dE, slots, p, c->stream);
+        li ^= 1;
+    };
+    auto seed = [&](const void* state_T) {
+        c->launches += lbm::launch_adjoint_seed(vel, sto, state_T, c->nbr, wr_d, wj_d, lam[li], slots,
+                                                T > t_begin && T <= t_end, p, c->stream);
+    };
+    if (!binomial) {
+        // --- forward with checkpoints every K steps ---
+        for (int64_t t = 0; t < T; ++t) {
+            if (t % K == 0)
+                ADJ_CHECK(
+                    cudaMemcpyAsync(ckpt[t / K], c->pop[c->cur], pop_bytes, cudaMemcpyDeviceToDevice, c->stream));
+            fstep(t, c->pop[c->cur], c->pop[c->cur ^ 1]);
+            c->cur ^= 1;
         }
         ADJ_CHECK(cudaGetLastError());
+        seed(c->pop[c->cur]);
+        // --- reverse sweep, one segment at a time: replay storing every state ---
+        for (int64_t s = nseg - 1; s >= 0; --s) {
+            const int64_t t0 = s * K, t1 = std::min(t0 + K, T);
+            seg[0] = ckpt[s];
+            for (int64_t t = t0; t < t1 - 1; ++t) fstep(t, seg[t - t0], seg[t - t0 + 1]);
+            for (int64_t t = t1 - 1; t >= t0; --t) rstep(t, seg[t - t0]);
+            ADJ_CHECK(cudaGetLastError());
+        }
+        seg[0] = nullptr;
+    } else {
+        // --- binomial schedule (the recursion of Griewank's revolve): with s
+        // free snapshots, a span of n steps is split so that the right part
+        // [m, t1) is reversed first with s - 1 snapshots and the left part
+        // [t0, m) after it with s; with r the smallest number of sweeps such
+        // that C(s + r, s) >= n, the left part takes C(s + r - 1, s) steps.
+        // Each forward state is recomputed bit for bit (the rounding stream
+        // depends only on the global step index), so every schedule gives the
+        // same gradients.  The state at T ends in the context's other buffer.
+        ADJ_CHECK(cudaMemcpyAsync(base, c->pop[c->cur], pop_bytes, cudaMemcpyDeviceToDevice, c->stream));
+        void* work[2] = {c->pop[c->cur], work1};
+        void* final_state = c->pop[c->cur ^ 1];
+        bool seeded = false;
+        auto binom = [](int64_t n, int64_t k) {  // C(n, k), saturating
+            double v = 1.0;
+            for (int64_t i = 1; i <= k; ++i) {
+                v = v * (double)(n - k + i) / (double)i;
+                if (v > 4e18) return (int64_t)4e18;
+            }
+            return (int64_t)(v + 0.5);
+        };
+        // state at t0 + n from `from` (at t0): the last step writes `dst`
+        auto advance_to = [&](const void* from, int64_t t0, int64_t n, void* dst) {
+            const void* in = from;
+            for (int64_t k = 0; k < n; ++k) {
+                void* out = (k == n - 1) ? dst : work[k & 1];
+                fstep(t0 + k, in, out);
+                in = out;
+            }
+        };
+        // state at t0 + n in a work buffer (or `from` itself when n = 0)
+        auto advance_w = [&](const void* from, int64_t t0, int64_t n) {
+            const void* in = from;
+            for (int64_t k = 0; k < n; ++k) {
+                fstep(t0 + k, in, work[k & 1]);
+                in = work[k & 1];
+            }
+            return in;
+        };
+        std::vector<void*> pool = snaps;
+        // reverses [t0, t1) with the state at t0 in `at`; recursion depth <= s + 1
+        std::function<void(int64_t, int64_t, const void*)> reverse = [&](int64_t t0, int64_t t1, const void* at) {
+            while (t1 > t0) {
+                const int64_t n = t1 - t0;
+                if (!seeded) {  // the first leaf is the rightmost: make the state at T and seed lam_T
+                    if (n == 1 || pool.empty()) {
+                        advance_to(at, t0, n, final_state);
+                        seed(final_state);
+                        seeded = true;
+                    }
+                }
+                if (n == 1) {
+                    rstep(t0, at);
+                    return;
+                }
+                if (pool.empty()) {  // no snapshot left: recompute from t0 for every step
+                    for (int64_t t = t1 - 1; t >= t0; --t) rstep(t, advance_w(at, t0, t - t0));
+                    return;
+                }
+                const int64_t sfree = (int64_t)pool.size();
+                int64_t r = 1;
+                while (binom(sfree + r, sfree) < n) ++r;
+                const int64_t left = std::max<int64_t>(1, std::min<int64_t>(binom(sfree + r - 1, sfree), n - 1));
+                void* snap = pool.back();
+                pool.pop_back();
+                advance_to(at, t0, left, snap);
+                reverse(t0 + left, t1, snap);
+                pool.push_back(snap);
+                t1 = t0 + left;  // then the left part, with the snapshot free again
+            }
+        };
+        reverse(0, T, base);
+        ADJ_CHECK(cudaGetLastError());
+        c->cur ^= 1;  // the context's current state is the state at T
     }
-    seg[0] = nullptr;
+    c->adj_stats[0] = binomial ? 1 : 0;
+    c->adj_stats[1] = binomial ? 2 + nsnap : nseg + K - 1;
+    c->adj_stats[2] = fwd_steps;
+    c->adj_stats[3] = T;
     if (dL_df0) ADJ_CHECK(cudaMemcpyAsync(dL_df0, lam[li], lam_bytes, cudaMemcpyDeviceToDevice, c->stream));
     c->launches += lbm::launch_reduce_slots(slots, nslot / 5, 5, red, c->stream);
     double host[5];

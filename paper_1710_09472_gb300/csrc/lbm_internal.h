@@ -246,6 +246,8 @@ struct lbm_ctx {
     double* totals_dev = nullptr;
     double* totals_host = nullptr;  // pinned, 4 doubles
     unsigned long long* count_dev = nullptr;
+    size_t mem_budget = 0;         // device bytes an lbm_adjoint call may allocate (0: free memory)
+    int64_t adj_stats[4] = {0, 0, 0, 0};  // last lbm_adjoint: schedule, state buffers, forward steps, reverse steps
     int* status_host = nullptr;    // mapped pinned word written by kernels on a wait timeout
     int* status_dev = nullptr;     // its device address
     float* stage = nullptr;  // device staging for host-pointer arguments

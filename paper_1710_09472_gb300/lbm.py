@@ -166,6 +166,16 @@ class LBM:
             return tr.value, np.array(list(tj))
         return None
 
+    def set_memory_budget(self, nbytes: int):
+        """Device bytes an adjoint call with checkpoint_every=0 may allocate (0 = free memory)."""
+        _lib.check(_lib.load().lbm_set_memory_budget(self._h, int(nbytes)), self._h, "lbm_set_memory_budget")
+
+    def adjoint_stats(self) -> dict:
+        out = (ctypes.c_int64 * 5)()
+        _lib.check(_lib.load().lbm_adjoint_stats(self._h, out), self._h, "lbm_adjoint_stats")
+        return {"schedule": "binomial" if out[0] else "segments", "states": int(out[1]),
+                "forward_steps": int(out[2]), "reverse_steps": int(out[3]), "state_bytes": int(out[4])}
+
     def selftest_wait_timeout(self, clocks: int = 1 << 20) -> int:
         """Run the bounded-wait probe (lbm_selftest_wait_timeout) and return its
         raw status; LBM_ERR_TIMEOUT is the expected answer."""

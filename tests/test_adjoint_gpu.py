@@ -112,6 +112,14 @@ def test_adjoint_many_rows_porous_3d(force):
                       checkpoint_every=3, dL_dE=dE, dL_df0=lam0)
     _compare(sim, res, dE, lam0, "D3V19", shape, mask, B, Ef, rho0, u0, wr, wj, tau, T, tb, force)
     sim.close()
+    # without dL/dE the staged reverse kernel skips the dL/dE rows; the other
+    # gradients and the loss are the same numbers
+    sim = _gpu_sim("D3V19", shape, mask, B, Ef, rho0, u0, tau, force)
+    res2 = sim.adjoint(tb, T, torch.from_numpy(wr.reshape(-1)).cuda(), torch.from_numpy(wj.reshape(-1)).cuda(),
+                       checkpoint_every=3)
+    assert res2["loss"] == res["loss"] and res2["dL_dtau"] == res["dL_dtau"]
+    assert np.array_equal(np.asarray(res2["dL_dB"]), np.asarray(res["dL_dB"]))
+    sim.close()
 
 
 def test_checkpoint_spacing_does_not_change_the_result():
@@ -127,6 +135,55 @@ def test_checkpoint_spacing_does_not_change_the_result():
     for res, dE in outs[1:]:
         assert res["loss"] == outs[0][0]["loss"] and res["dL_dtau"] == outs[0][0]["dL_dtau"]
         assert np.array_equal(dE, outs[0][1])
+
+
+@pytest.mark.parametrize("vel", ["D2V9", "D3V19"])
+def test_binomial_schedule_matches_segments(vel):
+    """checkpoint_every < 0 (binomial schedule with -K snapshots) and the
+    budget-driven automatic choice give the same numbers, bit for bit, as the
+    segment schedule: every forward state is recomputed exactly.  The forward
+    step counts follow the schedules (2 T for segments; at most T (r + 1) for
+    s snapshots and r sweeps with C(s + r, s) >= T)."""
+    import math
+
+    shape, mask, B, Ef, rho0, u0, wr, wj = _case(vel)
+    T, tb = 23, 9
+    runs = []
+    for K in (5, -1, -3, -7, -40, 0):
+        sim = _gpu_sim(vel, shape, mask, B, Ef, rho0, u0, 0.8, "term", storage="f16")
+        if K == 0:
+            # a budget below two states is refused; one of six states (the
+            # segment schedule needs 5 + 4) forces the automatic choice onto
+            # the binomial schedule with 4 snapshots
+            state = sim.adjoint_stats()["state_bytes"]
+            sim.set_memory_budget(state)
+            with pytest.raises(Exception):
+                sim.adjoint(tb, T, wr.reshape(-1), wj.reshape(-1), checkpoint_every=0)
+            sim.close()
+            sim = _gpu_sim(vel, shape, mask, B, Ef, rho0, u0, 0.8, "term", storage="f16")
+            sim.set_memory_budget(6 * state)
+        dE = torch.empty(sim.D * sim.N, dtype=torch.float64, device="cuda")
+        lam0 = torch.empty(sim.Q * sim.N, dtype=torch.float32, device="cuda")
+        res = sim.adjoint(tb, T, wr.reshape(-1), wj.reshape(-1), checkpoint_every=K, dL_dE=dE, dL_df0=lam0)
+        st = sim.adjoint_stats()
+        assert sim.info()["steps"] == T and st["reverse_steps"] == T
+        fT = sim.populations()
+        runs.append((K, res, dE.cpu().numpy(), lam0.cpu().numpy(), fT, st))
+        sim.close()
+    K0, r0, e0, l0, f0, s0 = runs[0]
+    assert s0["schedule"] == "segments" and s0["forward_steps"] == 2 * T - math.ceil(T / 5)
+    for K, res, dE, lam0, fT, st in runs[1:]:
+        assert st["schedule"] == "binomial", (K, st)
+        if K <= 0:
+            s = min(-K, T) if K < 0 else 4
+            r = 1
+            while math.comb(s + r, s) < T:
+                r += 1
+            assert st["states"] == s + 2 and st["forward_steps"] <= T * (r + 1), (K, st)
+        assert res["loss"] == r0["loss"] and res["dL_dtau"] == r0["dL_dtau"], K
+        assert np.array_equal(np.asarray(res["dL_dB"]), np.asarray(r0["dL_dB"])), K
+        assert np.array_equal(dE, e0) and np.array_equal(lam0, l0), K
+        assert np.array_equal(fT, f0), K  # the context ends at the state after T steps
 
 
 def test_adjoint_vs_gpu_finite_differences():
