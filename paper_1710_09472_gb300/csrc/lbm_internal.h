@@ -76,18 +76,20 @@ __host__ __device__ constexpr int opposite(int a) { return a == 0 ? 0 : ((a & 1)
 // otherwise): raw() decodes to FP32 without unscaling, put() rounds to
 // nearest even.
 // ---------------------------------------------------------------------------
-// put_sr() rounds stochastically with 16 random bits r: the value is rounded
-// up in magnitude with probability equal to the dropped fraction, so the
-// expected stored value is the exact FP32 value (unbiased; no stagnation of
-// increments smaller than half an ulp).  FP16: 13 mantissa bits are dropped
-// from FP32 (exact for the normal FP16 range); BF16: 16 bits.
+// sr2() rounds two values stochastically: each is rounded up in magnitude
+// with probability equal to the dropped fraction, so the expected stored
+// value is the exact FP32 value (unbiased; no stagnation of increments
+// smaller than half an ulp).  FP16 drops 13 mantissa bits of FP32, BF16 16.
 struct StoreF32 {
     using T = float;
     static constexpr int kBytes = 4;
     __device__ __forceinline__ static float raw(const T* p) { return __ldg(p); }
     __device__ __forceinline__ static float cvt(T v) { return v; }
     __device__ __forceinline__ static void put(T* p, float v) { *p = v; }
-    __device__ __forceinline__ static void put_sr(T* p, float v, uint32_t) { *p = v; }
+    __device__ __forceinline__ static void sr2(float va, float vb, uint32_t, T& ta, T& tb) {
+        ta = va;
+        tb = vb;
+    }
 };
 
 struct StoreF16 {
@@ -96,8 +98,14 @@ struct StoreF16 {
     __device__ __forceinline__ static float raw(const T* p) { return __half2float(__ldg(p)); }
     __device__ __forceinline__ static float cvt(T v) { return __half2float(v); }
     __device__ __forceinline__ static void put(T* p, float v) { *p = __float2half_rn(v); }
-    __device__ __forceinline__ static void put_sr(T* p, float v, uint32_t r) {
-        *p = __float2half_rz(__uint_as_float(__float_as_uint(v) + (r & 0x1FFFu)));
+    // stochastic rounding of two values in one conversion (cvt.rs): the low
+    // 13 bits of each 16-bit half of r are added below the kept mantissa of
+    // va (low half) and vb (high half) before truncation
+    __device__ __forceinline__ static void sr2(float va, float vb, uint32_t r, T& ta, T& tb) {
+        uint32_t d;
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(vb), "f"(va), "r"(r));
+        ta = __ushort_as_half((unsigned short)(d & 0xFFFFu));
+        tb = __ushort_as_half((unsigned short)(d >> 16));
     }
 };
 
@@ -107,8 +115,12 @@ struct StoreBF16 {
     __device__ __forceinline__ static float raw(const T* p) { return __bfloat162float(__ldg(p)); }
     __device__ __forceinline__ static float cvt(T v) { return __bfloat162float(v); }
     __device__ __forceinline__ static void put(T* p, float v) { *p = __float2bfloat16_rn(v); }
-    __device__ __forceinline__ static void put_sr(T* p, float v, uint32_t r) {
-        *p = __float2bfloat16_rz(__uint_as_float((__float_as_uint(v) + (r & 0xFFFFu)) & 0xFFFF0000u));
+    // as StoreF16::sr2, with all 16 bits of each half of r
+    __device__ __forceinline__ static void sr2(float va, float vb, uint32_t r, T& ta, T& tb) {
+        uint32_t d;
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(vb), "f"(va), "r"(r));
+        ta = __ushort_as_bfloat16((unsigned short)(d & 0xFFFFu));
+        tb = __ushort_as_bfloat16((unsigned short)(d >> 16));
     }
 };
 

@@ -228,9 +228,7 @@ __device__ __forceinline__ void collide_acc(const float* h, const float* E, cons
     out[0] = rest + rest_lo;
 }
 
-// Counter-based random bits for stochastic rounding: a hash of (step, cell,
-// direction pair) (the "lowbias32" integer hash of C. Wellons), so that a
-// replayed step reproduces its stores bit for bit.
+// The "lowbias32" integer hash of C. Wellons (seeds the rounding stream).
 __device__ __forceinline__ uint32_t hash32(uint32_t x) {
     x ^= x >> 16;
     x *= 0x7feb352dU;
@@ -240,35 +238,36 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
     return x;
 }
 
-template <class S, bool SR>
-__device__ __forceinline__ void store_val(typename S::T* ptr, float v, uint32_t rnd) {
-    if (SR)
-        S::put_sr(ptr, v, rnd);
-    else
-        S::put(ptr, v);
-}
-
 // Random stream for stochastic rounding: one hash of (cell, step) per cell,
-// then a 32-bit LCG (Numerical Recipes constants) whose upper 16 bits feed
-// each store.  A replayed step reproduces its stores bit for bit.
+// then per pair of stores one step of a 32-bit LCG (Numerical Recipes
+// constants) folded as x ^ (x >> 16), so that the low bits of each 16-bit half
+// (the bits the conversion consumes) mix in the LCG's strong high bits.  A
+// replayed step reproduces its stores bit for bit.
 struct Rng {
-    uint32_t x, cur;
-    int half;
+    uint32_t x;
     __device__ __forceinline__ Rng(uint32_t cell, const KParams& p)
-        : x(hash32(cell ^ hash32(p.step * 0x9E3779B9u + p.seed))), cur(0u), half(0) {}
-    // 16 random bits; one LCG step serves two calls (high then low half of a
-    // fresh state, whose low half is decorrelated by a multiply-xorshift)
-    __device__ __forceinline__ uint32_t next() {
-        if (half == 0) {
-            x = x * 1664525u + 1013904223u;
-            cur = x;
-            half = 1;
-            return cur >> 16;
-        }
-        half = 0;
-        return ((cur * 0x2c1b3c6du) ^ (cur >> 15)) & 0xFFFFu;
+        : x(hash32(cell ^ hash32(p.step * 0x9E3779B9u + p.seed))) {}
+    __device__ __forceinline__ uint32_t pair() {
+        x = x * 1664525u + 1013904223u;
+        return x ^ (x >> 16);
     }
 };
+
+// Rounds the Q post-collision values to storage: out[0] (converted as a pair
+// with itself), then the opposite pairs (a, a + 1), stochastically when SR.
+template <class L, class S, bool SR>
+__device__ __forceinline__ void round_all(const float* out, uint32_t cell, const KParams& p, typename S::T* t) {
+    if (SR) {
+        Rng rng(cell, p);
+        typename S::T unused;
+        S::sr2(out[0], out[0], rng.pair(), t[0], unused);
+#pragma unroll
+        for (int a = 1; a < L::Q; a += 2) S::sr2(out[a], out[a + 1], rng.pair(), t[a], t[a + 1]);
+    } else {
+#pragma unroll
+        for (int a = 0; a < L::Q; ++a) S::put(&t[a], out[a]);
+    }
+}
 
 template <class L>
 __device__ __forceinline__ void load_E(const float* __restrict__ Ef, bool ef, const KParams& p, uint32_t cell,
@@ -313,15 +312,15 @@ __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict
     load_E<L>(Ef, EF, p, c.cell, E);
     float out[L::Q];
     collide_any<L, S, FORCE>(h, E, p, out);
-    Rng rng(c.cell, p);
+    typename S::T t[L::Q];
+    round_all<L, S, SR>(out, c.cell, p, t);
     typename S::T* Gout = reinterpret_cast<typename S::T*>(reinterpret_cast<char*>(Pout) + p.gofs);
     const uint32_t o = outgoing<L::Q>(m);
     const uint32_t base = m ? __ldg(p.lbase + c.cell) : 0u;
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
-        const uint32_t rnd = SR ? rng.next() : 0u;
-        store_val<S, SR>(Pout + (int64_t)a * p.N + c.cell, out[a], rnd);
-        if (a != 0 && ((o >> a) & 1u)) store_val<S, SR>(Gout + link_slot(base, o, a), out[a], rnd);
+        Pout[(int64_t)a * p.N + c.cell] = t[a];
+        if (a != 0 && ((o >> a) & 1u)) Gout[link_slot(base, o, a)] = t[a];
     }
 }
 
@@ -504,9 +503,10 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
                 load_E<L>(Ef, EF, p, cell, E);
                 float out[L::Q];
                 collide_any<L, S, FORCE>(h, E, p, out);
-                Rng rng(cell, p);
+                typename S::T t[L::Q];
+                round_all<L, S, SR>(out, cell, p, t);
 #pragma unroll
-                for (int a = 0; a < L::Q; ++a) store_val<S, SR>(outrow + a * nx + x, out[a], SR ? rng.next() : 0u);
+                for (int a = 0; a < L::Q; ++a) outrow[a * nx + x] = t[a];
             } else {
 #pragma unroll
                 for (int a = 0; a < L::Q; ++a) S::put(outrow + a * nx + x, 0.f);
