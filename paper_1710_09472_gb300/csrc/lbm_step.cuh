@@ -30,8 +30,27 @@ using dev::kBlock;
 // work is done once per pair; the rest population closes the mass balance
 // exactly: h~*_0 = sum_a h~_a - sum_{a>0} h~*_a.
 // ---------------------------------------------------------------------------
+// The weights w_a, k2_a and W1_a depend on the shell |e_a|^2 only (axis 1,
+// diagonal 2), so the per-cell factors are folded per shell first:
+//   even_a = w_s (c0 + k2_s Ku) + w_s Cp s rho (e.u*) (w (e.u*) + 2 (e.E)),
+//            c0 = w A drho~, Ku = s rho (w u*^2 + 2 u.E)        (the E terms: FORCE 1)
+//   odd_a  = e_a . V_s,  V_s = W1_s v + 2 s rho w_s k2_s (B x u) / c_s  (B term: FORCE 1),
+// with v = w j~ + s c_s rho E (FORCE 1) or w j~ + s c_s rho a (FORCE 0), and
+// W1_s applied as its double-float pair once per cell.
+template <class L>
+struct Shells {
+    static constexpr int kAx = 1;  // first axis direction
+    __host__ __device__ static constexpr int diag() {
+        int r = 0;
+        for (int a = L::Q - 1; a > 0; --a)
+            if (L::c(a, 0) * L::c(a, 0) + L::c(a, 1) * L::c(a, 1) + L::c(a, 2) * L::c(a, 2) == 2) r = a;
+        return r;
+    }
+};
+
 template <class L, int FORCE>
 __device__ __forceinline__ void collide(const float* h, const float* E, const KParams& p, float* out) {
+    constexpr int kAx = Shells<L>::kAx, kDg = Shells<L>::diag();
     float drho = h[0], j[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int a = 1; a < L::Q; a += 2) {
@@ -48,9 +67,8 @@ __device__ __forceinline__ void collide(const float* h, const float* E, const KP
     const float u[3] = {j[0] * q, j[1] * q, j[2] * q};
     const float srho = p.scale * rho;
     const float om = p.omega, omm = 1.0f - p.omega;
-    float ue[3], v[3];
-    float uE = 0.f, bu[3] = {0.f, 0.f, 0.f};
     const float scr = srho * p.cs;  // s c_s rho
+    float ue[3], v[3], bu[3] = {0.f, 0.f, 0.f}, Ku, cq;
     if (FORCE == 0) {
         const float a0 = E[0] + (u[1] * p.B[2] - u[2] * p.B[1]);
         const float a1 = E[1] + (u[2] * p.B[0] - u[0] * p.B[2]);
@@ -58,10 +76,12 @@ __device__ __forceinline__ void collide(const float* h, const float* E, const KP
         ue[0] = u[0] + p.tau * a0;
         ue[1] = u[1] + p.tau * a1;
         ue[2] = u[2] + p.tau * a2;
-        // odd part of w heq~ at u*: W1 (e . w (j~ + s c_s rho tau a)) = W1 (e . (w j~ + s c_s rho a))
+        // odd part of w heq~ at u*: W1 (e . (w j~ + s c_s rho a))
         v[0] = om * j[0] + scr * a0;
         v[1] = om * j[1] + scr * a1;
         v[2] = om * j[2] + scr * a2;
+        Ku = om * srho * (ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2]);
+        cq = om * srho * p.Cp;
     } else {
         ue[0] = u[0];
         ue[1] = u[1];
@@ -69,28 +89,38 @@ __device__ __forceinline__ void collide(const float* h, const float* E, const KP
         v[0] = om * j[0] + scr * E[0];
         v[1] = om * j[1] + scr * E[1];
         v[2] = om * j[2] + scr * E[2];
-        uE = u[0] * E[0] + u[1] * E[1] + u[2] * E[2];
+        const float uE = u[0] * E[0] + u[1] * E[1] + u[2] * E[2];
         const float tb = 2.f * srho * p.cs_inv;  // 2 s rho / c_s times (B x u)
         bu[0] = tb * (p.B[1] * u[2] - p.B[2] * u[1]);
         bu[1] = tb * (p.B[2] * u[0] - p.B[0] * u[2]);
         bu[2] = tb * (p.B[0] * u[1] - p.B[1] * u[0]);
+        Ku = srho * (om * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) + 2.f * uE);
+        cq = srho * p.Cp;
     }
-    const float u2 = ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2];
-    const float omAdr = om * p.A * drho;
+    const float c0 = om * p.A * drho;
+    // per shell: the even constant, the (e.u) coefficient and the odd vector
+    const float e0a = p.w[kAx] * (c0 + p.k2[kAx] * Ku), e0d = p.w[kDg] * (c0 + p.k2[kDg] * Ku);
+    const float cqa = p.w[kAx] * cq, cqd = p.w[kDg] * cq;
+    float Va[3], Vd[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        Va[d] = fmaf(p.W1lo[kAx], v[d], p.W1hi[kAx] * v[d]);
+        Vd[d] = fmaf(p.W1lo[kDg], v[d], p.W1hi[kDg] * v[d]);
+        if (FORCE == 1) {
+            Va[d] = fmaf(p.w[kAx] * p.k2[kAx], bu[d], Va[d]);
+            Vd[d] = fmaf(p.w[kDg] * p.k2[kDg], bu[d], Vd[d]);
+        }
+    }
     float rest = drho;
 #pragma unroll
     for (int a = 1; a < L::Q; a += 2) {
+        const bool ax = dev::esq<L>(a) == 1;
         const float eu = dev::edot<L>(a, ue);
-        const float ev_ = dev::edot<L>(a, v);
-        float even = p.w[a] * (omAdr + om * srho * (p.Cp * eu * eu + p.k2[a] * u2));
-        float odd = p.W1hi[a] * ev_ + p.W1lo[a] * ev_;
-        if (FORCE == 1) {
-            const float eE = dev::edot<L>(a, E);
-            even += 2.f * srho * p.w[a] * (p.Cp * eu * eE + p.k2[a] * uE);
-            odd += p.w[a] * p.k2[a] * dev::edot<L>(a, bu);
-        }
-        const float ha = omm * h[a] + even + odd;
-        const float hb = omm * h[a + 1] + even - odd;
+        const float g = (FORCE == 1) ? fmaf(om, eu, 2.f * dev::edot<L>(a, E)) : eu;
+        const float even = fmaf(ax ? cqa : cqd, eu * g, ax ? e0a : e0d);
+        const float odd = dev::edot<L>(a, ax ? Va : Vd);
+        const float ha = fmaf(omm, h[a], even) + odd;
+        const float hb = fmaf(omm, h[a + 1], even) - odd;
         out[a] = ha;
         out[a + 1] = hb;
         rest -= ha + hb;
