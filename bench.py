@@ -111,6 +111,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.samples)}
 
 
+def max_over_ranks(times, world: int, device):
+    """Each rank's timings -> the element-wise maximum over the ranks of the
+    initialised process group (the slowest replica sets the job time)."""
+    if world <= 1:
+        return list(times)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor(list(times), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 def make_geometry():
     from paper_1710_09472_gb300 import workloads as wl
 
@@ -196,6 +209,7 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     ms_adj = a0.elapsed_time(a1)
     adj_launches = sim.launch_count() - l0
+    adj_stats = sim.adjoint_stats()
     sim.close()
 
     # whole-job through the public API with pinned host buffers
@@ -227,14 +241,7 @@ def run_gpu(args, rank, world):
     err_j = rel(m16[1], m32[1])
 
     # max over ranks
-    times = [ms16, ms32, e2e_s, ms_adj]
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor(times, dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        times = t.tolist()
-    ms16, ms32, e2e_s, ms_adj = times
+    ms16, ms32, e2e_s, ms_adj = max_over_ranks([ms16, ms32, e2e_s, ms_adj], world, dev)
     n_fluid = info["n_fluid"]
     Q = 19
     peak, peak_kind = hbm_peak()
@@ -280,9 +287,11 @@ def run_gpu(args, rank, world):
             "value": round(world * N * T_adj / (ms_adj * 1e-3) / 1e6, 1), "unit": "MLUPS",
             "steps": T_adj, "checkpoint_every": K_adj, "ms_per_step": round(ms_adj / T_adj, 5),
             "cost_vs_forward_step": round((ms_adj / T_adj) / (ms16 / args.steps), 3),
-            "what": ("one lbm_adjoint call: T forward steps with checkpoints, segment replay storing every "
-                     "state, T reverse steps (FP64 per-cell dL/dE, dL/dB, dL/dtau); loss = mean x-current "
-                     "after the last step; storage f16-deviation"),
+            "schedule": adj_stats["schedule"], "states_kept": adj_stats["states"],
+            "forward_steps": adj_stats["forward_steps"],
+            "what": ("one lbm_adjoint call: the forward steps of its checkpoint schedule and T reverse steps "
+                     "(FP64 per-cell dL/dE, dL/dB, dL/dtau); loss = mean x-current after the last step; "
+                     "storage f16-deviation"),
             "launches": int(adj_launches), "dL_dtau": adj["dL_dtau"], "dL_dBz": float(adj["dL_dB"][2])},
         "fp16_vs_fp32": {"rho_rel_linf": err_rho, "j_rel_linf": err_j, "after_steps": args.warmup + args.steps},
         "e2e": {"value": round(world * N * args.steps / e2e_s / 1e6, 1), "unit": "MLUPS",
@@ -404,7 +413,7 @@ def run_reference(args, rank, world):
     return {"metric": "MLUPS", "value": v, "unit": "MLUPS", "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(n), "sample": sample},
+            "config": {"workload": workload_name(WORKLOAD["n"]), "sample": sample},
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -418,7 +427,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=200)
-    ap.add_argument("--adjoint-checkpoint", type=int, default=14)
+    ap.add_argument("--adjoint-checkpoint", type=int, default=0,
+                    help="checkpoint_every of lbm_adjoint (0: schedule sized to the free memory)")
     ap.add_argument("--n", type=int, default=256, help="box edge (256 is the benchmark; smaller for profiling)")
     ap.add_argument("--adjoint-512", type=int, default=0,
                     help="also run the 512^3 forward + full adjoint over this many steps within 180 GB (0 = off)")
