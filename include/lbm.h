@@ -192,7 +192,7 @@ lbm_status lbm_window_totals(lbm_ctx* ctx, int64_t t_begin, int64_t t_end, doubl
 lbm_status lbm_set_memory_budget(lbm_ctx* ctx, uint64_t bytes);
 
 /* Schedule of the last lbm_adjoint call and the size of one kept state:
- * out = {0 segment / 1 binomial, state buffers held, forward steps run,
+ * out = {0 segment / 1 binomial / 2 every state kept, state buffers held, forward steps run,
  * reverse steps run, bytes per state buffer}.  Errors: INVALID_ARG. */
 lbm_status lbm_adjoint_stats(const lbm_ctx* ctx, int64_t out[5]);
 
@@ -217,8 +217,10 @@ lbm_status lbm_selftest_wait_timeout(lbm_ctx* ctx, int64_t clocks);
  *   K > 0 : segment schedule: t_end forward steps keeping a copy every K
  *           steps, then each segment is replayed from its copy storing every
  *           state (ceil(t_end / K) + K - 1 states; 2 t_end forward steps);
- *   K = 0 : the segment schedule with K = ceil(sqrt(t_end)) when it fits the
- *           memory budget (lbm_set_memory_budget), else the binomial schedule
+ *   K = 0 : every state kept during the one forward sweep (t_end - 1 extra
+ *           states, no replay) when they fit the memory budget
+ *           (lbm_set_memory_budget); else the segment schedule with
+ *           K = ceil(sqrt(t_end)) when it fits; else the binomial schedule
  *           with as many snapshots as fit;
  *   K < 0 : binomial schedule with -K snapshots: the recursion of Griewank's
  *           revolve (snapshots placed so that s snapshots and r sweeps cover

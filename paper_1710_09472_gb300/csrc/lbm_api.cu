@@ -808,6 +808,13 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
     const size_t budget = c->mem_budget ? std::min(c->mem_budget, avail) : avail - avail / 20;
     const int64_t states_fit = (int64_t)(budget / pop_bytes);
     bool binomial = checkpoint_every < 0 || (checkpoint_every == 0 && nseg + K - 1 > states_fit);
+    // K = 0 and room for every state: keep them all during the one forward
+    // sweep (no replay); the state at t = 0 is the context's current buffer
+    const bool store_all = checkpoint_every == 0 && T - 1 <= states_fit;
+    if (store_all) {
+        binomial = false;
+        K = T;
+    }
     int64_t nsnap = 0;  // binomial: snapshots besides the initial state and the work buffer
     if (checkpoint_every < 0) {
         nsnap = std::min<int64_t>(-checkpoint_every, T);
@@ -824,7 +831,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
                     "checkpoint_every near sqrt(t_end), or 0 for a schedule sized to the memory budget",
                     ((size_t)(nseg + K - 1) * pop_bytes + fixed) / 1e9, free_b / 1e9);
     }
-    std::vector<void*> ckpt(binomial ? 0 : nseg, nullptr), seg(binomial ? 0 : K, nullptr), snaps;
+    std::vector<void*> ckpt(binomial || store_all ? 0 : nseg, nullptr), seg(binomial ? 0 : K, nullptr), snaps;
     void* base = nullptr;   // binomial: the state at t = 0
     void* work1 = nullptr;  // binomial: second work buffer
     float* lam[2] = {nullptr, nullptr};
@@ -859,7 +866,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
         snaps.assign((size_t)nsnap, nullptr);
         for (auto& q : snaps) ADJ_CHECK(cudaMalloc(&q, pop_bytes));
     } else {
-        for (int64_t s = 0; s < nseg; ++s) ADJ_CHECK(cudaMalloc(&ckpt[s], pop_bytes));
+        for (size_t s = 0; s < ckpt.size(); ++s) ADJ_CHECK(cudaMalloc(&ckpt[s], pop_bytes));
         for (int64_t k = 1; k < K; ++k) ADJ_CHECK(cudaMalloc(&seg[k], pop_bytes));
     }
     ADJ_CHECK(cudaMalloc((void**)&lam[0], lam_alloc));
@@ -906,7 +913,17 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
         c->launches += lbm::launch_adjoint_seed(vel, sto, state_T, c->nbr, wr_d, wj_d, lam[li], slots,
                                                 T > t_begin && T <= t_end, p, c->stream);
     };
-    if (!binomial) {
+    if (store_all) {
+        // --- one forward sweep keeping every state, then the reverse sweep ---
+        seg[0] = c->pop[c->cur];
+        for (int64_t t = 0; t < T; ++t) fstep(t, seg[t], t + 1 < T ? seg[t + 1] : c->pop[c->cur ^ 1]);
+        ADJ_CHECK(cudaGetLastError());
+        seed(c->pop[c->cur ^ 1]);
+        for (int64_t t = T - 1; t >= 0; --t) rstep(t, seg[t]);
+        ADJ_CHECK(cudaGetLastError());
+        seg[0] = nullptr;
+        c->cur ^= 1;  // the context's current state is the state at T
+    } else if (!binomial) {
         // --- forward with checkpoints every K steps ---
         for (int64_t t = 0; t < T; ++t) {
             if (t % K == 0)
@@ -1001,8 +1018,8 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
         ADJ_CHECK(cudaGetLastError());
         c->cur ^= 1;  // the context's current state is the state at T
     }
-    c->adj_stats[0] = binomial ? 1 : 0;
-    c->adj_stats[1] = binomial ? 2 + nsnap : nseg + K - 1;
+    c->adj_stats[0] = store_all ? 2 : (binomial ? 1 : 0);
+    c->adj_stats[1] = store_all ? T + 1 : (binomial ? 2 + nsnap : nseg + K - 1);
     c->adj_stats[2] = fwd_steps;
     c->adj_stats[3] = T;
     if (dL_df0) ADJ_CHECK(cudaMemcpyAsync(dL_df0, lam[li], lam_bytes, cudaMemcpyDeviceToDevice, c->stream));

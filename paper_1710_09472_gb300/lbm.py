@@ -173,7 +173,7 @@ class LBM:
     def adjoint_stats(self) -> dict:
         out = (ctypes.c_int64 * 5)()
         _lib.check(_lib.load().lbm_adjoint_stats(self._h, out), self._h, "lbm_adjoint_stats")
-        return {"schedule": "binomial" if out[0] else "segments", "states": int(out[1]),
+        return {"schedule": ["segments", "binomial", "store_all"][int(out[0])], "states": int(out[1]),
                 "forward_steps": int(out[2]), "reverse_steps": int(out[3]), "state_bytes": int(out[4])}
 
     def selftest_wait_timeout(self, clocks: int = 1 << 20) -> int:

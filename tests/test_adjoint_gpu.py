@@ -149,7 +149,7 @@ def test_binomial_schedule_matches_segments(vel):
     shape, mask, B, Ef, rho0, u0, wr, wj = _case(vel)
     T, tb = 23, 9
     runs = []
-    for K in (5, -1, -3, -7, -40, 0):
+    for K in (5, -1, -3, -7, -40, 0, "all"):
         sim = _gpu_sim(vel, shape, mask, B, Ef, rho0, u0, 0.8, "term", storage="f16")
         if K == 0:
             # a budget below two states is refused; one of six states (the
@@ -162,6 +162,8 @@ def test_binomial_schedule_matches_segments(vel):
             sim.close()
             sim = _gpu_sim(vel, shape, mask, B, Ef, rho0, u0, 0.8, "term", storage="f16")
             sim.set_memory_budget(6 * state)
+        if K == "all":
+            K = 0  # default budget: every state fits, so nothing is replayed
         dE = torch.empty(sim.D * sim.N, dtype=torch.float64, device="cuda")
         lam0 = torch.empty(sim.Q * sim.N, dtype=torch.float32, device="cuda")
         res = sim.adjoint(tb, T, wr.reshape(-1), wj.reshape(-1), checkpoint_every=K, dL_dE=dE, dL_df0=lam0)
@@ -172,9 +174,10 @@ def test_binomial_schedule_matches_segments(vel):
         sim.close()
     K0, r0, e0, l0, f0, s0 = runs[0]
     assert s0["schedule"] == "segments" and s0["forward_steps"] == 2 * T - math.ceil(T / 5)
+    assert runs[-1][5]["schedule"] == "store_all" and runs[-1][5]["forward_steps"] == T
     for K, res, dE, lam0, fT, st in runs[1:]:
-        assert st["schedule"] == "binomial", (K, st)
-        if K <= 0:
+        assert st["schedule"] in ("binomial", "store_all"), (K, st)
+        if st["schedule"] == "binomial":
             s = min(-K, T) if K < 0 else 4
             r = 1
             while math.comb(s + r, s) < T:
