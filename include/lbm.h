@@ -184,6 +184,12 @@ lbm_status lbm_get_populations(lbm_ctx* ctx, float* f, int deviation);
  * Synchronises.  Errors: INVALID_ARG, STATE, CUDA, NONFINITE. */
 lbm_status lbm_window_totals(lbm_ctx* ctx, int64_t t_begin, int64_t t_end, double out[4]);
 
+/* Frees the device buffers that lbm_adjoint keeps in the context between
+ * calls (forward states, adjoint fields, gradient scratch).  Synchronises the
+ * context's stream.  Infrastructure; the paper has no counterpart.  Errors:
+ * INVALID_ARG. */
+lbm_status lbm_release_workspace(lbm_ctx* ctx);
+
 /* Device bytes that an lbm_adjoint call with checkpoint_every = 0 may spend
  * on kept forward states (0, the default: 95% of the free device memory left
  * after the adjoint fields).  The adjoint fields and gradient scratch come on
@@ -238,7 +244,10 @@ lbm_status lbm_selftest_wait_timeout(lbm_ctx* ctx, int64_t clocks);
  *   dL_df0  : [Q * N] FP32 device, dL/df_0 (population layout), or NULL.
  * Device memory: the schedule's states (populations + bounce-back link
  * buffer each) plus two FP32 adjoint fields (Q N values + one per bounce-back
- * link each), allocated for the call and released before it returns.
+ * link each).  The context keeps these buffers after the call and reuses
+ * them in the next one (buffers it already holds count as free memory when
+ * the schedule is chosen); lbm_release_workspace, lbm_set_geometry and
+ * lbm_destroy free them.
  * Gradients accumulate in FP64; the sweep is deterministic.
  * Synchronises.  Errors: INVALID_ARG, STATE, OOM (with the size needed), CUDA,
  * NONFINITE. */

@@ -50,6 +50,7 @@ SIGNATURES = {
     "lbm_selftest_wait_timeout": (_i, [_vp, _i64]),
     "lbm_set_memory_budget": (_i, [_vp, ctypes.c_uint64]),
     "lbm_adjoint_stats": (_i, [_vp, _vp]),
+    "lbm_release_workspace": (_i, [_vp]),
 }
 
 

@@ -534,9 +534,10 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
         // ascending-x compaction: each thread's FP64 sums then see the same
         // cells in the same order on every run
         dev::compact_fluid_ordered(reinterpret_cast<const uint32_t*>(lay.masks(st)), nx, flist, wcnt, &nfluid);
-        dev::patch_links<L, true>(prow, nx, reinterpret_cast<const T*>(lay.plinks(st)), wstart[cs][0], g0, g1, desc,
-                                  d0);
-        dev::patch_links<L, false>(lrow, nx, reinterpret_cast<const float*>(lay.llinks(st)), d0, g0, g1, desc, d0);
+        dev::patch_links<L, true>(prow, nx, nx, reinterpret_cast<const T*>(lay.plinks(st)), wstart[cs][0], g0, g1,
+                                  desc, d0);
+        dev::patch_links<L, false>(lrow, nx, nx, reinterpret_cast<const float*>(lay.llinks(st)), d0, g0, g1, desc,
+                                   d0);
         if (warp0) dev::bulk_wait_read();  // the previous row's bulk stores have read the output rows
         __syncthreads();  // list complete, bounced values in place, output rows free
         if (warp0) {

@@ -239,6 +239,21 @@ struct StateHeader {
     uint32_t pad;
 };
 
+// Frees the adjoint workspace (after the stream has drained).
+void ws_release(lbm_ctx* c) {
+    AdjWorkspace& w = c->ws;
+    if (w.states.empty() && !w.lam[0] && !w.lam[1] && !w.slots && !w.red && !w.wstage) return;
+    cudaStreamSynchronize(c->stream);
+    for (void* q : w.states) cudaFree(q);
+    w.states.clear();
+    cudaFree(w.lam[0]);
+    cudaFree(w.lam[1]);
+    cudaFree(w.slots);
+    cudaFree(w.red);
+    cudaFree(w.wstage);
+    w = AdjWorkspace();
+}
+
 // Link-buffer layout for the current link masks, then state buffers sized
 // for populations + links (contents undefined until lbm_init_equilibrium).
 lbm_status build_links_and_state(lbm_ctx* c) {
@@ -273,6 +288,7 @@ lbm_status build_links_and_state(lbm_ctx* c) {
     const size_t pbytes = (size_t)c->Q * (size_t)c->N * eb;
     c->gofs = (pbytes + 255) & ~(size_t)255;
     const size_t need = c->gofs + ((((size_t)c->n_links * eb) + 16 + 255) & ~(size_t)255);
+    if (need != c->state_bytes || c->ws.lam_bytes) ws_release(c);  // sizes follow the links
     if (need != c->state_bytes) {
         cudaFree(c->pop[0]);
         cudaFree(c->pop[1]);
@@ -443,6 +459,7 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_lattice* lat, const int64_t dims[
 void lbm_destroy(lbm_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    ws_release(c);
     cudaFree(c->pop[0]);
     cudaFree(c->pop[1]);
     cudaFree(c->nbr);
@@ -745,6 +762,12 @@ lbm_status lbm_set_memory_budget(lbm_ctx* c, uint64_t bytes) {
     return LBM_OK;
 }
 
+lbm_status lbm_release_workspace(lbm_ctx* c) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    ws_release(c);
+    return LBM_OK;
+}
+
 lbm_status lbm_adjoint_stats(const lbm_ctx* c, int64_t out[5]) {
     if (!c || !out) return LBM_ERR_INVALID_ARG;
     for (int k = 0; k < 4; ++k) out[k] = c->adj_stats[k];
@@ -799,9 +822,15 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
     // Fixed: two adjoint fields, the gradient slots, staged loss weights.
     // States: the segment schedule (K > 0, or K = 0 when it fits) keeps
     // ceil(T/K) checkpoints and K - 1 replay states; the binomial schedule
-    // keeps the initial state, one work buffer and s snapshots.
+    // keeps the initial state, one work buffer and s snapshots.  Buffers held
+    // in the context's workspace from earlier calls count as free.
+    AdjWorkspace& ws = c->ws;
+    if ((ws.state_bytes && ws.state_bytes != pop_bytes) || (ws.lam_bytes && ws.lam_bytes != lam_alloc) ||
+        (ws.nslot && ws.nslot != nslot))
+        ws_release(c);
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
+    free_b += ws.held();
     const size_t fixed = 2 * lam_alloc + sizeof(double) * (nslot + 8) + sizeof(float) * (size_t)c->N * (1 + c->D);
     // bytes for the kept forward states: the budget, or 95% of what the fixed part leaves free
     const size_t avail = free_b > fixed ? free_b - fixed : 0;
@@ -831,54 +860,63 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
                     "checkpoint_every near sqrt(t_end), or 0 for a schedule sized to the memory budget",
                     ((size_t)(nseg + K - 1) * pop_bytes + fixed) / 1e9, free_b / 1e9);
     }
-    std::vector<void*> ckpt(binomial || store_all ? 0 : nseg, nullptr), seg(binomial ? 0 : K, nullptr), snaps;
-    void* base = nullptr;   // binomial: the state at t = 0
-    void* work1 = nullptr;  // binomial: second work buffer
-    float* lam[2] = {nullptr, nullptr};
-    double* slots = nullptr;
-    double* red = nullptr;
-    float* wstage = nullptr;
+    const int64_t nstates = binomial ? nsnap + 2 : (store_all ? T - 1 : nseg + K - 1);
     lbm_status st = LBM_OK;
-    auto release = [&]() {
-        cudaStreamSynchronize(c->stream);
-        for (void* q : ckpt) cudaFree(q);
-        for (size_t k = 1; k < seg.size(); ++k) cudaFree(seg[k]);
-        for (void* q : snaps) cudaFree(q);
-        cudaFree(base);
-        cudaFree(work1);
-        cudaFree(lam[0]);
-        cudaFree(lam[1]);
-        cudaFree(slots);
-        cudaFree(red);
-        cudaFree(wstage);
-    };
 #define ADJ_CHECK(call)                                        \
     do {                                                       \
         st = cuda_check(c, (call), #call);                     \
         if (st != LBM_OK) {                                    \
-            release();                                         \
+            cudaStreamSynchronize(c->stream);                  \
             return st;                                         \
         }                                                      \
     } while (0)
-    if (binomial) {
-        ADJ_CHECK(cudaMalloc(&base, pop_bytes));
-        ADJ_CHECK(cudaMalloc(&work1, pop_bytes));
-        snaps.assign((size_t)nsnap, nullptr);
-        for (auto& q : snaps) ADJ_CHECK(cudaMalloc(&q, pop_bytes));
-    } else {
-        for (size_t s = 0; s < ckpt.size(); ++s) ADJ_CHECK(cudaMalloc(&ckpt[s], pop_bytes));
-        for (int64_t k = 1; k < K; ++k) ADJ_CHECK(cudaMalloc(&seg[k], pop_bytes));
+    // grow the workspace to this call's needs (buffers are reused as they are)
+    ws.state_bytes = pop_bytes;
+    while ((int64_t)ws.states.size() < nstates) {
+        void* q = nullptr;
+        ADJ_CHECK(cudaMalloc(&q, pop_bytes));
+        ws.states.push_back(q);
     }
-    ADJ_CHECK(cudaMalloc((void**)&lam[0], lam_alloc));
-    ADJ_CHECK(cudaMalloc((void**)&lam[1], lam_alloc));
-    ADJ_CHECK(cudaMalloc((void**)&slots, sizeof(double) * nslot));
-    ADJ_CHECK(cudaMalloc((void**)&red, sizeof(double) * 8));
+    if (!ws.lam[0]) {
+        ADJ_CHECK(cudaMalloc(&ws.lam[0], lam_alloc));
+        ADJ_CHECK(cudaMalloc(&ws.lam[1], lam_alloc));
+        ws.lam_bytes = lam_alloc;
+    }
+    if (!ws.slots) {
+        ADJ_CHECK(cudaMalloc((void**)&ws.slots, sizeof(double) * nslot));
+        ws.nslot = nslot;
+    }
+    if (!ws.red) ADJ_CHECK(cudaMalloc((void**)&ws.red, sizeof(double) * 8));
+    // the schedule's views of the state buffers
+    std::vector<void*> ckpt, seg, snaps;
+    void* base = nullptr;   // binomial: the state at t = 0
+    void* work1 = nullptr;  // binomial: second work buffer
+    {
+        size_t k = 0;
+        if (binomial) {
+            base = ws.states[k++];
+            work1 = ws.states[k++];
+            for (int64_t i = 0; i < nsnap; ++i) snaps.push_back(ws.states[k++]);
+        } else {
+            if (!store_all)
+                for (int64_t i = 0; i < nseg; ++i) ckpt.push_back(ws.states[k++]);
+            seg.assign((size_t)K, nullptr);
+            for (int64_t i = 1; i < K; ++i) seg[i] = ws.states[k++];
+        }
+    }
+    float* lam[2] = {(float*)ws.lam[0], (float*)ws.lam[1]};
+    double* slots = ws.slots;
+    double* red = ws.red;
     ADJ_CHECK(cudaMemsetAsync(slots, 0, sizeof(double) * nslot, c->stream));
     // loss weights: device, or staged from the host
     const float* wr_d = w_rho;
     const float* wj_d = w_j;
     if ((w_rho && !is_device_ptr(w_rho)) || (w_j && !is_device_ptr(w_j))) {
-        ADJ_CHECK(cudaMalloc((void**)&wstage, sizeof(float) * (size_t)c->N * (1 + c->D)));
+        if (!ws.wstage) {
+            ADJ_CHECK(cudaMalloc((void**)&ws.wstage, sizeof(float) * (size_t)c->N * (1 + c->D)));
+            ws.wstage_bytes = sizeof(float) * (size_t)c->N * (1 + c->D);
+        }
+        float* wstage = ws.wstage;
         if (w_rho && !is_device_ptr(w_rho)) {
             ADJ_CHECK(cudaMemcpyAsync(wstage, w_rho, sizeof(float) * c->N, cudaMemcpyHostToDevice, c->stream));
             wr_d = wstage;
@@ -1027,7 +1065,6 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
     double host[5];
     ADJ_CHECK(cudaMemcpyAsync(host, red, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->stream));
     ADJ_CHECK(cudaStreamSynchronize(c->stream));
-    release();
 #undef ADJ_CHECK
     {
         lbm_status _ds = device_status(c);

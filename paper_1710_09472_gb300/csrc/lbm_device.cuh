@@ -191,19 +191,19 @@ __device__ __forceinline__ void compact_fluid_ordered(const uint32_t* mrow, int 
 // direction: by x itself, in the pull of direction bbar (which reads
 // x - e_bbar = x + e_b) and in the adjoint gather of direction b (which reads
 // x + e_b).  So the halfway bounce-back value win[k - w0] is written into that
-// staged slot, rows[d * nx + (x + e_bx mod nx)] with d = bbar (PULL) or b
+// staged slot, rows[d * rs + (x + e_bx mod nx)] (rs the row stride) with d = bbar (PULL) or b
 // (gather), and the cells then read their rows without any link logic.
 // The descriptors come from the staged window desc (first element d0).
 template <class L, bool PULL, class T>
-__device__ __forceinline__ void patch_links(T* rows, int nx, const T* win, uint32_t w0, uint32_t g0, uint32_t g1,
-                                            const uint32_t* desc, uint32_t d0) {
+__device__ __forceinline__ void patch_links(T* rows, int nx, int rs, const T* win, uint32_t w0, uint32_t g0,
+                                            uint32_t g1, const uint32_t* desc, uint32_t d0) {
     const unsigned long long kPx = packed_x<L>();
     for (uint32_t k = g0 + threadIdx.x; k < g1; k += blockDim.x) {
         const uint32_t d = desc[k - d0];
         const int x = (int)(d & 0xFFFFFFu), b = (int)(d >> 24);
         int xs = x + (int)((kPx >> (2 * b)) & 3ull) - 1;
         xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
-        rows[(PULL ? opposite(b) : b) * nx + xs] = win[k - w0];
+        rows[(PULL ? opposite(b) : b) * rs + xs] = win[k - w0];
     }
 }
 

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "lbm.h"
 
@@ -222,6 +223,24 @@ KParams make_params(const lbm_ctx* c);
 }  // namespace lbm
 
 // The context (opaque to C callers).
+// Device buffers of lbm_adjoint, kept by the context between calls so that
+// repeated calls allocate once (released by lbm_release_workspace,
+// lbm_set_geometry and lbm_destroy).
+struct AdjWorkspace {
+    std::vector<void*> states;  // forward-state buffers of state_bytes each
+    size_t state_bytes = 0;
+    void* lam[2] = {nullptr, nullptr};
+    size_t lam_bytes = 0;
+    double* slots = nullptr;
+    int64_t nslot = 0;
+    double* red = nullptr;
+    float* wstage = nullptr;  // loss weights staged from the host
+    size_t wstage_bytes = 0;
+    size_t held() const {
+        return states.size() * state_bytes + 2 * lam_bytes + sizeof(double) * (size_t)nslot + wstage_bytes;
+    }
+};
+
 struct lbm_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -258,6 +277,7 @@ struct lbm_ctx {
     double* totals_dev = nullptr;
     double* totals_host = nullptr;  // pinned, 4 doubles
     unsigned long long* count_dev = nullptr;
+    AdjWorkspace ws;               // lbm_adjoint buffers kept between calls
     size_t mem_budget = 0;         // device bytes an lbm_adjoint call may allocate (0: free memory)
     int64_t adj_stats[4] = {0, 0, 0, 0};  // last lbm_adjoint: schedule, state buffers, forward steps, reverse steps
     int* status_host = nullptr;    // mapped pinned word written by kernels on a wait timeout

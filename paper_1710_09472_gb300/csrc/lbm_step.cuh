@@ -384,19 +384,19 @@ __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict
 // the link descriptors (dcap bytes), both as 16-byte aligned windows.
 template <class L, class S>
 struct StageLayout {
-    int nx, gcap, dcap;
-    __device__ __forceinline__ int bytes() const { return L::Q * nx * S::kBytes + 4 * nx + gcap + dcap; }
+    int nx, rs, gcap, dcap;  // row length, shared-memory row stride (elements)
+    __device__ __forceinline__ int bytes() const { return L::Q * rs * S::kBytes + 4 * nx + gcap + dcap; }
     __device__ __forceinline__ typename S::T* rows(unsigned char* st) const {
         return reinterpret_cast<typename S::T*>(st);
     }
     __device__ __forceinline__ uint32_t* masks(unsigned char* st) const {
-        return reinterpret_cast<uint32_t*>(st + L::Q * nx * S::kBytes);
+        return reinterpret_cast<uint32_t*>(st + L::Q * rs * S::kBytes);
     }
     __device__ __forceinline__ typename S::T* links(unsigned char* st) const {
-        return reinterpret_cast<typename S::T*>(st + L::Q * nx * S::kBytes + 4 * nx);
+        return reinterpret_cast<typename S::T*>(st + L::Q * rs * S::kBytes + 4 * nx);
     }
     __device__ __forceinline__ uint32_t* descs(unsigned char* st) const {
-        return reinterpret_cast<uint32_t*>(st + L::Q * nx * S::kBytes + 4 * nx + gcap);
+        return reinterpret_cast<uint32_t*>(st + L::Q * rs * S::kBytes + 4 * nx + gcap);
     }
 };
 
@@ -426,7 +426,7 @@ __device__ __forceinline__ void stage_row(unsigned char* st, const StageLayout<L
         // source row of direction a: (y - e_ay, z - e_az), periodic
         const int ys = L::c(a, 1) > 0 ? ym : (L::c(a, 1) < 0 ? yp : y);
         const int zs = L::c(a, 2) > 0 ? zm : (L::c(a, 2) < 0 ? zp : z);
-        dev::bulk_load(lay.rows(st) + a * p.nx, Pin + (int64_t)a * p.N + ((int64_t)zs * p.ny + ys) * p.nx, row_bytes,
+        dev::bulk_load(lay.rows(st) + a * lay.rs, Pin + (int64_t)a * p.N + ((int64_t)zs * p.ny + ys) * p.nx, row_bytes,
                        bar);
     }
     dev::bulk_load(lay.masks(st), nbr + (int64_t)row * p.nx, 4u * (uint32_t)p.nx, bar);
@@ -438,17 +438,18 @@ __device__ __forceinline__ void stage_row(unsigned char* st, const StageLayout<L
                        bar);
 }
 
-template <class L, class S, int FORCE, bool EF, bool SR, int STAGES>
+template <class L, class S, int FORCE, bool EF, bool SR, int STAGES, int RS>
 __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restrict__ Pin,
                                                    typename S::T* __restrict__ Pout, const uint32_t* __restrict__ nbr,
                                                    const float* __restrict__ Ef, int gcap, int dcap, KParams p) {
     using T = typename S::T;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int nx = p.nx;
-    const StageLayout<L, S> lay{nx, gcap, dcap};
+    const int rs = RS ? RS : nx;  // shared-memory row stride: a constant for the common row lengths
+    const StageLayout<L, S> lay{nx, rs, gcap, dcap};
     const int sbytes = lay.bytes();
     T* outrow = reinterpret_cast<T*>(smem_raw + STAGES * sbytes);
-    uint32_t* flist = reinterpret_cast<uint32_t*>(outrow + L::Q * nx);  // fluid x from the front, solid from the back
+    uint32_t* flist = reinterpret_cast<uint32_t*>(outrow + L::Q * rs);  // fluid x from the front, solid from the back
     __shared__ __align__(8) uint64_t bar[STAGES];
     __shared__ int counts[2][2];  // [row parity][fluid, solid]
     __shared__ uint32_t gstart[STAGES], dstart[STAGES];
@@ -499,7 +500,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
         const uint32_t d0 = dstart[cs];
         int* cnt = counts[it & 1];
         dev::compact_fluid(lay.masks(st), nx, flist, cnt);
-        dev::patch_links<L, true>(buf, nx, lay.links(st), gstart[cs], g0, g1, desc, d0);
+        dev::patch_links<L, true>(buf, nx, rs, lay.links(st), gstart[cs], g0, g1, desc, d0);
         if (warp0) dev::bulk_wait_read();  // the previous row's bulk stores have read the output rows
         if (leader) counts[(it + 1) & 1][0] = counts[(it + 1) & 1][1] = 0;
         __syncthreads();  // list complete, bounced values in place, output rows free
@@ -527,7 +528,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
 #pragma unroll
                 for (int a = 0; a < L::Q; ++a) {
                     const int ex = L::c(a, 0);
-                    h[a] = S::cvt(buf[a * nx + (ex > 0 ? xm : (ex < 0 ? xp : x))]);
+                    h[a] = S::cvt(buf[a * rs + (ex > 0 ? xm : (ex < 0 ? xp : x))]);
                 }
                 float E[3];
                 load_E<L>(Ef, EF, p, cell, E);
@@ -536,10 +537,10 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
                 typename S::T t[L::Q];
                 round_all<L, S, SR>(out, cell, p, t);
 #pragma unroll
-                for (int a = 0; a < L::Q; ++a) outrow[a * nx + x] = t[a];
+                for (int a = 0; a < L::Q; ++a) outrow[a * rs + x] = t[a];
             } else {
 #pragma unroll
-                for (int a = 0; a < L::Q; ++a) S::put(outrow + a * nx + x, 0.f);
+                for (int a = 0; a < L::Q; ++a) S::put(outrow + a * rs + x, 0.f);
             }
         }
         dev::fence_proxy_async();  // this thread's shared-memory writes before the bulk copies
@@ -547,13 +548,13 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
         if (threadIdx.x < L::Q) {
             // lane a of warp 0: the bulk store of direction a, in its own group
             const int a = threadIdx.x;
-            dev::bulk_store(Pout + (int64_t)a * p.N + rowbase, outrow + a * nx, row_bytes);
+            dev::bulk_store(Pout + (int64_t)a * p.N + rowbase, outrow + a * rs, row_bytes);
             dev::bulk_commit();
         }
         // outgoing links: slot k of (x, b) takes f*_b(x)
         for (uint32_t k = g0 + threadIdx.x; k < g1; k += blockDim.x) {
             const uint32_t d = desc[k - d0];
-            Gout[k] = outrow[(int)(d >> 24) * nx + (int)(d & 0xFFFFFFu)];
+            Gout[k] = outrow[(int)(d >> 24) * rs + (int)(d & 0xFFFFFFu)];
         }
     }
     if (warp0) dev::bulk_wait_all();
@@ -592,29 +593,45 @@ int persistent_grid(K kernel, int threads, size_t smem) {
     return last_blocks;
 }
 
+template <class L, class S, int FORCE, bool EF, bool SR, int RS>
+bool launch_rows(const S*, const void* fin, void* fout, const uint32_t* nbr, const float* Ef, const KParams& p,
+                 cudaStream_t s) {
+    using T = typename S::T;
+    const int rs = RS ? RS : p.nx;
+    const size_t row_bytes = (size_t)p.nx * S::kBytes, srow = (size_t)rs * S::kBytes;
+    const int gcap = dev::window_cap(p.max_row_links, S::kBytes);
+    const int dcap = dev::window_cap(p.max_row_links, 4);
+    const size_t stage_bytes = (size_t)L::Q * srow + 4 * (size_t)p.nx + gcap + dcap;
+    const size_t smem = (size_t)kStages * stage_bytes + (size_t)L::Q * srow + 4 * (size_t)p.nx;
+    if (row_bytes % 16 != 0 || smem > kSmemBudget || p.nx < 32 || p.nx % 4 != 0) return false;
+    const int threads = p.nx >= kRowThreads ? kRowThreads : ((p.nx + 31) / 32) * 32;
+    auto kern = k_step_rows<L, S, FORCE, EF, SR, kStages, RS>;
+    const int blocks = persistent_grid(kern, threads, smem);
+    if (blocks <= 0) return false;
+    const int rows = p.ny * p.nz;
+    kern<<<blocks < rows ? blocks : rows, threads, smem, s>>>((const T*)fin, (T*)fout, nbr, Ef, gcap, dcap, p);
+    return true;
+}
+
+// Row-staged kernel when the rows qualify, with the shared-memory row stride
+// a compile-time 256 or 512 for rows up to that length (the indexing then
+// folds into immediate offsets) and the row length itself above; otherwise
+// the general kernel.
 template <class L, class S, int FORCE, bool EF, bool SR>
 int launch_one(const void* fin, void* fout, const uint32_t* nbr, const float* Ef, const KParams& p, cudaStream_t s) {
     using T = typename S::T;
-    const T* in = (const T*)fin;
-    T* out = (T*)fout;
-    const size_t row_bytes = (size_t)p.nx * S::kBytes;
-    const int gcap = dev::window_cap(p.max_row_links, S::kBytes);
-    const int dcap = dev::window_cap(p.max_row_links, 4);
-    const size_t stage_bytes = (size_t)L::Q * row_bytes + 4 * (size_t)p.nx + gcap + dcap;
-    const size_t smem = (size_t)kStages * stage_bytes + (size_t)L::Q * row_bytes + 4 * (size_t)p.nx;
-    if (row_bytes % 16 == 0 && smem <= kSmemBudget && p.nx >= 32 && p.nx % 4 == 0) {
-        const int threads = p.nx >= kRowThreads ? kRowThreads : ((p.nx + 31) / 32) * 32;
-        auto kern = k_step_rows<L, S, FORCE, EF, SR, kStages>;
-        const int blocks = persistent_grid(kern, threads, smem);
-        if (blocks > 0) {
-            const int rows = p.ny * p.nz;
-            kern<<<blocks < rows ? blocks : rows, threads, smem, s>>>(in, out, nbr, Ef, gcap, dcap, p);
-            return 1;
-        }
-    }
+    const S* tag = nullptr;
+    bool done;
+    if (p.nx <= 256)
+        done = launch_rows<L, S, FORCE, EF, SR, 256>(tag, fin, fout, nbr, Ef, p, s);
+    else if (p.nx <= 512)
+        done = launch_rows<L, S, FORCE, EF, SR, 512>(tag, fin, fout, nbr, Ef, p, s);
+    else
+        done = launch_rows<L, S, FORCE, EF, SR, 0>(tag, fin, fout, nbr, Ef, p, s);
+    if (done) return 1;
     const int bx = p.nx >= kBlock ? kBlock : ((p.nx + 31) / 32) * 32;
     const dim3 grid((unsigned)(p.ny * p.nz), (unsigned)((p.nx + bx - 1) / bx));
-    k_step<L, S, FORCE, EF, SR><<<grid, bx, 0, s>>>(in, out, nbr, Ef, p);
+    k_step<L, S, FORCE, EF, SR><<<grid, bx, 0, s>>>((const T*)fin, (T*)fout, nbr, Ef, p);
     return 1;
 }
 

@@ -170,6 +170,10 @@ class LBM:
         """Device bytes an adjoint call with checkpoint_every=0 may allocate (0 = free memory)."""
         _lib.check(_lib.load().lbm_set_memory_budget(self._h, int(nbytes)), self._h, "lbm_set_memory_budget")
 
+    def release_workspace(self):
+        """Free the device buffers kept by earlier adjoint calls."""
+        _lib.check(_lib.load().lbm_release_workspace(self._h), self._h, "lbm_release_workspace")
+
     def adjoint_stats(self) -> dict:
         out = (ctypes.c_int64 * 5)()
         _lib.check(_lib.load().lbm_adjoint_stats(self._h, out), self._h, "lbm_adjoint_stats")

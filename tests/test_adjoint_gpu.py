@@ -313,3 +313,28 @@ def test_adjoint_f16_storage_close_to_f32():
     assert abs(a["dL_dtau"] / b["dL_dtau"] - 1) < 1e-2
     assert abs(a["dL_dB"][2] / b["dL_dB"][2] - 1) < 1e-2
     assert rel_linf(a["dE"], b["dE"]) < 1e-2
+
+
+def test_workspace_reused_across_calls():
+    """The context keeps the adjoint's buffers between calls; calls with
+    different schedules on the same context (state reset in between), before
+    and after lbm_release_workspace, give the same numbers bit for bit."""
+    shape, mask, B, Ef, rho0, u0, wr, wj = _case("D3V19")
+    T, tb = 17, 4
+    sim = _gpu_sim("D3V19", shape, mask, B, Ef, rho0, u0, 0.8, "term", storage="f16")
+    blob = sim.save_state()
+    outs = []
+    for K in (5, -3, 0, "release", 5):
+        if K == "release":
+            sim.release_workspace()
+            continue
+        sim.load_state(blob)
+        dE = torch.empty(sim.D * sim.N, dtype=torch.float64, device="cuda")
+        res = sim.adjoint(tb, T, wr.reshape(-1), wj.reshape(-1), checkpoint_every=K, dL_dE=dE)
+        outs.append((res, dE.cpu().numpy(), sim.adjoint_stats()["schedule"]))
+    assert [o[2] for o in outs] == ["segments", "binomial", "store_all", "segments"]
+    for res, dE, _ in outs[1:]:
+        assert res["loss"] == outs[0][0]["loss"] and res["dL_dtau"] == outs[0][0]["dL_dtau"]
+        assert np.array_equal(np.asarray(res["dL_dB"]), np.asarray(outs[0][0]["dL_dB"]))
+        assert np.array_equal(dE, outs[0][1])
+    sim.close()

@@ -74,6 +74,23 @@ def test_parity_2d(storage, force, efield, shape):
     sim.close()
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("shape", [(12, 200), (10, 320), (6, 640)])
+def test_parity_row_strides(storage, shape):
+    """The row-staged step kernel keeps its shared-memory rows at a stride of
+    256 elements for rows up to 256 cells (200: padded), 512 up to 512 (320)
+    and the row length above (640); D2V9 disks, 40 steps, against the oracle."""
+    solid, _ = wl.boolean_obstacles(shape, 3.0, 0.8, seed=47)
+    rho, u = _fields(shape, 2, 48)
+    E, B = (2e-4, -5e-5, 0.0), (0.0, 0.0, 3e-3)
+    rg, jg, totg, sim = gpu_run("D2V9", shape, solid, 0.7, 40, storage, "term", E, B, rho, u)
+    ro, jo, toto, _, _ = oracle_run("D2V9", shape, solid, 0.7, 40, "term", E, B, rho, u)
+    er, ej = rel_linf(rg, ro), rel_linf(jg, jo)
+    print(f"strides {shape} {storage}: rho {er:.3e} j {ej:.3e}")
+    assert er <= TOL[storage] and ej <= TOL[storage], (er, ej)
+    sim.close()
+
+
 CASES_3D = [(s, f, e, shp) for s in ("f32", "f16", "bf16") for f in ("term", "shift") for e in (False, True)
             for shp in ((9, 10, 133), (8, 12, 64))]
 
