@@ -337,7 +337,7 @@ def adjoint_512(T: int, dev, stream):
     # an adjoint field: FP32 lambda plus one FP32 per link (the state holds one FP16 per link)
     lam_field = 4 * 19 * N + 2 * max(0, state - 2 * 19 * N) + 1024
     fixed = 2 * lam_field + 2 * state + dE.numel() * 8 + wj.numel() * 4
-    budget = 180 * 10**9 - fixed
+    budget = 180 * 10**9 - fixed - 4 * 10**9  # margin: CUDA context, library scratch, torch buffers
     sim.set_memory_budget(budget)
     torch.cuda.synchronize()
     t0 = time.perf_counter()

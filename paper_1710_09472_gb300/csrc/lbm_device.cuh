@@ -262,6 +262,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
         if (clock64() - t0 > limit) return false;
     return true;
 }
+// Sleeps about n SM clock cycles.  After a wait has run out, a block pauses
+// so that bulk copies it issued earlier land before it moves on or exits.
+__device__ __forceinline__ void pause_cycles(long long n) {
+    const long long t0 = clock64();
+    while (clock64() - t0 < n) __nanosleep(1000);
+}
+
 // global -> shared, completing `bytes` on the mbarrier
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(

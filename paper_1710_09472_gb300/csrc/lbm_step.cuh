@@ -48,8 +48,12 @@ struct Shells {
     }
 };
 
-template <class L, int FORCE>
-__device__ __forceinline__ void collide(const float* h, const float* E, const KParams& p, float* out) {
+// The post-collision values go to emit(a, h*_a, h*_a+1) pair by pair (a odd)
+// and then to emit_rest(h*_0), so a caller can round and store each pair as
+// soon as it exists instead of holding all Q values.
+template <class L, int FORCE, class Emit, class EmitRest>
+__device__ __forceinline__ void collide_emit(const float* h, const float* E, const KParams& p, Emit&& emit,
+                                             EmitRest&& emit_rest) {
     constexpr int kAx = Shells<L>::kAx, kDg = Shells<L>::diag();
     float drho = h[0], j[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -121,11 +125,21 @@ __device__ __forceinline__ void collide(const float* h, const float* E, const KP
         const float odd = dev::edot<L>(a, ax ? Va : Vd);
         const float ha = fmaf(omm, h[a], even) + odd;
         const float hb = fmaf(omm, h[a + 1], even) - odd;
-        out[a] = ha;
-        out[a + 1] = hb;
         rest -= ha + hb;
+        emit(a, ha, hb);
     }
-    out[0] = rest;
+    emit_rest(rest);
+}
+
+template <class L, int FORCE>
+__device__ __forceinline__ void collide(const float* h, const float* E, const KParams& p, float* out) {
+    collide_emit<L, FORCE>(
+        h, E, p,
+        [&](int a, float ha, float hb) {
+            out[a] = ha;
+            out[a + 1] = hb;
+        },
+        [&](float rest) { out[0] = rest; });
 }
 
 // Error-free transformations (Knuth TwoSum, FMA TwoProd) for the compensated
@@ -283,16 +297,16 @@ struct Rng {
     }
 };
 
-// Rounds the Q post-collision values to storage: out[0] (converted as a pair
-// with itself), then the opposite pairs (a, a + 1), stochastically when SR.
+// Rounds the Q post-collision values to storage: the opposite pairs (a, a + 1),
+// then out[0] (converted as a pair with itself), stochastically when SR.
 template <class L, class S, bool SR>
 __device__ __forceinline__ void round_all(const float* out, uint32_t cell, const KParams& p, typename S::T* t) {
     if (SR) {
         Rng rng(cell, p);
         typename S::T unused;
-        S::sr2(out[0], out[0], rng.pair(), t[0], unused);
 #pragma unroll
         for (int a = 1; a < L::Q; a += 2) S::sr2(out[a], out[a + 1], rng.pair(), t[a], t[a + 1]);
+        S::sr2(out[0], out[0], rng.pair(), t[0], unused);
     } else {
 #pragma unroll
         for (int a = 0; a < L::Q; ++a) S::put(&t[a], out[a]);
@@ -493,6 +507,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
         if (ok && !dev::mbar_wait(&bar[cs], (uint32_t)(it / STAGES) & 1u)) {
             ok = false;
             if (p.status) atomicExch(p.status, 1);
+            dev::pause_cycles(1ll << 22);  // let this block's copies in flight land
         }
         unsigned char* st = smem_raw + cs * sbytes;
         T* buf = lay.rows(st);
@@ -504,7 +519,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
         if (warp0) dev::bulk_wait_read();  // the previous row's bulk stores have read the output rows
         if (leader) counts[(it + 1) & 1][0] = counts[(it + 1) & 1][1] = 0;
         __syncthreads();  // list complete, bounced values in place, output rows free
-        if (warp0) {
+        if (warp0 && ok) {
             // refill the stage of the previous row: every thread is past its
             // last reads of it (the link pass that follows the output)
             const int rn = r + (STAGES - 1) * G;
@@ -532,12 +547,38 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
                 }
                 float E[3];
                 load_E<L>(Ef, EF, p, cell, E);
-                float out[L::Q];
-                collide_any<L, S, FORCE>(h, E, p, out);
-                typename S::T t[L::Q];
-                round_all<L, S, SR>(out, cell, p, t);
+                if (S::kBytes == 4) {
+                    float out[L::Q];
+                    collide_any<L, S, FORCE>(h, E, p, out);
+                    typename S::T t[L::Q];
+                    round_all<L, S, SR>(out, cell, p, t);
 #pragma unroll
-                for (int a = 0; a < L::Q; ++a) outrow[a * rs + x] = t[a];
+                    for (int a = 0; a < L::Q; ++a) outrow[a * rs + x] = t[a];
+                } else {
+                    // 16-bit storage: each pair is rounded and stored as soon as it exists
+                    Rng rng(cell, p);
+                    collide_emit<L, FORCE>(
+                        h, E, p,
+                        [&](int a, float ha, float hb) {
+                            T ta, tb;
+                            if (SR) {
+                                S::sr2(ha, hb, rng.pair(), ta, tb);
+                            } else {
+                                S::put(&ta, ha);
+                                S::put(&tb, hb);
+                            }
+                            outrow[a * rs + x] = ta;
+                            outrow[(a + 1) * rs + x] = tb;
+                        },
+                        [&](float rest) {
+                            T t0, unused;
+                            if (SR)
+                                S::sr2(rest, rest, rng.pair(), t0, unused);
+                            else
+                                S::put(&t0, rest);
+                            outrow[x] = t0;
+                        });
+                }
             } else {
 #pragma unroll
                 for (int a = 0; a < L::Q; ++a) S::put(outrow + a * rs + x, 0.f);
