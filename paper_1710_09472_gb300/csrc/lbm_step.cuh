@@ -48,17 +48,35 @@ struct Shells {
     }
 };
 
+// Arithmetic helpers of the value type V of collide_emit (float here).
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float vdiv(float c, float x) { return c / x; }
+
+template <class L, class V>
+__device__ __forceinline__ V vedot(int a, const V* v) {
+    V r(0.f);
+    if (L::c(a, 0) > 0) r += v[0];
+    if (L::c(a, 0) < 0) r -= v[0];
+    if (L::c(a, 1) > 0) r += v[1];
+    if (L::c(a, 1) < 0) r -= v[1];
+    if (L::D == 3) {
+        if (L::c(a, 2) > 0) r += v[2];
+        if (L::c(a, 2) < 0) r -= v[2];
+    }
+    return r;
+}
+
 // The post-collision values go to emit(a, h*_a, h*_a+1) pair by pair (a odd)
 // and then to emit_rest(h*_0), so a caller can round and store each pair as
 // soon as it exists instead of holding all Q values.
-template <class L, int FORCE, class Emit, class EmitRest>
-__device__ __forceinline__ void collide_emit(const float* h, const float* E, const KParams& p, Emit&& emit,
+template <class L, int FORCE, class V, class Emit, class EmitRest>
+__device__ __forceinline__ void collide_emit(const V* h, const V* E, const KParams& p, Emit&& emit,
                                              EmitRest&& emit_rest) {
     constexpr int kAx = Shells<L>::kAx, kDg = Shells<L>::diag();
-    float drho = h[0], j[3] = {0.f, 0.f, 0.f};
+    V drho = h[0], j[3] = {V(0.f), V(0.f), V(0.f)};
 #pragma unroll
     for (int a = 1; a < L::Q; a += 2) {
-        const float sum = h[a] + h[a + 1], dif = h[a] - h[a + 1];
+        const V sum = h[a] + h[a + 1], dif = h[a] - h[a + 1];
         drho += sum;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -66,65 +84,65 @@ __device__ __forceinline__ void collide_emit(const float* h, const float* E, con
             if (L::c(a, d) < 0) j[d] -= dif;
         }
     }
-    const float rho = p.rho0 + drho * p.inv_scale;
-    const float q = p.inv_scale * p.cs_inv / rho;  // u = j~ q  (xi units)
-    const float u[3] = {j[0] * q, j[1] * q, j[2] * q};
-    const float srho = p.scale * rho;
-    const float om = p.omega, omm = 1.0f - p.omega;
-    const float scr = srho * p.cs;  // s c_s rho
-    float ue[3], v[3], bu[3] = {0.f, 0.f, 0.f}, Ku, cq;
+    const V rho = vfma(drho, V(p.inv_scale), V(p.rho0));
+    const V q = vdiv(p.inv_scale * p.cs_inv, rho);  // u = j~ q  (xi units)
+    const V u[3] = {j[0] * q, j[1] * q, j[2] * q};
+    const V srho = V(p.scale) * rho;
+    const V om(p.omega), omm(1.0f - p.omega);
+    const V scr = srho * V(p.cs);  // s c_s rho
+    V ue[3], v[3], bu[3] = {V(0.f), V(0.f), V(0.f)}, Ku, cq;
     if (FORCE == 0) {
-        const float a0 = E[0] + (u[1] * p.B[2] - u[2] * p.B[1]);
-        const float a1 = E[1] + (u[2] * p.B[0] - u[0] * p.B[2]);
-        const float a2 = (L::D == 3) ? E[2] + (u[0] * p.B[1] - u[1] * p.B[0]) : 0.f;
-        ue[0] = u[0] + p.tau * a0;
-        ue[1] = u[1] + p.tau * a1;
-        ue[2] = u[2] + p.tau * a2;
+        const V a0 = E[0] + (u[1] * V(p.B[2]) - u[2] * V(p.B[1]));
+        const V a1 = E[1] + (u[2] * V(p.B[0]) - u[0] * V(p.B[2]));
+        const V a2 = (L::D == 3) ? E[2] + (u[0] * V(p.B[1]) - u[1] * V(p.B[0])) : V(0.f);
+        ue[0] = vfma(V(p.tau), a0, u[0]);
+        ue[1] = vfma(V(p.tau), a1, u[1]);
+        ue[2] = vfma(V(p.tau), a2, u[2]);
         // odd part of w heq~ at u*: W1 (e . (w j~ + s c_s rho a))
-        v[0] = om * j[0] + scr * a0;
-        v[1] = om * j[1] + scr * a1;
-        v[2] = om * j[2] + scr * a2;
+        v[0] = vfma(om, j[0], scr * a0);
+        v[1] = vfma(om, j[1], scr * a1);
+        v[2] = vfma(om, j[2], scr * a2);
         Ku = om * srho * (ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2]);
-        cq = om * srho * p.Cp;
+        cq = om * srho * V(p.Cp);
     } else {
         ue[0] = u[0];
         ue[1] = u[1];
         ue[2] = u[2];
-        v[0] = om * j[0] + scr * E[0];
-        v[1] = om * j[1] + scr * E[1];
-        v[2] = om * j[2] + scr * E[2];
-        const float uE = u[0] * E[0] + u[1] * E[1] + u[2] * E[2];
-        const float tb = 2.f * srho * p.cs_inv;  // 2 s rho / c_s times (B x u)
-        bu[0] = tb * (p.B[1] * u[2] - p.B[2] * u[1]);
-        bu[1] = tb * (p.B[2] * u[0] - p.B[0] * u[2]);
-        bu[2] = tb * (p.B[0] * u[1] - p.B[1] * u[0]);
-        Ku = srho * (om * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) + 2.f * uE);
-        cq = srho * p.Cp;
+        v[0] = vfma(om, j[0], scr * E[0]);
+        v[1] = vfma(om, j[1], scr * E[1]);
+        v[2] = vfma(om, j[2], scr * E[2]);
+        const V uE = u[0] * E[0] + u[1] * E[1] + u[2] * E[2];
+        const V tb = V(2.f * p.cs_inv) * srho;  // 2 s rho / c_s times (B x u)
+        bu[0] = tb * (V(p.B[1]) * u[2] - V(p.B[2]) * u[1]);
+        bu[1] = tb * (V(p.B[2]) * u[0] - V(p.B[0]) * u[2]);
+        bu[2] = tb * (V(p.B[0]) * u[1] - V(p.B[1]) * u[0]);
+        Ku = srho * vfma(om, u[0] * u[0] + u[1] * u[1] + u[2] * u[2], V(2.f) * uE);
+        cq = srho * V(p.Cp);
     }
-    const float c0 = om * p.A * drho;
+    const V c0 = V(p.omega * p.A) * drho;
     // per shell: the even constant, the (e.u) coefficient and the odd vector
-    const float e0a = p.w[kAx] * (c0 + p.k2[kAx] * Ku), e0d = p.w[kDg] * (c0 + p.k2[kDg] * Ku);
-    const float cqa = p.w[kAx] * cq, cqd = p.w[kDg] * cq;
-    float Va[3], Vd[3];
+    const V e0a = V(p.w[kAx]) * vfma(V(p.k2[kAx]), Ku, c0), e0d = V(p.w[kDg]) * vfma(V(p.k2[kDg]), Ku, c0);
+    const V cqa = V(p.w[kAx]) * cq, cqd = V(p.w[kDg]) * cq;
+    V Va[3], Vd[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        Va[d] = fmaf(p.W1lo[kAx], v[d], p.W1hi[kAx] * v[d]);
-        Vd[d] = fmaf(p.W1lo[kDg], v[d], p.W1hi[kDg] * v[d]);
+        Va[d] = vfma(V(p.W1lo[kAx]), v[d], V(p.W1hi[kAx]) * v[d]);
+        Vd[d] = vfma(V(p.W1lo[kDg]), v[d], V(p.W1hi[kDg]) * v[d]);
         if (FORCE == 1) {
-            Va[d] = fmaf(p.w[kAx] * p.k2[kAx], bu[d], Va[d]);
-            Vd[d] = fmaf(p.w[kDg] * p.k2[kDg], bu[d], Vd[d]);
+            Va[d] = vfma(V(p.w[kAx] * p.k2[kAx]), bu[d], Va[d]);
+            Vd[d] = vfma(V(p.w[kDg] * p.k2[kDg]), bu[d], Vd[d]);
         }
     }
-    float rest = drho;
+    V rest = drho;
 #pragma unroll
     for (int a = 1; a < L::Q; a += 2) {
         const bool ax = dev::esq<L>(a) == 1;
-        const float eu = dev::edot<L>(a, ue);
-        const float g = (FORCE == 1) ? fmaf(om, eu, 2.f * dev::edot<L>(a, E)) : eu;
-        const float even = fmaf(ax ? cqa : cqd, eu * g, ax ? e0a : e0d);
-        const float odd = dev::edot<L>(a, ax ? Va : Vd);
-        const float ha = fmaf(omm, h[a], even) + odd;
-        const float hb = fmaf(omm, h[a + 1], even) - odd;
+        const V eu = vedot<L>(a, ue);
+        const V g = (FORCE == 1) ? vfma(om, eu, V(2.f) * vedot<L>(a, E)) : eu;
+        const V even = vfma(ax ? cqa : cqd, eu * g, ax ? e0a : e0d);
+        const V odd = vedot<L>(a, ax ? Va : Vd);
+        const V ha = vfma(omm, h[a], even) + odd;
+        const V hb = vfma(omm, h[a + 1], even) - odd;
         rest -= ha + hb;
         emit(a, ha, hb);
     }
@@ -221,35 +239,48 @@ __device__ __forceinline__ void collide_acc(const float* h, const float* E, cons
         two_sum(pp, scr * F[d], vh[d], e);
         vl[d] = e + ep + om * jl[d];
     }
+    // per shell (axis, diagonal): V_s = W1_s v as a double-float product, plus
+    // the B term 2 s rho w_s k2_s (B x u) / c_s (FORCE 1) in the low part; the
+    // even constant and the (e.u) coefficient, as in collide()
+    constexpr int kAx = Shells<L>::kAx, kDg = Shells<L>::diag();
+    float Vh[2][3], Vl[2][3];
+#pragma unroll
+    for (int sh = 0; sh < 2; ++sh) {
+        const int rep = sh == 0 ? kAx : kDg;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            float e;
+            two_prod(p.W1hi[rep], vh[d], Vh[sh][d], e);
+            Vl[sh][d] = e + p.W1hi[rep] * vl[d] + p.W1lo[rep] * vh[d];
+            if (FORCE == 1) Vl[sh][d] += p.w[rep] * p.k2[rep] * bu[d];
+        }
+    }
     const float u2 = ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2];
-    const float omAdr = om * p.A * drho_f;
+    const float c0 = om * p.A * drho_f;
+    const float Ku = (FORCE == 1) ? srho * (om * u2 + 2.f * uE) : om * srho * u2;
+    const float cq = (FORCE == 1) ? srho * p.Cp : om * srho * p.Cp;
+    const float e0a = p.w[kAx] * (c0 + p.k2[kAx] * Ku), e0d = p.w[kDg] * (c0 + p.k2[kDg] * Ku);
+    const float cqa = p.w[kAx] * cq, cqd = p.w[kDg] * cq;
     float rest = drho, rest_lo = drho_lo;
 #pragma unroll
     for (int a = 1; a < L::Q; a += 2) {
+        const int sh = dev::esq<L>(a) == 1 ? 0 : 1;
         const float eu = dev::edot<L>(a, ue);
-        float even = p.w[a] * (omAdr + om * srho * (p.Cp * eu * eu + p.k2[a] * u2));
-        // e . v in double-float
-        float evh = 0.f, evl = 0.f;
+        const float g = (FORCE == 1) ? fmaf(om, eu, 2.f * dev::edot<L>(a, E)) : eu;
+        const float even = fmaf(sh == 0 ? cqa : cqd, eu * g, sh == 0 ? e0a : e0d);
+        // odd = e . V_s in double-float
+        float oh = 0.f, ol = 0.f;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             float e;
             if (L::c(a, d) > 0) {
-                two_sum(evh, vh[d], evh, e);
-                evl += e + vl[d];
+                two_sum(oh, Vh[sh][d], oh, e);
+                ol += e + Vl[sh][d];
             }
             if (L::c(a, d) < 0) {
-                two_sum(evh, -vh[d], evh, e);
-                evl += e - vl[d];
+                two_sum(oh, -Vh[sh][d], oh, e);
+                ol += e - Vl[sh][d];
             }
-        }
-        // odd = W1 (e . v): double-float product
-        float oh, ol;
-        two_prod(p.W1hi[a], evh, oh, ol);
-        ol += p.W1hi[a] * evl + p.W1lo[a] * evh;
-        if (FORCE == 1) {
-            const float eE = dev::edot<L>(a, E);
-            even += 2.f * srho * p.w[a] * (p.Cp * eu * eE + p.k2[a] * uE);
-            ol += p.w[a] * p.k2[a] * dev::edot<L>(a, bu);
         }
         // (1 - w) h + even +/- odd, rounded once
         float pa, ea, pb, eb, sa, sb, e1, e2;
@@ -548,6 +579,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
                 float E[3];
                 load_E<L>(Ef, EF, p, cell, E);
                 if (S::kBytes == 4) {
+                    // FP32 storage: compensated collision
                     float out[L::Q];
                     collide_any<L, S, FORCE>(h, E, p, out);
                     typename S::T t[L::Q];
@@ -612,26 +644,46 @@ constexpr int kStages = 2;
 constexpr int kRowThreads = 256;
 constexpr size_t kSmemBudget = 160 * 1024;
 
+// Block size and persistent grid of the row-staged kernel.  A block walks
+// whole rows, so any multiple of 32 threads up to the row length works; the
+// choice is the one with the most co-resident blocks per SM (occupancy API),
+// the larger block on a tie: more rows in flight per SM hide the per-row
+// copy latency (256-cell FP16 rows: 160 threads give six blocks per SM,
+// 0.367 ms per 256^3 step, against four blocks and 0.395 ms at 256).
+struct Shape {
+    int threads, blocks;
+};
 template <class K>
-int persistent_grid(K kernel, int threads, size_t smem) {
+Shape launch_shape(K kernel, int nx, size_t smem) {
     static std::mutex mu;
     static const void* last_k = nullptr;
     static size_t last_smem = 0;
-    static int last_threads = 0, last_blocks = 0, sms = 0;
+    static int last_nx = 0;
+    static Shape last{0, 0};
     std::lock_guard<std::mutex> lock(mu);
-    if ((const void*)kernel != last_k || smem != last_smem || threads != last_threads) {
-        int dev = 0;
+    if ((const void*)kernel != last_k || smem != last_smem || nx != last_nx) {
+        int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+        const int tmax = nx >= kRowThreads ? kRowThreads : ((nx + 31) / 32) * 32;
+        Shape best{tmax, 0};
+        int best_per_sm = -1;
+        for (int t = tmax; t >= 32 && t >= tmax / 2; t -= 32) {
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, t, smem);
+            if (per_sm > best_per_sm) {
+                best_per_sm = per_sm;
+                best.threads = t;
+            }
+        }
+        best.blocks = best_per_sm > 0 ? best_per_sm * sms : 0;
         last_k = (const void*)kernel;
         last_smem = smem;
-        last_threads = threads;
-        last_blocks = per_sm > 0 ? per_sm * sms : 0;
+        last_nx = nx;
+        last = best;
     }
-    return last_blocks;
+    return last;
 }
 
 template <class L, class S, int FORCE, bool EF, bool SR, int RS>
@@ -645,9 +697,9 @@ bool launch_rows(const S*, const void* fin, void* fout, const uint32_t* nbr, con
     const size_t stage_bytes = (size_t)L::Q * srow + 4 * (size_t)p.nx + gcap + dcap;
     const size_t smem = (size_t)kStages * stage_bytes + (size_t)L::Q * srow + 4 * (size_t)p.nx;
     if (row_bytes % 16 != 0 || smem > kSmemBudget || p.nx < 32 || p.nx % 4 != 0) return false;
-    const int threads = p.nx >= kRowThreads ? kRowThreads : ((p.nx + 31) / 32) * 32;
     auto kern = k_step_rows<L, S, FORCE, EF, SR, kStages, RS>;
-    const int blocks = persistent_grid(kern, threads, smem);
+    const Shape sh = launch_shape(kern, p.nx, smem);
+    const int threads = sh.threads, blocks = sh.blocks;
     if (blocks <= 0) return false;
     const int rows = p.ny * p.nz;
     kern<<<blocks < rows ? blocks : rows, threads, smem, s>>>((const T*)fin, (T*)fout, nbr, Ef, gcap, dcap, p);
