@@ -40,7 +40,6 @@ using dev::edot;
 using dev::kBlock;
 using dev::warp_sum;
 constexpr int kSlots = 5;         // gB[3], gtau, loss
-constexpr int kAdjMaxChunks = 64;  // nx <= 2048 for the row-staged reverse step
 
 // Adds the block's sums of acc[kSlots] into slots[block * kSlots + k].
 __device__ __forceinline__ void block_accumulate(double* acc, double* __restrict__ slots, int64_t block) {
@@ -375,60 +374,66 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(
 // ---------------------------------------------------------------------------
 // Row-staged reverse step (persistent; block b takes rows b, b + G, ...).
 // One stage holds, for the row (y, z):
+//   - with dL/dE, the row's D rows of it (FP64, accumulated in place and
+//     stored back after the row); with a per-cell field, its D rows of E;
 //   - the Q pull rows of the forward state P_t: direction a from row
 //     (y - e_ay, z - e_az), read at x - e_ax;
-//   - the row's link masks;
+//   - the row's cell order (fluid cells first, ascending x);
 //   - its window of P_t's link buffer (bounced pulls);
 //   - the Q gather rows of lam_{t+1}: direction a from row
 //     (y + e_ay, z + e_az), read at x + e_ax;
 //   - its windows of lam_{t+1}'s link buffer (bounced gathers) and of the
 //     link descriptors;
-// all by bulk asynchronous copies issued by one thread, completing on the
-// stage's mbarrier (bounded waits, as in the forward's row-staged kernel).
-// One pass over the row's links patches both bounced reads into the staged
-// rows (the solid neighbour's slot, read by that cell alone), so cells read
-// their rows without link logic; fluid cells are compacted; lam_t goes
-// through shared-memory output rows (zeros for solid cells) that leave by
-// bulk stores, and one pass over the links copies lam_bbar(x) into the row's
-// range of the new link buffer.  dL/dB, dL/dtau and the loss stay in
-// registers until the block's single reduction at the end.
+// all by bulk asynchronous copies, completing on the stage's mbarrier, armed
+// and issued by lane 0 of the last warp (as in the forward's row-staged
+// kernel; waits are bounded).  One pass over the
+// row's links patches both bounced reads into the staged rows (the solid
+// neighbour's slot, read by that cell alone), so cells read their rows
+// without link logic.  Thread i takes the i-th cell of the row's order, so
+// each thread's FP64 sums see the same cells in the same order on every run.
+// lam_t goes through shared-memory output rows (zeros for solid cells) that
+// leave by bulk stores, and one pass over the links copies lam_bbar(x) into
+// the row's range of the new link buffer.  dL/dB, dL/dtau and the loss stay
+// in registers until the block's single reduction at the end.
 // ---------------------------------------------------------------------------
 template <class L, class S>
 struct AdjLayout {
-    int nx, rs, gcapP, gcapL;  // row length, shared-memory row stride (elements); gcapL also bounds the
-                               // descriptor window (4-byte elements)
-    int gerow, efrow;          // bytes of the staged dL/dE rows (FP64) and E rows (FP32), 0 when absent
+    int nx, rs, lorder, gcapP, gcapL;  // row length, shared-memory row stride (elements), order entries;
+                                       // gcapL also bounds the descriptor window (4-byte elements)
+    int gerow, efrow;                  // bytes of the staged dL/dE rows (FP64) and E rows (FP32), 0 when absent
     __device__ __host__ int prow() const { return L::Q * rs * S::kBytes; }
     __device__ __host__ int lrow() const { return L::Q * rs * 4; }
-    __device__ __host__ int bytes() const { return gerow + prow() + 4 * nx + gcapP + lrow() + 2 * gcapL + efrow; }
+    __device__ __host__ int bytes() const {
+        return gerow + prow() + 2 * lorder + gcapP + lrow() + 2 * gcapL + efrow;
+    }
     __device__ unsigned char* gerows(unsigned char* st) const { return st; }
     __device__ unsigned char* prows(unsigned char* st) const { return st + gerow; }
-    __device__ unsigned char* masks(unsigned char* st) const { return st + gerow + prow(); }
-    __device__ unsigned char* plinks(unsigned char* st) const { return masks(st) + 4 * nx; }
+    __device__ unsigned char* order(unsigned char* st) const { return st + gerow + prow(); }
+    __device__ unsigned char* plinks(unsigned char* st) const { return order(st) + 2 * lorder; }
     __device__ unsigned char* lrows(unsigned char* st) const { return plinks(st) + gcapP; }
     __device__ unsigned char* llinks(unsigned char* st) const { return lrows(st) + lrow(); }
     __device__ unsigned char* descs(unsigned char* st) const { return llinks(st) + gcapL; }
     __device__ unsigned char* efrows(unsigned char* st) const { return descs(st) + gcapL; }
 };
 
-// Issued by one thread (lane 0 of warp 0; the other lanes return): the bulk
-// copies of row `row` into stage `st`, all completing on `bar`; the window
-// starts are written before the barrier is armed.  With gE, the row's dL/dE
-// (accumulated in place, stored back after the row); with Ef, its E.
+// One thread: arms a stage's mbarrier with the byte count of row `row`
+// (links [g0, g1)), records where its windows start (ws[0]: P_t's link
+// window; ws[1]: lam's link window and the descriptor window, which start at
+// the same element), and issues the row's copies into stage st, all
+// completing on bar.  With gE, the row's dL/dE (accumulated in place, stored
+// back after the row); with Ef, its E.
 template <class L, class S>
 __device__ __forceinline__ void adj_stage(unsigned char* st, const AdjLayout<L, S>& lay, uint64_t* bar,
-                                          const typename S::T* P, const float* lam, const uint32_t* nbr,
-                                          const double* gE, const float* Ef, int row, uint32_t g0, uint32_t g1,
-                                          uint32_t* ws, const KParams& p) {
-    if ((threadIdx.x & 31) != 0) return;
+                                          const typename S::T* P, const float* lam, const double* gE, const float* Ef,
+                                          int row, uint32_t g0, uint32_t g1, uint32_t* ws, const KParams& p) {
     const uint32_t prb = (uint32_t)p.nx * S::kBytes, lrb = (uint32_t)p.nx * 4u;
     const int rs = lay.rs;
     uint64_t pb0, pb1, lb0, lb1;
     dev::window_bytes(g0, g1, S::kBytes, pb0, pb1);
     dev::window_bytes(g0, g1, 4, lb0, lb1);
     ws[0] = (uint32_t)(pb0 / S::kBytes);
-    ws[1] = (uint32_t)(lb0 / 4);  // the lam-link and descriptor windows start at the same element
-    dev::mbar_expect_tx(bar, L::Q * (prb + lrb) + 4u * (uint32_t)p.nx + (uint32_t)(pb1 - pb0) +
+    ws[1] = (uint32_t)(lb0 / 4);
+    dev::mbar_expect_tx(bar, L::Q * (prb + lrb) + 2u * (uint32_t)lay.lorder + (uint32_t)(pb1 - pb0) +
                                  2u * (uint32_t)(lb1 - lb0) + (lay.gerow ? L::D * (uint32_t)p.nx * 8u : 0u) +
                                  (lay.efrow ? L::D * (uint32_t)p.nx * 4u : 0u));
     const int y = row % p.ny, z = row / p.ny;
@@ -445,7 +450,7 @@ __device__ __forceinline__ void adj_stage(unsigned char* st, const AdjLayout<L, 
         dev::bulk_load(pr + a * rs * S::kBytes, P + (int64_t)a * p.N + ((int64_t)zsP * p.ny + ysP) * p.nx, prb, bar);
         dev::bulk_load(lr + a * rs * 4, lam + (int64_t)a * p.N + ((int64_t)zsL * p.ny + ysL) * p.nx, lrb, bar);
     }
-    dev::bulk_load(lay.masks(st), nbr + (int64_t)row * p.nx, 4u * (uint32_t)p.nx, bar);
+    dev::bulk_load(lay.order(st), p.rorder + (int64_t)row * lay.lorder, 2u * (uint32_t)lay.lorder, bar);
     if (pb1 > pb0)
         dev::bulk_load(lay.plinks(st), reinterpret_cast<const unsigned char*>(P) + p.gofs + pb0, (uint32_t)(pb1 - pb0),
                        bar);
@@ -473,7 +478,6 @@ template <class L, class S, int FORCE, bool EF, bool WIN, int STAGES, int RS>
 __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __restrict__ P,
                                                          const float* __restrict__ lam_in,
                                                          float* __restrict__ lam_out,
-                                                         const uint32_t* __restrict__ nbr,
                                                          const float* __restrict__ Ef,
                                                          const float* __restrict__ w_rho,
                                                          const float* __restrict__ w_j, double* __restrict__ gE,
@@ -482,19 +486,17 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int nx = p.nx;
     const int rs = RS ? RS : nx;  // shared-memory row stride: a constant for the common row lengths
-    const AdjLayout<L, S> lay{nx, rs, gcapP, gcapL, gE ? L::D * rs * 8 : 0, EF ? L::D * rs * 4 : 0};
+    const AdjLayout<L, S> lay{nx, rs, p.lorder, gcapP, gcapL, gE ? L::D * rs * 8 : 0, EF ? L::D * rs * 4 : 0};
     const int sbytes = lay.bytes();
     float* outrow = reinterpret_cast<float*>(smem_raw + STAGES * sbytes);
-    uint32_t* flist = reinterpret_cast<uint32_t*>(outrow + L::Q * rs);
     __shared__ __align__(8) uint64_t bar[STAGES];
-    __shared__ int wcnt[kAdjMaxChunks];  // fluid cells per 32-cell chunk of the row
-    __shared__ int nfluid;
     __shared__ uint32_t wstart[STAGES][2];
     float* lamG_out = link_part(lam_out, p);
     const int R = p.ny * p.nz;
     const int G = gridDim.x;
     const bool leader = threadIdx.x == 0;
-    const bool warp0 = threadIdx.x < 32;
+    const int warp = (int)(threadIdx.x >> 5), nw = (int)(blockDim.x >> 5), lane = (int)(threadIdx.x & 31);
+    const bool issuer = (int)threadIdx.x == (int)blockDim.x - 32;  // lane 0 of the last warp
     auto range = [&](int row, uint32_t& g0, uint32_t& g1) {
         g0 = g1 = 0u;
         if (row < R) {
@@ -508,23 +510,24 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
-    if (warp0) {
+    if (issuer) {
 #pragma unroll
         for (int k = 0; k < STAGES - 1; ++k) {
             const int rk = blockIdx.x + k * G;
             if (rk < R) {
                 uint32_t g0, g1;
                 range(rk, g0, g1);
-                adj_stage<L, S>(smem_raw + k * sbytes, lay, &bar[k], P, lam_in, nbr, gE, Ef, rk, g0, g1, wstart[k],
-                                p);
+                adj_stage<L, S>(smem_raw + k * sbytes, lay, &bar[k], P, lam_in, gE, Ef, rk, g0, g1, wstart[k], p);
             }
         }
     }
     double acc[kSlots] = {0.0, 0.0, 0.0, 0.0, 0.0};
     int it = 0;
-    bool ok = true;  // false once a wait has run out: no further waits
+    bool ok = true;  // false once a wait has run out (the same in every thread after the first barrier)
     for (int r = blockIdx.x; r < R; r += G, ++it) {
         const int cs = it % STAGES;
+        const int rn = r + (STAGES - 1) * G;       // the row refilled during this one ...
+        const int sn = (it + STAGES - 1) % STAGES;  // ... into the stage of the previous row
         uint32_t g0, g1;
         range(r, g0, g1);
         if (ok && !dev::mbar_wait(&bar[cs], (uint32_t)(it / STAGES) & 1u)) {
@@ -537,32 +540,28 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
         double* ge_s = reinterpret_cast<double*>(lay.gerows(st));
         const float* ef_s = reinterpret_cast<const float*>(lay.efrows(st));
         float* lrow = reinterpret_cast<float*>(lay.lrows(st));
+        const uint16_t* ord = reinterpret_cast<const uint16_t*>(lay.order(st));
         const uint32_t* desc = reinterpret_cast<const uint32_t*>(lay.descs(st));
         const uint32_t d0 = wstart[cs][1];
-        // ascending-x compaction: each thread's FP64 sums then see the same
-        // cells in the same order on every run
-        dev::compact_fluid_ordered(reinterpret_cast<const uint32_t*>(lay.masks(st)), nx, flist, wcnt, &nfluid);
         dev::patch_links<L, true>(prow, nx, rs, reinterpret_cast<const T*>(lay.plinks(st)), wstart[cs][0], g0, g1,
                                   desc, d0);
         dev::patch_links<L, false>(lrow, nx, rs, reinterpret_cast<const float*>(lay.llinks(st)), d0, g0, g1, desc,
                                    d0);
-        if (warp0) dev::bulk_wait_read();  // the previous row's bulk stores have read the output rows
-        __syncthreads();  // list complete, bounced values in place, output rows free
-        if (warp0 && ok) {
-            // refill the stage of the previous row (every thread is past its reads of it)
-            const int rn = r + (STAGES - 1) * G;
-            if (rn < R) {
-                const int sn = (it + STAGES - 1) % STAGES;
-                uint32_t n0, n1;
-                range(rn, n0, n1);
-                adj_stage<L, S>(smem_raw + sn * sbytes, lay, &bar[sn], P, lam_in, nbr, gE, Ef, rn, n0, n1,
-                                wstart[sn], p);
-            }
+        dev::bulk_wait_read();  // this thread's bulk stores of the previous row have read their sources
+        // bounced values in place, output rows free; a timeout anywhere in
+        // the block stops the copies
+        ok = __syncthreads_and(ok) != 0;
+        if (issuer && ok && rn < R) {
+            // refill the stage of the previous row (every thread is past its
+            // reads of it and its wait on that stage's barrier)
+            uint32_t n0, n1;
+            range(rn, n0, n1);
+            adj_stage<L, S>(smem_raw + sn * sbytes, lay, &bar[sn], P, lam_in, gE, Ef, rn, n0, n1, wstart[sn], p);
         }
-        const int nf = nfluid;
+        const int nf = ord[0];
         const uint32_t rowbase = (uint32_t)r * (uint32_t)nx;
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            const int x = (int)flist[i];
+            const int x = (int)ord[8 + i];
             if (i < nf) {
                 const uint32_t cell = rowbase + (uint32_t)x;
                 const int xm = x == 0 ? nx - 1 : x - 1;
@@ -597,17 +596,19 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
         }
         dev::fence_proxy_async();
         __syncthreads();  // output rows complete
-        if (threadIdx.x < L::Q) {
-            // lane a of warp 0: the bulk store of direction a, in its own group
-            const int a = threadIdx.x;
-            dev::bulk_store(lam_out + (int64_t)a * p.N + rowbase, outrow + a * rs, (uint32_t)nx * 4u);
-            dev::bulk_commit();
-        } else if (gE && threadIdx.x < L::Q + L::D) {
-            // lanes Q .. Q + D - 1: the row's updated dL/dE back from the stage
-            // (the stage is refilled only after these lanes' reads are done)
-            const int d = threadIdx.x - L::Q;
-            dev::bulk_store(gE + (int64_t)d * p.N + rowbase, ge_s + d * rs, (uint32_t)nx * 8u);
-            dev::bulk_commit();
+        {
+            // lane l of warp w takes piece w + l nw: the Q output rows, then
+            // the row's D updated dL/dE rows back from the stage (which is
+            // refilled only after the issuing threads' reads are done)
+            const int k = warp + lane * nw;
+            if (k < L::Q) {
+                dev::bulk_store(lam_out + (int64_t)k * p.N + rowbase, outrow + k * rs, (uint32_t)nx * 4u);
+                dev::bulk_commit();
+            } else if (gE && k < L::Q + L::D) {
+                const int d = k - L::Q;
+                dev::bulk_store(gE + (int64_t)d * p.N + rowbase, ge_s + d * rs, (uint32_t)nx * 8u);
+                dev::bulk_commit();
+            }
         }
         // link copies of lam_t: slot k of (x, b) takes lam_bbar(x)
         for (uint32_t k = g0 + threadIdx.x; k < g1; k += blockDim.x) {
@@ -615,7 +616,7 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
             lamG_out[k] = outrow[opposite((int)(d >> 24)) * rs + (int)(d & 0xFFFFFFu)];
         }
     }
-    if (warp0) dev::bulk_wait_all();
+    dev::bulk_wait_all();
     block_accumulate(acc, slots, blockIdx.x);
 }
 
@@ -647,20 +648,22 @@ template <class L, class S, int FORCE, bool EF, bool WIN, int RS>
 bool launch_rows_rs(const void* P, const float* lam_in, float* lam_out, const uint32_t* nbr, const float* Ef,
                  const float* w_rho, const float* w_j, double* gE, double* slots, int64_t slot_blocks,
                  const KParams& p, cudaStream_t s) {
-    if ((p.nx * S::kBytes) % 16 != 0 || p.nx % 4 != 0 || p.nx < 32 || p.nx > 32 * kAdjMaxChunks) return false;
+    if (!p.rorder || (p.nx * S::kBytes) % 16 != 0 || p.nx % 4 != 0 || p.nx < 32) return false;
     if (reinterpret_cast<uintptr_t>(gE) % 16 != 0) return false;  // dL/dE rows move by bulk copies
     const int gcapP = dev::window_cap(p.max_row_links, S::kBytes);
     const int gcapL = dev::window_cap(p.max_row_links, 4);
     const int rs = RS ? RS : p.nx;
     const size_t stage =
-        (size_t)AdjLayout<L, S>{p.nx, rs, gcapP, gcapL, gE ? L::D * rs * 8 : 0, EF ? L::D * rs * 4 : 0}.bytes();
-    const size_t smem = kAdjStages * stage + (size_t)L::Q * rs * 4 + 4 * (size_t)p.nx;
+        (size_t)AdjLayout<L, S>{p.nx, rs, p.lorder, gcapP, gcapL, gE ? L::D * rs * 8 : 0, EF ? L::D * rs * 4 : 0}
+            .bytes();
+    const size_t smem = kAdjStages * stage + (size_t)L::Q * rs * 4;
     // the kernel choice and the persistent grid are taken for the layout with
     // dL/dE rows, whether or not this call has them, so that the blocks (and
     // with them the order of the FP64 gradient sums) are the same either way
     const size_t smem_ref =
-        kAdjStages * (size_t)AdjLayout<L, S>{p.nx, rs, gcapP, gcapL, L::D * rs * 8, EF ? L::D * rs * 4 : 0}.bytes() +
-        (size_t)L::Q * rs * 4 + 4 * (size_t)p.nx;
+        kAdjStages *
+            (size_t)AdjLayout<L, S>{p.nx, rs, p.lorder, gcapP, gcapL, L::D * rs * 8, EF ? L::D * rs * 4 : 0}.bytes() +
+        (size_t)L::Q * rs * 4;
     if (smem_ref > kAdjSmemBudget) return false;
     const int threads = p.nx >= kAdjThreads ? kAdjThreads : ((p.nx + 31) / 32) * 32;
     auto kern = k_adjoint_rows<L, S, FORCE, EF, WIN, kAdjStages, RS>;
@@ -688,7 +691,7 @@ bool launch_rows_rs(const void* P, const float* lam_in, float* lam_out, const ui
     const int rows = p.ny * p.nz;
     if (blocks > rows) blocks = rows;
     if (blocks <= 0 || blocks > slot_blocks) return false;
-    kern<<<blocks, threads, smem, s>>>((const typename S::T*)P, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE, slots,
+    kern<<<blocks, threads, smem, s>>>((const typename S::T*)P, lam_in, lam_out, Ef, w_rho, w_j, gE, slots,
                                        gcapP, gcapL, p);
     return true;
 }

@@ -190,6 +190,8 @@ lbm::KParams lbm::make_params(const lbm_ctx* c) {
     p.rowG = c->rowG;
     p.ldesc = c->ldesc;
     p.max_row_links = c->max_row_links;
+    p.rorder = c->rorder;
+    p.lorder = c->lorder;
     p.lgofs = 0;
     p.status = c->status_dev;
     return p;
@@ -284,6 +286,17 @@ lbm_status build_links_and_state(lbm_ctx* c) {
     p.ldesc = c->ldesc;
     c->launches += lbm::launch_build_link_desc(c->lat.vel, c->nbr, c->lbase, c->ldesc, p, c->stream);
     LBM_CUDA(c, cudaGetLastError());
+    // per-row cell order of the row-staged kernels (entries are 16-bit x)
+    if (!c->rorder && c->nx <= 65535) {
+        c->lorder = 8 + (int)((c->nx + 7) / 8) * 8;
+        LBM_CUDA(c, cudaMalloc((void**)&c->rorder, sizeof(uint16_t) * (size_t)R * (size_t)c->lorder));
+        p.lorder = c->lorder;
+    }
+    if (c->rorder) {
+        p.rorder = c->rorder;
+        c->launches += lbm::launch_build_row_order(c->nbr, c->rorder, p, c->stream);
+        LBM_CUDA(c, cudaGetLastError());
+    }
     const size_t eb = pop_elem_bytes(c->storage);
     const size_t pbytes = (size_t)c->Q * (size_t)c->N * eb;
     c->gofs = (pbytes + 255) & ~(size_t)255;
@@ -466,6 +479,7 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->lbase);
     cudaFree(c->rowG);
     cudaFree(c->ldesc);
+    cudaFree(c->rorder);
     cudaFree(c->mask_dev);
     cudaFree(c->Efield);
     cudaFree(c->partials);

@@ -96,17 +96,6 @@ __device__ __forceinline__ void pull(const typename S::T* __restrict__ P, const 
     }
 }
 
-// 16-byte asynchronous global -> shared copies (cp.async, L2 only).
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 // e_ay + 1 and e_az + 1 of every direction, 2 bits each, in two 64-bit words
 // (19 directions need 38 bits per word); the unrolled loops fold to constants.
 template <class L>
@@ -132,59 +121,6 @@ __device__ __forceinline__ unsigned long long packed_x() {
     return v;
 }
 
-// Compacts a staged row (link masks mrow[0..nx)) into flist: fluid cells from
-// the front, solid cells from the back, so that warps taking consecutive
-// entries mostly see one kind.  counts[0..1] must be zero on entry and
-// receive the numbers of fluid and solid cells; the caller synchronises the
-// block before reading them.  blockDim.x must be a multiple of 32.
-__device__ __forceinline__ void compact_fluid(const uint32_t* mrow, int nx, uint32_t* flist, int* counts) {
-    const unsigned lane = threadIdx.x & 31u, below = (1u << lane) - 1u;
-    for (int x0 = 0; x0 < nx; x0 += blockDim.x) {
-        const int x = x0 + (int)threadIdx.x;
-        const bool in = x < nx;
-        const bool fluid = in && !(mrow[x] & kSolidBit);
-        const unsigned bf = __ballot_sync(0xffffffffu, fluid), bs = __ballot_sync(0xffffffffu, in && !fluid);
-        int base_f = 0, base_s = 0;
-        if (lane == 0) {
-            if (bf) base_f = atomicAdd(&counts[0], __popc(bf));
-            if (bs) base_s = atomicAdd(&counts[1], __popc(bs));
-        }
-        base_f = __shfl_sync(0xffffffffu, base_f, 0);
-        base_s = __shfl_sync(0xffffffffu, base_s, 0);
-        if (fluid) flist[base_f + __popc(bf & below)] = (uint32_t)x;
-        if (in && !fluid) flist[nx - 1 - (base_s + __popc(bs & below))] = (uint32_t)x;
-    }
-}
-
-// As compact_fluid, but in ascending x within each kind, so the list (and any
-// per-thread accumulation over it) is the same on every run.  wcnt holds
-// ceil(nx / 32) ints; the fluid count goes to *nfluid.  Contains one block
-// barrier; the caller synchronises again before reading *nfluid.
-__device__ __forceinline__ void compact_fluid_ordered(const uint32_t* mrow, int nx, uint32_t* flist, int* wcnt,
-                                                      int* nfluid) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const unsigned below = (1u << lane) - 1u;
-    const int nch = (nx + 31) >> 5;
-    for (int c = warp; c < nch; c += nw) {
-        const int x = c * 32 + lane;
-        const unsigned b = __ballot_sync(0xffffffffu, x < nx && !(mrow[x] & kSolidBit));
-        if (lane == 0) wcnt[c] = __popc(b);
-    }
-    __syncthreads();
-    for (int c = warp; c < nch; c += nw) {
-        int before = 0;
-        for (int k = lane; k < c; k += 32) before += wcnt[k];
-        before = __reduce_add_sync(0xffffffffu, before);  // fluid cells with x < 32 c
-        const int x = c * 32 + lane;
-        const bool in = x < nx;
-        const bool fluid = in && !(mrow[x] & kSolidBit);
-        const unsigned bf = __ballot_sync(0xffffffffu, fluid), bs = __ballot_sync(0xffffffffu, in && !fluid);
-        if (fluid) flist[before + __popc(bf & below)] = (uint32_t)x;
-        if (in && !fluid) flist[nx - 1 - ((c * 32 - before) + __popc(bs & below))] = (uint32_t)x;
-        if (c == nch - 1 && lane == 0) *nfluid = before + __popc(bf);
-    }
-}
-
 // Bounce-back patch of a staged row set.  Link k of the row is a fluid cell x
 // with an outgoing direction b into a solid cell, descriptor x | b << 24.  The
 // solid neighbour x + e_b is read by exactly one cell of the row for each
@@ -205,19 +141,6 @@ __device__ __forceinline__ void patch_links(T* rows, int nx, int rs, const T* wi
         xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
         rows[(PULL ? opposite(b) : b) * rs + xs] = win[k - w0];
     }
-}
-
-// Stages elements [g0, g1) of an array of `esize`-byte elements as a 16-byte
-// aligned window (cp.async); the window's first element index goes to *start
-// (written by thread 0).  The window spans at most
-// round_up16((g1 - g0) * esize) + 16 bytes.
-__device__ __forceinline__ void stage_window(unsigned char* dst, const unsigned char* base, int esize, uint32_t g0,
-                                             uint32_t g1, uint32_t* start) {
-    const uint64_t b0 = ((uint64_t)g0 * esize) & ~15ull;
-    const uint64_t b1 = ((uint64_t)g1 * esize + 15ull) & ~15ull;
-    for (int k = threadIdx.x; k < (int)((b1 - b0) >> 4); k += blockDim.x)
-        cp_async16(dst + 16 * k, base + b0 + 16 * (uint64_t)k);
-    if (threadIdx.x == 0) *start = (uint32_t)(b0 / esize);
 }
 
 // Bytes reserved for a staged window of up to n elements of esize bytes.

@@ -163,6 +163,12 @@ struct KParams {
     // its outgoing direction b (the row-staged kernels' link passes)
     const uint32_t* ldesc;
     int max_row_links;
+    // per row, the cells in the order the row-staged kernels give them to
+    // threads: entry 0 the number of fluid cells nf, entries 1..7 zero, then
+    // the fluid x ascending and the solid x ascending (lorder entries per row,
+    // a multiple of 8; null when nx > 65535)
+    const uint16_t* rorder;
+    int lorder;
     // byte offset of the link buffer inside an adjoint field (reverse sweep)
     uint64_t lgofs;
     // host-mapped status word: a kernel whose bounded wait ran out writes a
@@ -182,6 +188,8 @@ int launch_build_neighbors(int vel, const uint8_t* mask, uint32_t* nbr, unsigned
 // Bounded-wait probe (writes code 3 into *status when its wait runs out).
 int launch_wait_probe(int* status, long long limit, cudaStream_t s);
 // Per-link descriptors ldesc[k] = x | b << 24 (needs lbase).
+// Per-row cell order (fluid cells first) for the row-staged kernels.
+int launch_build_row_order(const uint32_t* nbr, uint16_t* rorder, const KParams& p, cudaStream_t s);
 int launch_build_link_desc(int vel, const uint32_t* nbr, const uint32_t* lbase, uint32_t* ldesc, const KParams& p,
                            cudaStream_t s);
 int launch_build_links(int vel, const uint32_t* nbr, uint32_t* lbase, uint32_t* rowG, void* temp,
@@ -265,6 +273,8 @@ struct lbm_ctx {
     uint32_t* lbase = nullptr;     // per-cell first slot in the link buffer
     uint32_t* rowG = nullptr;      // per-row first slot (ny * nz + 1)
     uint32_t* ldesc = nullptr;     // per link slot: x | b << 24
+    uint16_t* rorder = nullptr;    // per row: fluid count, then fluid x, then solid x (lorder entries)
+    int lorder = 0;
     int64_t n_links = 0;           // outgoing links into solid cells
     int max_row_links = 0;
     size_t state_bytes = 0;        // populations + link buffer

@@ -13,6 +13,7 @@
 // among x's outgoing links), so the links of one row form a contiguous range
 // rowG[r] .. rowG[r+1].  The collision stores f*_b(x) there, and the next
 // step reads it back as f_bbar(x).
+#include <algorithm>
 #include <cstdio>
 
 #include <cub/device/device_scan.cuh>
@@ -125,6 +126,40 @@ __global__ void __launch_bounds__(kBlock) k_link_desc(const uint32_t* __restrict
 #pragma unroll
     for (int b = 1; b < L::Q; ++b)
         if ((o >> b) & 1u) ldesc[link_slot(base, o, b)] = (uint32_t)c.x | ((uint32_t)b << 24);
+}
+
+// Cell order of each row for the row-staged kernels: entry 0 the number of
+// fluid cells nf, entries 1..7 zero, entries 8 .. 8 + nf - 1 the fluid x
+// ascending, then the solid x ascending, then zeros up to lorder.  One warp
+// per row.
+__global__ void __launch_bounds__(kBlock) k_row_order(const uint32_t* __restrict__ nbr, uint16_t* __restrict__ ord,
+                                                      KParams p) {
+    const int64_t R = (int64_t)p.ny * p.nz;
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < R; r += nwarps) {
+        const uint32_t* m = nbr + r * p.nx;
+        uint16_t* o = ord + r * p.lorder;
+        int nf = 0;
+        for (int x0 = 0; x0 < p.nx; x0 += 32) {
+            const int x = x0 + lane;
+            nf += __popc(__ballot_sync(0xffffffffu, x < p.nx && !(m[x] & kSolidBit)));
+        }
+        int nfl = 0, nso = nf;  // entries written so far: fluid, and nf + solid
+        for (int x0 = 0; x0 < p.nx; x0 += 32) {
+            const int x = x0 + lane;
+            const bool in = x < p.nx;
+            const bool fluid = in && !(m[x] & kSolidBit);
+            const unsigned bf = __ballot_sync(0xffffffffu, fluid), bs = __ballot_sync(0xffffffffu, in && !fluid);
+            if (fluid) o[8 + nfl + __popc(bf & below)] = (uint16_t)x;
+            if (in && !fluid) o[8 + nso + __popc(bs & below)] = (uint16_t)x;
+            nfl += __popc(bf);
+            nso += __popc(bs);
+        }
+        if (lane < 8) o[lane] = lane == 0 ? (uint16_t)nf : (uint16_t)0;
+        for (int k = 8 + p.nx + lane; k < p.lorder; k += 32) o[k] = 0;
+    }
 }
 
 template <class L>
@@ -344,6 +379,13 @@ __global__ void k_wait_probe(int* status, long long limit) {
 
 int launch_wait_probe(int* status, long long limit, cudaStream_t s) {
     k_wait_probe<<<1, 32, 0, s>>>(status, limit);
+    return 1;
+}
+
+int launch_build_row_order(const uint32_t* nbr, uint16_t* rorder, const KParams& p, cudaStream_t s) {
+    const int64_t R = (int64_t)p.ny * p.nz;
+    const int64_t blocks = std::min<int64_t>((R * 32 + kBlock - 1) / kBlock, 65535);
+    k_row_order<<<(unsigned)blocks, kBlock, 0, s>>>(nbr, rorder, p);
     return 1;
 }
 

@@ -403,66 +403,74 @@ __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict
 // Row-staged step kernel (used when a whole x-row of one direction is a
 // whole number of 16-byte chunks and the stages fit shared memory).  A
 // persistent block walks rows r = blockIdx.x, blockIdx.x + gridDim.x, ...:
-//  - the Q source rows P_a(y - e_ay, z - e_az, :) of the row, its link masks
+//  - the Q source rows P_a(y - e_ay, z - e_az, :) of the row, its cell order
 //    and its ranges of the link buffer and of the link descriptors arrive by
-//    bulk asynchronous copies (one thread issues one copy per contiguous
-//    piece, completing on the stage's mbarrier) into a ring of STAGES stages,
-//    STAGES - 1 rows ahead of the row being computed;
+//    bulk asynchronous copies into a ring of STAGES stages, STAGES - 1 rows
+//    ahead of the row being computed.  One thread, lane 0 of the last warp,
+//    arms the stage's mbarrier with the byte count and issues the copies.  A
+//    bulk copy holds its issuing thread for many cycles, so the issuer is the
+//    warp with the least cell work (the order puts the solid cells, and the
+//    cells of a second pass, on the first warps);
 //  - one pass over the row's links writes each bounced value f*_b(x) into the
 //    staged slot that the pull of direction bbar at x reads (the slot of the
 //    solid neighbour), so the cells pull without link logic;
-//  - the row's fluid cells are compacted into a list, so the collision runs on
-//    full warps; solid cells only write zeros;
+//  - thread i takes the i-th cell of the row's order (the fluid cells first,
+//    fixed by the geometry), so the collision runs on full warps; solid cells
+//    only write zeros;
 //  - f_a(x) is read from the ring at x - e_ax (periodic wrap in x is a
 //    shared-memory index); results go into a shared-memory output row set
-//    that leaves by bulk stores (one per direction);
+//    that leaves by bulk stores (one per direction, spread over the warps,
+//    lane l of warp w storing direction w + l nw);
 //  - one pass over the row's links copies the outgoing values f*_b(x) from
 //    the output rows into the row's contiguous range of the link buffer.
 // Two block barriers per row; a stage is refilled after the first barrier of
 // the row that follows its own.  Every wait on an mbarrier is bounded; one that
-// runs out writes a code to p.status and the kernel carries on (its results
-// are then invalid, but it ends and no access leaves its buffers).
+// runs out writes a code to p.status, the block stops issuing copies, and the
+// kernel carries on (its results are then invalid, but it ends and no access
+// leaves its buffers).
 // ---------------------------------------------------------------------------
 
-// Shared-memory layout of one stage: Q source rows (Q nx elements), the row's
-// link masks (nx words), its range of the link buffer (gcap bytes) and of
-// the link descriptors (dcap bytes), both as 16-byte aligned windows.
+// Shared-memory layout of one stage: Q source rows (stride rs elements), the
+// row's cell order (lorder 16-bit entries), its range of the link buffer
+// (gcap bytes) and of the link descriptors (dcap bytes), both as 16-byte
+// aligned windows.
 template <class L, class S>
 struct StageLayout {
-    int nx, rs, gcap, dcap;  // row length, shared-memory row stride (elements)
-    __device__ __forceinline__ int bytes() const { return L::Q * rs * S::kBytes + 4 * nx + gcap + dcap; }
+    int nx, rs, lorder, gcap, dcap;  // row length, shared-memory row stride (elements), order entries
+    __device__ __forceinline__ int rows_bytes() const { return L::Q * rs * S::kBytes; }
+    __device__ __forceinline__ int bytes() const { return rows_bytes() + 2 * lorder + gcap + dcap; }
     __device__ __forceinline__ typename S::T* rows(unsigned char* st) const {
         return reinterpret_cast<typename S::T*>(st);
     }
-    __device__ __forceinline__ uint32_t* masks(unsigned char* st) const {
-        return reinterpret_cast<uint32_t*>(st + L::Q * rs * S::kBytes);
+    __device__ __forceinline__ uint16_t* order(unsigned char* st) const {
+        return reinterpret_cast<uint16_t*>(st + rows_bytes());
     }
     __device__ __forceinline__ typename S::T* links(unsigned char* st) const {
-        return reinterpret_cast<typename S::T*>(st + L::Q * rs * S::kBytes + 4 * nx);
+        return reinterpret_cast<typename S::T*>(st + rows_bytes() + 2 * lorder);
     }
     __device__ __forceinline__ uint32_t* descs(unsigned char* st) const {
-        return reinterpret_cast<uint32_t*>(st + L::Q * rs * S::kBytes + 4 * nx + gcap);
+        return reinterpret_cast<uint32_t*>(st + rows_bytes() + 2 * lorder + gcap);
     }
 };
 
-// Issued by one thread (lane 0 of warp 0; the other lanes return): the bulk
-// copies of row `row` into stage `st`, all completing on `bar`.  The window
-// starts go to *gstart and *dstart before the barrier is armed, so the arrive
-// releases them to the waiting threads.  (Spreading the copies over the
-// lanes of warp 0 measured slower.)
+// One thread: arms a stage's mbarrier with the byte count of row `row`
+// (links [g0, g1)), records the first elements of its two windows, and issues
+// the row's copies into stage st, all completing on bar: the Q source rows,
+// the cell order, the link window and the descriptor window.  The window
+// starts are written before the barrier is armed, so the arrive releases them
+// to the waiting threads.
 template <class L, class S>
 __device__ __forceinline__ void stage_row(unsigned char* st, const StageLayout<L, S>& lay, uint64_t* bar,
-                                          const typename S::T* __restrict__ Pin, const uint32_t* __restrict__ nbr,
-                                          int row, uint32_t g0, uint32_t g1, uint32_t* gstart, uint32_t* dstart,
-                                          const KParams& p) {
-    if ((threadIdx.x & 31) != 0) return;
+                                          const typename S::T* __restrict__ Pin, int row, uint32_t g0, uint32_t g1,
+                                          uint32_t* gstart, uint32_t* dstart, const KParams& p) {
     const uint32_t row_bytes = (uint32_t)p.nx * S::kBytes;
     uint64_t gb0, gb1, db0, db1;
     dev::window_bytes(g0, g1, S::kBytes, gb0, gb1);
     dev::window_bytes(g0, g1, 4, db0, db1);
     *gstart = (uint32_t)(gb0 / S::kBytes);
     *dstart = (uint32_t)(db0 / 4);
-    dev::mbar_expect_tx(bar, L::Q * row_bytes + 4u * (uint32_t)p.nx + (uint32_t)(gb1 - gb0) + (uint32_t)(db1 - db0));
+    dev::mbar_expect_tx(bar, L::Q * row_bytes + 2u * (uint32_t)lay.lorder + (uint32_t)(gb1 - gb0) +
+                                 (uint32_t)(db1 - db0));
     const int y = row % p.ny, z = row / p.ny;
     const int yp = y == p.ny - 1 ? 0 : y + 1, ym = y == 0 ? p.ny - 1 : y - 1;
     const int zp = z == p.nz - 1 ? 0 : z + 1, zm = z == 0 ? p.nz - 1 : z - 1;
@@ -474,7 +482,7 @@ __device__ __forceinline__ void stage_row(unsigned char* st, const StageLayout<L
         dev::bulk_load(lay.rows(st) + a * lay.rs, Pin + (int64_t)a * p.N + ((int64_t)zs * p.ny + ys) * p.nx, row_bytes,
                        bar);
     }
-    dev::bulk_load(lay.masks(st), nbr + (int64_t)row * p.nx, 4u * (uint32_t)p.nx, bar);
+    dev::bulk_load(lay.order(st), p.rorder + (int64_t)row * lay.lorder, 2u * (uint32_t)lay.lorder, bar);
     if (gb1 > gb0)
         dev::bulk_load(lay.links(st), reinterpret_cast<const unsigned char*>(Pin) + p.gofs + gb0,
                        (uint32_t)(gb1 - gb0), bar);
@@ -485,25 +493,24 @@ __device__ __forceinline__ void stage_row(unsigned char* st, const StageLayout<L
 
 template <class L, class S, int FORCE, bool EF, bool SR, int STAGES, int RS>
 __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restrict__ Pin,
-                                                   typename S::T* __restrict__ Pout, const uint32_t* __restrict__ nbr,
-                                                   const float* __restrict__ Ef, int gcap, int dcap, KParams p) {
+                                                   typename S::T* __restrict__ Pout, const float* __restrict__ Ef,
+                                                   int gcap, int dcap, KParams p) {
     using T = typename S::T;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int nx = p.nx;
     const int rs = RS ? RS : nx;  // shared-memory row stride: a constant for the common row lengths
-    const StageLayout<L, S> lay{nx, rs, gcap, dcap};
+    const StageLayout<L, S> lay{nx, rs, p.lorder, gcap, dcap};
     const int sbytes = lay.bytes();
     T* outrow = reinterpret_cast<T*>(smem_raw + STAGES * sbytes);
-    uint32_t* flist = reinterpret_cast<uint32_t*>(outrow + L::Q * rs);  // fluid x from the front, solid from the back
     __shared__ __align__(8) uint64_t bar[STAGES];
-    __shared__ int counts[2][2];  // [row parity][fluid, solid]
     __shared__ uint32_t gstart[STAGES], dstart[STAGES];
     T* Gout = reinterpret_cast<T*>(reinterpret_cast<char*>(Pout) + p.gofs);
     const uint32_t row_bytes = (uint32_t)nx * S::kBytes;
     const int R = p.ny * p.nz;
     const int G = gridDim.x;
     const bool leader = threadIdx.x == 0;
-    const bool warp0 = threadIdx.x < 32;
+    const int warp = (int)(threadIdx.x >> 5), nw = (int)(blockDim.x >> 5), lane = (int)(threadIdx.x & 31);
+    const bool issuer = (int)threadIdx.x == (int)blockDim.x - 32;  // lane 0 of the last warp
     auto range = [&](int row, uint32_t& g0, uint32_t& g1) {
         g0 = g1 = 0u;
         if (row < R) {
@@ -512,27 +519,28 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
         }
     };
     if (leader) {
-        counts[0][0] = counts[0][1] = counts[1][0] = counts[1][1] = 0;
 #pragma unroll
         for (int k = 0; k < STAGES; ++k) dev::mbar_init(&bar[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
-    if (warp0) {
+    if (issuer) {
 #pragma unroll
         for (int k = 0; k < STAGES - 1; ++k) {
             const int rk = blockIdx.x + k * G;
             if (rk < R) {
                 uint32_t g0, g1;
                 range(rk, g0, g1);
-                stage_row<L, S>(smem_raw + k * sbytes, lay, &bar[k], Pin, nbr, rk, g0, g1, &gstart[k], &dstart[k], p);
+                stage_row<L, S>(smem_raw + k * sbytes, lay, &bar[k], Pin, rk, g0, g1, &gstart[k], &dstart[k], p);
             }
         }
     }
     int it = 0;
-    bool ok = true;  // false once a wait has run out: no further waits
+    bool ok = true;  // false once a wait has run out (the same in every thread after the first barrier)
     for (int r = blockIdx.x; r < R; r += G, ++it) {
         const int cs = it % STAGES;
+        const int rn = r + (STAGES - 1) * G;       // the row refilled during this one ...
+        const int sn = (it + STAGES - 1) % STAGES;  // ... into the stage of the previous row
         uint32_t g0, g1;  // this row's links
         range(r, g0, g1);
         if (ok && !dev::mbar_wait(&bar[cs], (uint32_t)(it / STAGES) & 1u)) {
@@ -542,30 +550,26 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
         }
         unsigned char* st = smem_raw + cs * sbytes;
         T* buf = lay.rows(st);
+        const uint16_t* ord = lay.order(st);
         const uint32_t* desc = lay.descs(st);
         const uint32_t d0 = dstart[cs];
-        int* cnt = counts[it & 1];
-        dev::compact_fluid(lay.masks(st), nx, flist, cnt);
         dev::patch_links<L, true>(buf, nx, rs, lay.links(st), gstart[cs], g0, g1, desc, d0);
-        if (warp0) dev::bulk_wait_read();  // the previous row's bulk stores have read the output rows
-        if (leader) counts[(it + 1) & 1][0] = counts[(it + 1) & 1][1] = 0;
-        __syncthreads();  // list complete, bounced values in place, output rows free
-        if (warp0 && ok) {
+        dev::bulk_wait_read();  // this thread's bulk stores of the previous row have read the output rows
+        // bounced values in place, output rows free; a timeout anywhere in
+        // the block stops the copies
+        ok = __syncthreads_and(ok) != 0;
+        if (issuer && ok && rn < R) {
             // refill the stage of the previous row: every thread is past its
-            // last reads of it (the link pass that follows the output)
-            const int rn = r + (STAGES - 1) * G;
-            if (rn < R) {
-                const int sn = (it + STAGES - 1) % STAGES;
-                uint32_t n0, n1;
-                range(rn, n0, n1);
-                stage_row<L, S>(smem_raw + sn * sbytes, lay, &bar[sn], Pin, nbr, rn, n0, n1, &gstart[sn], &dstart[sn],
-                                p);
-            }
+            // last reads of it (the link pass that follows the output) and
+            // its wait on that stage's barrier
+            uint32_t n0, n1;
+            range(rn, n0, n1);
+            stage_row<L, S>(smem_raw + sn * sbytes, lay, &bar[sn], Pin, rn, n0, n1, &gstart[sn], &dstart[sn], p);
         }
-        const int nf = cnt[0];
+        const int nf = ord[0];
         const uint32_t rowbase = (uint32_t)r * (uint32_t)nx;
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            const int x = (int)flist[i];
+            const int x = (int)ord[8 + i];
             if (i < nf) {
                 const uint32_t cell = rowbase + (uint32_t)x;
                 const int xm = x == 0 ? nx - 1 : x - 1;
@@ -618,11 +622,13 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
         }
         dev::fence_proxy_async();  // this thread's shared-memory writes before the bulk copies
         __syncthreads();           // output rows complete; the stage is free for its refill
-        if (threadIdx.x < L::Q) {
-            // lane a of warp 0: the bulk store of direction a, in its own group
-            const int a = threadIdx.x;
-            dev::bulk_store(Pout + (int64_t)a * p.N + rowbase, outrow + a * rs, row_bytes);
-            dev::bulk_commit();
+        {
+            // lane l of warp w stores direction w + l nw, each in its own bulk group
+            const int a = warp + lane * nw;
+            if (a < L::Q) {
+                dev::bulk_store(Pout + (int64_t)a * p.N + rowbase, outrow + a * rs, row_bytes);
+                dev::bulk_commit();
+            }
         }
         // outgoing links: slot k of (x, b) takes f*_b(x)
         for (uint32_t k = g0 + threadIdx.x; k < g1; k += blockDim.x) {
@@ -630,7 +636,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
             Gout[k] = outrow[(int)(d >> 24) * rs + (int)(d & 0xFFFFFFu)];
         }
     }
-    if (warp0) dev::bulk_wait_all();
+    dev::bulk_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -648,7 +654,7 @@ constexpr size_t kSmemBudget = 160 * 1024;
 // whole rows, so any multiple of 32 threads up to the row length works; the
 // choice is the one with the most co-resident blocks per SM (occupancy API),
 // the larger block on a tie: more rows in flight per SM hide the per-row
-// copy latency (256-cell FP16 rows: 160 threads give six blocks per SM,
+// copy latency (256-cell FP16 rows: 160 threads gave six blocks per SM and
 // 0.367 ms per 256^3 step, against four blocks and 0.395 ms at 256).
 struct Shape {
     int threads, blocks;
@@ -694,15 +700,15 @@ bool launch_rows(const S*, const void* fin, void* fout, const uint32_t* nbr, con
     const size_t row_bytes = (size_t)p.nx * S::kBytes, srow = (size_t)rs * S::kBytes;
     const int gcap = dev::window_cap(p.max_row_links, S::kBytes);
     const int dcap = dev::window_cap(p.max_row_links, 4);
-    const size_t stage_bytes = (size_t)L::Q * srow + 4 * (size_t)p.nx + gcap + dcap;
-    const size_t smem = (size_t)kStages * stage_bytes + (size_t)L::Q * srow + 4 * (size_t)p.nx;
-    if (row_bytes % 16 != 0 || smem > kSmemBudget || p.nx < 32 || p.nx % 4 != 0) return false;
+    const size_t stage_bytes = (size_t)L::Q * srow + 2 * (size_t)p.lorder + gcap + dcap;
+    const size_t smem = (size_t)kStages * stage_bytes + (size_t)L::Q * srow;
+    if (!p.rorder || row_bytes % 16 != 0 || smem > kSmemBudget || p.nx < 32 || p.nx % 4 != 0) return false;
     auto kern = k_step_rows<L, S, FORCE, EF, SR, kStages, RS>;
     const Shape sh = launch_shape(kern, p.nx, smem);
     const int threads = sh.threads, blocks = sh.blocks;
     if (blocks <= 0) return false;
     const int rows = p.ny * p.nz;
-    kern<<<blocks < rows ? blocks : rows, threads, smem, s>>>((const T*)fin, (T*)fout, nbr, Ef, gcap, dcap, p);
+    kern<<<blocks < rows ? blocks : rows, threads, smem, s>>>((const T*)fin, (T*)fout, Ef, gcap, dcap, p);
     return true;
 }
 
