@@ -241,7 +241,8 @@ lbm_status lbm_selftest_wait_timeout(lbm_ctx* ctx, int64_t clocks);
  *             With a uniform E, sum_x dL/dE(x) is the uniform-field gradient.
  *   dL_dB   : 3 host doubles, dL/dB (2D: only the z component), or NULL.
  *   dL_dtau : host double, or NULL.   loss : host double (L itself), or NULL.
- *   dL_df0  : [Q * N] FP32 device, dL/df_0 (population layout), or NULL.
+ *   dL_df0  : [Q * N] FP32 device, dL/df_0 (population-major, [a * N + cell], as
+ *             lbm_get_populations), or NULL.
  * Device memory: the schedule's states (populations + bounce-back link
  * buffer each) plus two FP32 adjoint fields (Q N values + one per bounce-back
  * link each).  The context keeps these buffers after the call and reuses
@@ -260,8 +261,9 @@ lbm_status lbm_adjoint(lbm_ctx* ctx, const float* w_rho, const float* w_j, int64
  * Host only; needs no device.  Errors: INVALID_ARG. */
 lbm_status lbm_weight_integrals(int D, int stat, double theta, double mu, double I[5]);
 
-/* Serialise / restore the state (raw stored populations plus a header with
- * lattice, dims, storage, step count and a checksum) to / from host memory.
+/* Serialise / restore the state (raw stored populations, in the library's
+ * internal layout, plus a header with lattice, dims, storage, step count and a
+ * checksum) to / from host memory.
  * lbm_save_state with host_buf == NULL only reports the size in *used.
  * lbm_load_state checks the header against the context.
  * Errors: INVALID_ARG (short buffer, header mismatch, bad checksum), CUDA. */

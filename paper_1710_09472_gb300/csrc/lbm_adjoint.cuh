@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_seed(const typename S::T* __
         const uint32_t m = nbr[c.cell];
         if (m & kSolidBit) {
 #pragma unroll
-            for (int a = 0; a < L::Q; ++a) lam[(int64_t)a * p.N + c.cell] = 0.f;
+            for (int a = 0; a < L::Q; ++a) lam[dev::pop_at<L>(p, c, a, 0)] = 0.f;
         } else {
             float wr = 0.f, wj[3] = {0.f, 0.f, 0.f};
             if (in_window) {
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_seed(const typename S::T* __
 #pragma unroll
             for (int a = 0; a < L::Q; ++a) {
                 lm[a] = wr + edot<L>(a, wj);
-                lam[(int64_t)a * p.N + c.cell] = lm[a];
+                lam[dev::pop_at<L>(p, c, a, 0)] = lm[a];
             }
             const uint32_t o = outgoing<L::Q>(m);
             if (o) store_lam_links<L>(link_part(lam, p), o, __ldg(p.lbase + c.cell), lm);
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(
         const uint32_t m = __ldg(nbr + c.cell);
         if (m & kSolidBit) {
 #pragma unroll
-            for (int a = 0; a < L::Q; ++a) lam_out[(int64_t)a * p.N + c.cell] = 0.f;
+            for (int a = 0; a < L::Q; ++a) lam_out[dev::pop_at<L>(p, c, a, 0)] = 0.f;
         } else {
             // f_t(y): pull of the stored state; lamt(y): gather from downstream
             float h[L::Q], lt[L::Q];
@@ -353,14 +353,14 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(
                 if (a != 0 && ((o >> a) & 1u))
                     lt[a] = __ldg(lamG_in + link_slot(lb, o, a));
                 else
-                    lt[a] = __ldg(lam_in + (int64_t)a * p.N + (a == 0 ? c.cell : dev::shifted<L>(c, a, +1)));
+                    lt[a] = __ldg(lam_in + dev::pop_at<L>(p, c, a, +1));
             }
             float E[3], wr, wj[3], lam[L::Q], gEc[3];
             load_E<L, EF>(Ef, p, c.cell, E);
             load_weights<L, WIN>(w_rho, w_j, p, c.cell, wr, wj);
             adjoint_cell<L, FORCE, WIN>(h, lt, E, p, wr, wj, lam, gEc, acc);
 #pragma unroll
-            for (int b = 0; b < L::Q; ++b) lam_out[(int64_t)b * p.N + c.cell] = lam[b];
+            for (int b = 0; b < L::Q; ++b) lam_out[dev::pop_at<L>(p, c, b, 0)] = lam[b];
             if (o) store_lam_links<L>(link_part(lam_out, p), o, lb, lam);
             if (gE) {
 #pragma unroll
@@ -376,12 +376,13 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(
 // One stage holds, for the row (y, z):
 //   - with dL/dE, the row's D rows of it (FP64, accumulated in place and
 //     stored back after the row); with a per-cell field, its D rows of E;
-//   - the Q pull rows of the forward state P_t: direction a from row
-//     (y - e_ay, z - e_az), read at x - e_ax;
+//   - the Q pull rows of the forward state P_t in slot order: direction a
+//     from row (y - e_ay, z - e_az), read at x - e_ax (one copy per
+//     neighbouring row: its block of consecutive slots);
 //   - the row's cell order (fluid cells first, ascending x);
 //   - its window of P_t's link buffer (bounced pulls);
-//   - the Q gather rows of lam_{t+1}: direction a from row
-//     (y + e_ay, z + e_az), read at x + e_ax;
+//   - the Q gather rows of lam_{t+1} in slot order: direction a from row
+//     (y + e_ay, z + e_az), read at x + e_ax (again one copy per row);
 //   - its windows of lam_{t+1}'s link buffer (bounced gathers) and of the
 //     link descriptors;
 // all by bulk asynchronous copies, completing on the stage's mbarrier, armed
@@ -392,8 +393,9 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(
 // without link logic.  Thread i takes the i-th cell of the row's order, so
 // each thread's FP64 sums see the same cells in the same order on every run.
 // lam_t goes through shared-memory output rows (zeros for solid cells) that
-// leave by bulk stores, and one pass over the links copies lam_bbar(x) into
-// the row's range of the new link buffer.  dL/dB, dL/dtau and the loss stay
+// leave by one bulk store (lam has the populations' slot layout), and one
+// pass over the links copies lam_bbar(x) into the row's range of the new
+// link buffer.  dL/dB, dL/dtau and the loss stay
 // in registers until the block's single reduction at the end.
 // ---------------------------------------------------------------------------
 template <class L, class S>
@@ -442,13 +444,17 @@ __device__ __forceinline__ void adj_stage(unsigned char* st, const AdjLayout<L, 
     unsigned char* pr = lay.prows(st);
     unsigned char* lr = lay.lrows(st);
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) {
-        const int ey = L::c(a, 1), ez = L::c(a, 2);
-        // pull row (y - e_ay, z - e_az) of P_t, gather row (y + e_ay, z + e_az) of lam_{t+1}
+    for (int k = 0; k < 9; ++k) {
+        if (key_count<L>(k) == 0) continue;
+        // the slots key_first(k) .. of the directions with (e_y, e_z): from pull
+        // row (y - e_y, z - e_z) of P_t and gather row (y + e_y, z + e_z) of lam_{t+1}
+        const int ey = k / 3 - 1, ez = k % 3 - 1, s0 = key_first<L>(k), n = key_count<L>(k);
         const int ysP = ey > 0 ? ym : (ey < 0 ? yp : y), zsP = ez > 0 ? zm : (ez < 0 ? zp : z);
         const int ysL = ey > 0 ? yp : (ey < 0 ? ym : y), zsL = ez > 0 ? zp : (ez < 0 ? zm : z);
-        dev::bulk_load(pr + a * rs * S::kBytes, P + (int64_t)a * p.N + ((int64_t)zsP * p.ny + ysP) * p.nx, prb, bar);
-        dev::bulk_load(lr + a * rs * 4, lam + (int64_t)a * p.N + ((int64_t)zsL * p.ny + ysL) * p.nx, lrb, bar);
+        dev::bulk_load(pr + s0 * rs * S::kBytes, P + ((int64_t)(zsP * p.ny + ysP) * L::Q + s0) * p.nx,
+                       (uint32_t)n * prb, bar);
+        dev::bulk_load(lr + s0 * rs * 4, lam + ((int64_t)(zsL * p.ny + ysL) * L::Q + s0) * p.nx, (uint32_t)n * lrb,
+                       bar);
     }
     dev::bulk_load(lay.order(st), p.rorder + (int64_t)row * lay.lorder, 2u * (uint32_t)lay.lorder, bar);
     if (pb1 > pb0)
@@ -485,7 +491,7 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
     using T = typename S::T;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int nx = p.nx;
-    const int rs = RS ? RS : nx;  // shared-memory row stride: a constant for the common row lengths
+    const int rs = RS ? RS : nx;  // shared-memory row stride (= nx): a constant for the common row lengths
     const AdjLayout<L, S> lay{nx, rs, p.lorder, gcapP, gcapL, gE ? L::D * rs * 8 : 0, EF ? L::D * rs * 4 : 0};
     const int sbytes = lay.bytes();
     float* outrow = reinterpret_cast<float*>(smem_raw + STAGES * sbytes);
@@ -570,8 +576,8 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
 #pragma unroll
                 for (int a = 0; a < L::Q; ++a) {
                     const int ex = L::c(a, 0);
-                    h[a] = S::cvt(prow[a * rs + (ex > 0 ? xm : (ex < 0 ? xp : x))]) * p.inv_scale;
-                    lt[a] = lrow[a * rs + (ex > 0 ? xp : (ex < 0 ? xm : x))];
+                    h[a] = S::cvt(prow[pop_slot<L>(a) * rs + (ex > 0 ? xm : (ex < 0 ? xp : x))]) * p.inv_scale;
+                    lt[a] = lrow[pop_slot<L>(a) * rs + (ex > 0 ? xp : (ex < 0 ? xm : x))];
                 }
                 float E[3], wr, wj[3], lam[L::Q], gEc[3];
                 if (EF) {
@@ -584,7 +590,7 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
                 load_weights<L, WIN>(w_rho, w_j, p, cell, wr, wj);
                 adjoint_cell<L, FORCE, WIN>(h, lt, E, p, wr, wj, lam, gEc, acc);
 #pragma unroll
-                for (int b = 0; b < L::Q; ++b) outrow[b * rs + x] = lam[b];
+                for (int b = 0; b < L::Q; ++b) outrow[pop_slot<L>(b) * rs + x] = lam[b];
                 if (gE) {
 #pragma unroll
                     for (int d = 0; d < L::D; ++d) ge_s[d * rs + x] += (double)gEc[d];
@@ -597,15 +603,15 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
         dev::fence_proxy_async();
         __syncthreads();  // output rows complete
         {
-            // lane l of warp w takes piece w + l nw: the Q output rows, then
-            // the row's D updated dL/dE rows back from the stage (which is
-            // refilled only after the issuing threads' reads are done)
+            // lane l of warp w takes piece w + l nw: the row's Q output slots
+            // (one block), then its D updated dL/dE rows back from the stage
+            // (which is refilled only after the issuing threads' reads are done)
             const int k = warp + lane * nw;
-            if (k < L::Q) {
-                dev::bulk_store(lam_out + (int64_t)k * p.N + rowbase, outrow + k * rs, (uint32_t)nx * 4u);
+            if (k == 0) {
+                dev::bulk_store(lam_out + (int64_t)rowbase * L::Q, outrow, (uint32_t)(L::Q * nx) * 4u);
                 dev::bulk_commit();
-            } else if (gE && k < L::Q + L::D) {
-                const int d = k - L::Q;
+            } else if (gE && k <= L::D) {
+                const int d = k - 1;
                 dev::bulk_store(gE + (int64_t)d * p.N + rowbase, ge_s + d * rs, (uint32_t)nx * 8u);
                 dev::bulk_commit();
             }
@@ -613,7 +619,7 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
         // link copies of lam_t: slot k of (x, b) takes lam_bbar(x)
         for (uint32_t k = g0 + threadIdx.x; k < g1; k += blockDim.x) {
             const uint32_t d = desc[k - d0];
-            lamG_out[k] = outrow[opposite((int)(d >> 24)) * rs + (int)(d & 0xFFFFFFu)];
+            lamG_out[k] = outrow[slot_of<L>(opposite((int)(d >> 24))) * rs + (int)(d & 0xFFFFFFu)];
         }
     }
     dev::bulk_wait_all();
@@ -652,7 +658,8 @@ bool launch_rows_rs(const void* P, const float* lam_in, float* lam_out, const ui
     if (reinterpret_cast<uintptr_t>(gE) % 16 != 0) return false;  // dL/dE rows move by bulk copies
     const int gcapP = dev::window_cap(p.max_row_links, S::kBytes);
     const int gcapL = dev::window_cap(p.max_row_links, 4);
-    const int rs = RS ? RS : p.nx;
+    if (RS && RS != p.nx) return false;  // the stage rows are exactly nx long
+    const int rs = p.nx;
     const size_t stage =
         (size_t)AdjLayout<L, S>{p.nx, rs, p.lorder, gcapP, gcapL, gE ? L::D * rs * 8 : 0, EF ? L::D * rs * 4 : 0}
             .bytes();
@@ -696,16 +703,16 @@ bool launch_rows_rs(const void* P, const float* lam_in, float* lam_out, const ui
     return true;
 }
 
-// The shared-memory row stride is a compile-time 256 or 512 for rows up to
-// that length and the row length above (as in the step kernel).
+// The shared-memory row stride (the row length) is a compile-time constant
+// for rows of 256 or 512 cells (as in the step kernel).
 template <class L, class S, int FORCE, bool EF, bool WIN>
 bool launch_rows(const void* P, const float* lam_in, float* lam_out, const uint32_t* nbr, const float* Ef,
                  const float* w_rho, const float* w_j, double* gE, double* slots, int64_t slot_blocks,
                  const KParams& p, cudaStream_t s) {
-    if (p.nx <= 256)
+    if (p.nx == 256)
         return launch_rows_rs<L, S, FORCE, EF, WIN, 256>(P, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE, slots,
                                                           slot_blocks, p, s);
-    if (p.nx <= 512)
+    if (p.nx == 512)
         return launch_rows_rs<L, S, FORCE, EF, WIN, 512>(P, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE, slots,
                                                           slot_blocks, p, s);
     return launch_rows_rs<L, S, FORCE, EF, WIN, 0>(P, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE, slots, slot_blocks,

@@ -1074,7 +1074,10 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
     c->adj_stats[1] = store_all ? T + 1 : (binomial ? 2 + nsnap : nseg + K - 1);
     c->adj_stats[2] = fwd_steps;
     c->adj_stats[3] = T;
-    if (dL_df0) ADJ_CHECK(cudaMemcpyAsync(dL_df0, lam[li], lam_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (dL_df0) {
+        c->launches += lbm::launch_unslot(c->lat.vel, lam[li], dL_df0, p, c->stream);
+        ADJ_CHECK(cudaGetLastError());
+    }
     c->launches += lbm::launch_reduce_slots(slots, nslot / 5, 5, red, c->stream);
     double host[5];
     ADJ_CHECK(cudaMemcpyAsync(host, red, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->stream));

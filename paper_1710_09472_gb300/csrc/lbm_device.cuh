@@ -44,6 +44,15 @@ __device__ __forceinline__ uint32_t shifted(const Cell& c, int a, int s) {
     return c.r[ey + 1][ez + 1] + (uint32_t)xs;
 }
 
+// Storage index of direction a at the cell x + s e_a (s = -1, 0 or +1): slot
+// pop_slot(a) of that cell's row (see pop_slot).
+template <class L>
+__device__ __forceinline__ int64_t pop_at(const KParams& p, const Cell& c, int a, int s) {
+    const int ex = s * L::c(a, 0), ey = s * L::c(a, 1), ez = s * L::c(a, 2);
+    const int xs = ex > 0 ? c.xp : (ex < 0 ? c.xm : c.x);
+    return (int64_t)L::Q * c.r[ey + 1][ez + 1] + (int64_t)(pop_slot<L>(a) * p.nx + xs);
+}
+
 template <class L>
 __device__ __forceinline__ float edot(int a, const float* v) {
     float r = 0.f;
@@ -75,8 +84,9 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Pull the stored (scaled) deviations of f(x, t) from a state (populations P
-// followed by the link buffer G): f_a(x) = P_a(x - e_a) when x - e_a is fluid;
+// Pull the stored (scaled) deviations of f(x, t) from a state (populations P,
+// in the slot layout of pop_slot, followed by the link buffer G):
+// f_a(x) = P_a(x - e_a) when x - e_a is fluid;
 // when it is solid (bit a of the link mask) the halfway bounce-back value
 // f_a(x) = f*_abar(x), which the collision at x stored in the link slot of its
 // outgoing direction abar.
@@ -92,7 +102,7 @@ __device__ __forceinline__ void pull(const typename S::T* __restrict__ P, const 
         if (a != 0 && ((m >> a) & 1u))
             h[a] = S::raw(G + link_slot(base, o, opposite(a)));
         else
-            h[a] = S::raw(P + (int64_t)a * p.N + (a == 0 ? c.cell : shifted<L>(c, a, -1)));
+            h[a] = S::raw(P + pop_at<L>(p, c, a, -1));
     }
 }
 
@@ -127,8 +137,9 @@ __device__ __forceinline__ unsigned long long packed_x() {
 // direction: by x itself, in the pull of direction bbar (which reads
 // x - e_bbar = x + e_b) and in the adjoint gather of direction b (which reads
 // x + e_b).  So the halfway bounce-back value win[k - w0] is written into that
-// staged slot, rows[d * rs + (x + e_bx mod nx)] (rs the row stride) with d = bbar (PULL) or b
-// (gather), and the cells then read their rows without any link logic.
+// staged slot, rows[slot(d) * rs + (x + e_bx mod nx)] (rows in slot order, rs
+// the row stride) with d = bbar (PULL) or b (gather), and the cells then read
+// their rows without any link logic.
 // The descriptors come from the staged window desc (first element d0).
 template <class L, bool PULL, class T>
 __device__ __forceinline__ void patch_links(T* rows, int nx, int rs, const T* win, uint32_t w0, uint32_t g0,
@@ -139,7 +150,7 @@ __device__ __forceinline__ void patch_links(T* rows, int nx, int rs, const T* wi
         const int x = (int)(d & 0xFFFFFFu), b = (int)(d >> 24);
         int xs = x + (int)((kPx >> (2 * b)) & 3ull) - 1;
         xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
-        rows[(PULL ? opposite(b) : b) * rs + xs] = win[k - w0];
+        rows[slot_of<L>(PULL ? opposite(b) : b) * rs + xs] = win[k - w0];
     }
 }
 

@@ -72,6 +72,53 @@ struct LatD3V19 {
 __host__ __device__ constexpr int opposite(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
 
 // ---------------------------------------------------------------------------
+// Population storage.  Row r = z ny + y keeps its Q directions one after
+// another, nx values each: direction a of cell (x, r) is element
+// (r Q + slot(a)) nx + x.  The slots order the directions by (e_ay, e_az)
+// (key 3 (e_ay + 1) + e_az + 1, ties by a), so the directions that a row
+// pulls from one neighbouring row (y - e_ay, z - e_az) are consecutive slots
+// of that row, and a row's Q directions are one contiguous block.
+// ---------------------------------------------------------------------------
+template <class L>
+__host__ __device__ constexpr int pop_key(int a) {
+    return (L::c(a, 1) + 1) * 3 + (L::c(a, 2) + 1);
+}
+template <class L>
+__host__ __device__ constexpr int pop_slot(int a) {
+    int s = 0;
+    for (int b = 0; b < L::Q; ++b)
+        if (pop_key<L>(b) < pop_key<L>(a) || (pop_key<L>(b) == pop_key<L>(a) && b < a)) ++s;
+    return s;
+}
+// first slot and number of directions with key k (0 .. 8)
+template <class L>
+__host__ __device__ constexpr int key_first(int k) {
+    int s = 0;
+    for (int b = 0; b < L::Q; ++b) s += pop_key<L>(b) < k ? 1 : 0;
+    return s;
+}
+template <class L>
+__host__ __device__ constexpr int key_count(int k) {
+    int s = 0;
+    for (int b = 0; b < L::Q; ++b) s += pop_key<L>(b) == k ? 1 : 0;
+    return s;
+}
+// slot(a) for a direction known only at run time: 5 bits per direction,
+// directions 0 .. 11 in the first word, 12 .. in the second
+template <class L>
+__host__ __device__ constexpr unsigned long long packed_slots(int word) {
+    unsigned long long v = 0;
+    for (int a = 12 * word; a < L::Q && a < 12 * (word + 1); ++a)
+        v |= (unsigned long long)pop_slot<L>(a) << (5 * (a - 12 * word));
+    return v;
+}
+template <class L>
+__host__ __device__ __forceinline__ int slot_of(int a) {
+    constexpr unsigned long long lo = packed_slots<L>(0), hi = packed_slots<L>(1);
+    return (int)((a < 12 ? (lo >> (5 * a)) : (hi >> (5 * (a - 12)))) & 31ull);
+}
+
+// ---------------------------------------------------------------------------
 // Storage of the deviation h_a = f_a - rho0 w_a / I_0.  The kernels work in
 // the storage's scaled units h~ = scale * h (scale = 2^12 for FP16, 1
 // otherwise): raw() decodes to FP32 without unscaling, put() rounds to
@@ -188,6 +235,8 @@ int launch_build_neighbors(int vel, const uint8_t* mask, uint32_t* nbr, unsigned
 // Bounded-wait probe (writes code 3 into *status when its wait runs out).
 int launch_wait_probe(int* status, long long limit, cudaStream_t s);
 // Per-link descriptors ldesc[k] = x | b << 24 (needs lbase).
+// FP32 field in the populations' slot layout -> direction-major out[a * N + cell].
+int launch_unslot(int vel, const float* in, float* out, const KParams& p, cudaStream_t s);
 // Per-row cell order (fluid cells first) for the row-staged kernels.
 int launch_build_row_order(const uint32_t* nbr, uint16_t* rorder, const KParams& p, cudaStream_t s);
 int launch_build_link_desc(int vel, const uint32_t* nbr, const uint32_t* lbase, uint32_t* ldesc, const KParams& p,

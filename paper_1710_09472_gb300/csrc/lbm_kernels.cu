@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kBlock) k_init(typename S::T* __restrict__ P, 
                 v = heq_unscaled<L>(p, b, r1, u1);
             }
         }
-        S::put(P + (int64_t)b * p.N + c.cell, v * p.scale);
+        S::put(P + dev::pop_at<L>(p, c, b, 0), v * p.scale);
     }
 }
 
@@ -301,6 +301,16 @@ __global__ void __launch_bounds__(kBlock) k_populations(const typename S::T* __r
     }
 }
 
+// Copies an FP32 field in the slot layout of the populations (see pop_slot)
+// into direction-major order out[a * N + cell].
+template <class L>
+__global__ void __launch_bounds__(kBlock) k_unslot(const float* __restrict__ in, float* __restrict__ out, KParams p) {
+    Cell c;
+    if (!dev::cell_of_thread(p, c)) return;
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) out[(int64_t)a * p.N + c.cell] = in[dev::pop_at<L>(p, c, a, 0)];
+}
+
 Launch grid_of(const KParams& p) {
     Launch l;
     const int bx = p.nx >= kBlock ? kBlock : ((p.nx + 31) / 32) * 32;
@@ -380,6 +390,15 @@ __global__ void k_wait_probe(int* status, long long limit) {
 int launch_wait_probe(int* status, long long limit, cudaStream_t s) {
     k_wait_probe<<<1, 32, 0, s>>>(status, limit);
     return 1;
+}
+
+int launch_unslot(int vel, const float* in, float* out, const KParams& p, cudaStream_t s) {
+    Launch l = grid_of(p);
+    return dispatch_lattice(vel, [&](auto lat) {
+        using L = decltype(lat);
+        k_unslot<L><<<l.grid, l.block, 0, s>>>(in, out, p);
+        return 1;
+    });
 }
 
 int launch_build_row_order(const uint32_t* nbr, uint16_t* rorder, const KParams& p, cudaStream_t s) {

@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict
     const uint32_t m = __ldg(nbr + c.cell);
     if (m & kSolidBit) {
 #pragma unroll
-        for (int a = 0; a < L::Q; ++a) S::put(Pout + (int64_t)a * p.N + c.cell, 0.f);
+        for (int a = 0; a < L::Q; ++a) S::put(Pout + dev::pop_at<L>(p, c, a, 0), 0.f);
         return;
     }
     float h[L::Q];
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict
     const uint32_t base = m ? __ldg(p.lbase + c.cell) : 0u;
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
-        Pout[(int64_t)a * p.N + c.cell] = t[a];
+        Pout[dev::pop_at<L>(p, c, a, 0)] = t[a];
         if (a != 0 && ((o >> a) & 1u)) Gout[link_slot(base, o, a)] = t[a];
     }
 }
@@ -403,10 +403,11 @@ __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict
 // Row-staged step kernel (used when a whole x-row of one direction is a
 // whole number of 16-byte chunks and the stages fit shared memory).  A
 // persistent block walks rows r = blockIdx.x, blockIdx.x + gridDim.x, ...:
-//  - the Q source rows P_a(y - e_ay, z - e_az, :) of the row, its cell order
-//    and its ranges of the link buffer and of the link descriptors arrive by
-//    bulk asynchronous copies into a ring of STAGES stages, STAGES - 1 rows
-//    ahead of the row being computed.  One thread, lane 0 of the last warp,
+//  - the Q source rows P_a(y - e_ay, z - e_az, :) of the row (one contiguous
+//    block of consecutive slots per neighbouring row, at most 9 copies), its
+//    cell order and its ranges of the link buffer and of the link
+//    descriptors arrive by bulk asynchronous copies into a ring of STAGES
+//    stages, STAGES - 1 rows ahead of the row being computed.  One thread, lane 0 of the last warp,
 //    arms the stage's mbarrier with the byte count and issues the copies.  A
 //    bulk copy holds its issuing thread for many cycles, so the issuer is the
 //    warp with the least cell work (the order puts the solid cells, and the
@@ -419,8 +420,7 @@ __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict
 //    only write zeros;
 //  - f_a(x) is read from the ring at x - e_ax (periodic wrap in x is a
 //    shared-memory index); results go into a shared-memory output row set
-//    that leaves by bulk stores (one per direction, spread over the warps,
-//    lane l of warp w storing direction w + l nw);
+//    that leaves by one bulk store (the row's Q slots are contiguous);
 //  - one pass over the row's links copies the outgoing values f*_b(x) from
 //    the output rows into the row's contiguous range of the link buffer.
 // Two block barriers per row; a stage is refilled after the first barrier of
@@ -430,10 +430,11 @@ __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict
 // leaves its buffers).
 // ---------------------------------------------------------------------------
 
-// Shared-memory layout of one stage: Q source rows (stride rs elements), the
-// row's cell order (lorder 16-bit entries), its range of the link buffer
-// (gcap bytes) and of the link descriptors (dcap bytes), both as 16-byte
-// aligned windows.
+// Shared-memory layout of one stage: the Q source rows in slot order (row s
+// at s rs, rs = nx, so that consecutive slots of one neighbouring row land
+// with one copy), the row's cell order (lorder 16-bit entries), its range of
+// the link buffer (gcap bytes) and of the link descriptors (dcap bytes), both
+// as 16-byte aligned windows.
 template <class L, class S>
 struct StageLayout {
     int nx, rs, lorder, gcap, dcap;  // row length, shared-memory row stride (elements), order entries
@@ -455,8 +456,9 @@ struct StageLayout {
 
 // One thread: arms a stage's mbarrier with the byte count of row `row`
 // (links [g0, g1)), records the first elements of its two windows, and issues
-// the row's copies into stage st, all completing on bar: the Q source rows,
-// the cell order, the link window and the descriptor window.  The window
+// the row's copies into stage st, all completing on bar: per neighbouring row
+// (y - e_ay, z - e_az) the block of slots of the directions with that
+// (e_ay, e_az), the cell order, the link window and the descriptor window.  The window
 // starts are written before the barrier is armed, so the arrive releases them
 // to the waiting threads.
 template <class L, class S>
@@ -475,12 +477,14 @@ __device__ __forceinline__ void stage_row(unsigned char* st, const StageLayout<L
     const int yp = y == p.ny - 1 ? 0 : y + 1, ym = y == 0 ? p.ny - 1 : y - 1;
     const int zp = z == p.nz - 1 ? 0 : z + 1, zm = z == 0 ? p.nz - 1 : z - 1;
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) {
-        // source row of direction a: (y - e_ay, z - e_az), periodic
-        const int ys = L::c(a, 1) > 0 ? ym : (L::c(a, 1) < 0 ? yp : y);
-        const int zs = L::c(a, 2) > 0 ? zm : (L::c(a, 2) < 0 ? zp : z);
-        dev::bulk_load(lay.rows(st) + a * lay.rs, Pin + (int64_t)a * p.N + ((int64_t)zs * p.ny + ys) * p.nx, row_bytes,
-                       bar);
+    for (int k = 0; k < 9; ++k) {
+        if (key_count<L>(k) == 0) continue;
+        // slots key_first(k) .. of source row (y - e_y, z - e_z), periodic
+        const int ey = k / 3 - 1, ez = k % 3 - 1, s0 = key_first<L>(k);
+        const int ys = ey > 0 ? ym : (ey < 0 ? yp : y);
+        const int zs = ez > 0 ? zm : (ez < 0 ? zp : z);
+        dev::bulk_load(lay.rows(st) + s0 * lay.rs, Pin + ((int64_t)(zs * p.ny + ys) * L::Q + s0) * p.nx,
+                       (uint32_t)key_count<L>(k) * row_bytes, bar);
     }
     dev::bulk_load(lay.order(st), p.rorder + (int64_t)row * lay.lorder, 2u * (uint32_t)lay.lorder, bar);
     if (gb1 > gb0)
@@ -498,7 +502,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
     using T = typename S::T;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int nx = p.nx;
-    const int rs = RS ? RS : nx;  // shared-memory row stride: a constant for the common row lengths
+    const int rs = RS ? RS : nx;  // shared-memory row stride (= nx): a constant for the common row lengths
     const StageLayout<L, S> lay{nx, rs, p.lorder, gcap, dcap};
     const int sbytes = lay.bytes();
     T* outrow = reinterpret_cast<T*>(smem_raw + STAGES * sbytes);
@@ -509,7 +513,6 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
     const int R = p.ny * p.nz;
     const int G = gridDim.x;
     const bool leader = threadIdx.x == 0;
-    const int warp = (int)(threadIdx.x >> 5), nw = (int)(blockDim.x >> 5), lane = (int)(threadIdx.x & 31);
     const bool issuer = (int)threadIdx.x == (int)blockDim.x - 32;  // lane 0 of the last warp
     auto range = [&](int row, uint32_t& g0, uint32_t& g1) {
         g0 = g1 = 0u;
@@ -578,7 +581,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
 #pragma unroll
                 for (int a = 0; a < L::Q; ++a) {
                     const int ex = L::c(a, 0);
-                    h[a] = S::cvt(buf[a * rs + (ex > 0 ? xm : (ex < 0 ? xp : x))]);
+                    h[a] = S::cvt(buf[pop_slot<L>(a) * rs + (ex > 0 ? xm : (ex < 0 ? xp : x))]);
                 }
                 float E[3];
                 load_E<L>(Ef, EF, p, cell, E);
@@ -589,7 +592,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
                     typename S::T t[L::Q];
                     round_all<L, S, SR>(out, cell, p, t);
 #pragma unroll
-                    for (int a = 0; a < L::Q; ++a) outrow[a * rs + x] = t[a];
+                    for (int a = 0; a < L::Q; ++a) outrow[pop_slot<L>(a) * rs + x] = t[a];
                 } else {
                     // 16-bit storage: each pair is rounded and stored as soon as it exists
                     Rng rng(cell, p);
@@ -603,8 +606,8 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
                                 S::put(&ta, ha);
                                 S::put(&tb, hb);
                             }
-                            outrow[a * rs + x] = ta;
-                            outrow[(a + 1) * rs + x] = tb;
+                            outrow[pop_slot<L>(a) * rs + x] = ta;
+                            outrow[pop_slot<L>(a + 1) * rs + x] = tb;
                         },
                         [&](float rest) {
                             T t0, unused;
@@ -612,7 +615,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
                                 S::sr2(rest, rest, rng.pair(), t0, unused);
                             else
                                 S::put(&t0, rest);
-                            outrow[x] = t0;
+                            outrow[pop_slot<L>(0) * rs + x] = t0;
                         });
                 }
             } else {
@@ -622,18 +625,15 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
         }
         dev::fence_proxy_async();  // this thread's shared-memory writes before the bulk copies
         __syncthreads();           // output rows complete; the stage is free for its refill
-        {
-            // lane l of warp w stores direction w + l nw, each in its own bulk group
-            const int a = warp + lane * nw;
-            if (a < L::Q) {
-                dev::bulk_store(Pout + (int64_t)a * p.N + rowbase, outrow + a * rs, row_bytes);
-                dev::bulk_commit();
-            }
+        if (threadIdx.x == 0) {
+            // the row's Q slots, one contiguous block
+            dev::bulk_store(Pout + (int64_t)rowbase * L::Q, outrow, L::Q * row_bytes);
+            dev::bulk_commit();
         }
         // outgoing links: slot k of (x, b) takes f*_b(x)
         for (uint32_t k = g0 + threadIdx.x; k < g1; k += blockDim.x) {
             const uint32_t d = desc[k - d0];
-            Gout[k] = outrow[(int)(d >> 24) * rs + (int)(d & 0xFFFFFFu)];
+            Gout[k] = outrow[slot_of<L>((int)(d >> 24)) * rs + (int)(d & 0xFFFFFFu)];
         }
     }
     dev::bulk_wait_all();
@@ -696,7 +696,8 @@ template <class L, class S, int FORCE, bool EF, bool SR, int RS>
 bool launch_rows(const S*, const void* fin, void* fout, const uint32_t* nbr, const float* Ef, const KParams& p,
                  cudaStream_t s) {
     using T = typename S::T;
-    const int rs = RS ? RS : p.nx;
+    if (RS && RS != p.nx) return false;  // the stage rows are exactly nx long
+    const int rs = p.nx;
     const size_t row_bytes = (size_t)p.nx * S::kBytes, srow = (size_t)rs * S::kBytes;
     const int gcap = dev::window_cap(p.max_row_links, S::kBytes);
     const int dcap = dev::window_cap(p.max_row_links, 4);
@@ -713,17 +714,16 @@ bool launch_rows(const S*, const void* fin, void* fout, const uint32_t* nbr, con
 }
 
 // Row-staged kernel when the rows qualify, with the shared-memory row stride
-// a compile-time 256 or 512 for rows up to that length (the indexing then
-// folds into immediate offsets) and the row length itself above; otherwise
-// the general kernel.
+// (the row length) a compile-time constant for rows of 256 or 512 cells (the
+// indexing then folds into immediate offsets); otherwise the general kernel.
 template <class L, class S, int FORCE, bool EF, bool SR>
 int launch_one(const void* fin, void* fout, const uint32_t* nbr, const float* Ef, const KParams& p, cudaStream_t s) {
     using T = typename S::T;
     const S* tag = nullptr;
     bool done;
-    if (p.nx <= 256)
+    if (p.nx == 256)
         done = launch_rows<L, S, FORCE, EF, SR, 256>(tag, fin, fout, nbr, Ef, p, s);
-    else if (p.nx <= 512)
+    else if (p.nx == 512)
         done = launch_rows<L, S, FORCE, EF, SR, 512>(tag, fin, fout, nbr, Ef, p, s);
     else
         done = launch_rows<L, S, FORCE, EF, SR, 0>(tag, fin, fout, nbr, Ef, p, s);
