@@ -22,9 +22,11 @@ def _built():
 
 
 # nx a multiple of 4 (and of 16 bytes per row) takes the row-staged reverse
-# kernel; a ragged nx takes the general one.
-SHAPES = {("D2V9", "staged"): (14, 40), ("D2V9", "general"): (14, 38),
-          ("D3V19", "staged"): (6, 7, 36), ("D3V19", "general"): (6, 7, 35)}
+# kernel; a ragged nx takes the general one.  "wide" rows (nx above the
+# staged kernel's 256 threads) take the staged kernel with two passes per
+# row and output rows of their own instead of the staged lam rows.
+SHAPES = {("D2V9", "staged"): (14, 40), ("D2V9", "general"): (14, 38), ("D2V9", "wide"): (6, 320),
+          ("D3V19", "staged"): (6, 7, 36), ("D3V19", "general"): (6, 7, 35), ("D3V19", "wide"): (2, 3, 288)}
 
 
 def _case(vel, layout="staged"):
@@ -74,7 +76,7 @@ def _compare(sim, res, dE, lam0, vel, shape, mask, B, Ef, rho0, u0, wr, wj, tau,
 
 @pytest.mark.parametrize("vel", ["D2V9", "D3V19"])
 @pytest.mark.parametrize("force", ["term", "shift"])
-@pytest.mark.parametrize("layout", ["staged", "general"])
+@pytest.mark.parametrize("layout", ["staged", "general", "wide"])
 def test_adjoint_matches_oracle(vel, force, layout):
     shape, mask, B, Ef, rho0, u0, wr, wj = _case(vel, layout)
     tau, T, tb = 0.75, 14, 6
