@@ -33,11 +33,10 @@ def workload_name(n: int) -> str:
             "tau=0.8 E_x=1e-6 B_z=1e-3 force=term")
 
 # DRAM traffic per launch of the step kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum) from an ncu capture of a 160^3 launch of the same
-# sphere recipe, scaled to 256^3 by the fluid cells processed; keyed by
-# storage, with the hash of the kernel source it was taken on, and reported
-# as null once the source has changed.
-NCU_TRAFFIC = {"f16": (1257078319, "1d4fceaf620ae57b")}
+# dram__bytes_write.sum) from an ncu capture of one 256^3 launch of this
+# workload; keyed by storage, with the hash of the kernel source it was taken
+# on, and reported as null once the source has changed.
+NCU_TRAFFIC = {"f16": (1361818368, "d1ad8e473eb9ad71")}
 
 FALLBACK_HBM_GBS = 6800.0
 
