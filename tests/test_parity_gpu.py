@@ -75,11 +75,11 @@ def test_parity_2d(storage, force, efield, shape):
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
-@pytest.mark.parametrize("shape", [(12, 200), (10, 320), (6, 640)])
+@pytest.mark.parametrize("shape", [(12, 200), (8, 256), (10, 320), (4, 512), (6, 640)])
 def test_parity_row_strides(storage, shape):
-    """The row-staged step kernel keeps its shared-memory rows at a stride of
-    256 elements for rows up to 256 cells (200: padded), 512 up to 512 (320)
-    and the row length above (640); D2V9 disks, 40 steps, against the oracle."""
+    """The row-staged step kernel keeps its shared-memory rows exactly nx long,
+    at a compile-time stride for nx = 256 and 512 and a run-time one otherwise
+    (200, 320, 640); D2V9 disks, 40 steps, against the oracle."""
     solid, _ = wl.boolean_obstacles(shape, 3.0, 0.8, seed=47)
     rho, u = _fields(shape, 2, 48)
     E, B = (2e-4, -5e-5, 0.0), (0.0, 0.0, 3e-3)
