@@ -13,7 +13,7 @@
  * bounce-back on links into solid cells, and a hand-written adjoint.
  *
  * Conventions shared by every call:
- *   - dims = {nx, ny, nz}; 2D lattices take nz = 1.  Cells are numbered
+ *   - dims = {nx, ny, nz}; 2D lattices take nz = 1, 1D ny = nz = 1.  Cells are numbered
  *     cell = (z * ny + y) * nx + x (x fastest); N = nx * ny * nz.
  *   - The box is periodic in every direction; walls and obstacles come
  *     only from the solid mask.
@@ -25,6 +25,9 @@
  *              5 (0,0,1) 6 (0,0,-1) 7 (1,1,0) 8 (-1,-1,0) 9 (1,-1,0)
  *              10 (-1,1,0) 11 (1,0,1) 12 (-1,0,-1) 13 (1,0,-1) 14 (-1,0,1)
  *              15 (0,1,1) 16 (0,-1,-1) 17 (0,1,-1) 18 (0,-1,1)
+ *       D3V27: D3V19's 0 .. 18, then 19 (1,1,1) 20 (-1,-1,-1) 21 (1,1,-1)
+ *              22 (-1,-1,1) 23 (1,-1,1) 24 (-1,1,-1) 25 (-1,1,1) 26 (1,-1,-1)
+ *       D1V3 : 0 (0) 1 (1) 2 (-1)
  *   - Velocities u, currents j = rho u, fields E and B are in the paper's
  *     xi units (velocity / reference speed c_s, Sec. 8; Sec. 9.3 takes the
  *     acceleration a = E).  A lattice-unit velocity is c_s * u.
@@ -68,7 +71,8 @@ typedef enum {
     LBM_ERR_STATE = 7             /* call out of order (e.g. step before init) */
 } lbm_status;
 
-typedef enum { LBM_D2V9 = 0, LBM_D3V19 = 1 } lbm_velset;          /* Sec. 8.2; Table lattices-tab */
+typedef enum { LBM_D2V9 = 0, LBM_D3V19 = 1, LBM_D3V27 = 2, LBM_D1V3 = 3 } lbm_velset;
+    /* D2V9 Sec. 8.2, D1V3 Sec. 8.1, D3V19 and D3V27 Table lattices-tab (App. A) */
 typedef enum { LBM_FD = 0, LBM_BE = 1, LBM_MB = 2 } lbm_stat;      /* Sec. 2, Eq. be-fd-dist-eq */
 typedef enum { LBM_F32 = 0, LBM_F16_DEV = 1, LBM_BF16_DEV = 2 } lbm_dtype;
 typedef enum { LBM_FORCE_SHIFT = 0, LBM_FORCE_TERM = 1 } lbm_force; /* Sec. 7 */
@@ -94,7 +98,7 @@ typedef struct {
 } lbm_lattice;
 
 /* Create a context and allocate its device buffers.
- *   dims   : {nx, ny, nz}, each >= 1 (nz == 1 for D2V9); N < 2^31 * 16.
+ *   dims   : {nx, ny, nz}, each >= 1 (nz == 1 for D2V9, ny == nz == 1 for D1V3); N < 2^31 * 16.
  *   tau    : BGK relaxation time, > 1/2.
  *   E, B   : uniform field (3 components each, may be NULL = 0).  In 2D only
  *            E_x, E_y and B_z act.

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "_build", "liblbm.so")
 LBM_OK = 0
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_INVALID_ARG", 2: "LBM_ERR_UNSTABLE_LATTICE", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_OOM",
           5: "LBM_ERR_NONFINITE", 6: "LBM_ERR_TIMEOUT", 7: "LBM_ERR_STATE"}
-VEL = {"D2V9": 0, "D3V19": 1}
+VEL = {"D2V9": 0, "D3V19": 1, "D3V27": 2, "D1V3": 3}
 STAT = {"fd": 0, "be": 1, "mb": 2}
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 FORCE = {"shift": 0, "term": 1}

@@ -67,7 +67,7 @@ template <class L, bool EF>
 __device__ __forceinline__ void load_E(const float* __restrict__ Ef, const KParams& p, uint32_t cell, float* E) {
     if (EF) {
         E[0] = __ldg(Ef + cell);
-        E[1] = __ldg(Ef + p.N + cell);
+        E[1] = (L::D >= 2) ? __ldg(Ef + p.N + cell) : 0.f;
         E[2] = (L::D == 3) ? __ldg(Ef + 2 * p.N + cell) : 0.f;
     } else {
         E[0] = p.E[0];
@@ -88,15 +88,6 @@ __device__ __forceinline__ void load_weights(const float* __restrict__ w_rho, co
     }
 }
 
-// First direction of the shell |e|^2 = s (0 rest, 1 axis, 2 diagonal); the
-// weight w_a and the coefficient k2_a depend on the shell only.
-template <class L>
-__host__ __device__ constexpr int shell_rep(int s) {
-    int r = 0;
-    for (int a = L::Q - 1; a >= 0; --a)
-        if (dev::esq<L>(a) == s) r = a;
-    return r;
-}
 
 // The reverse step at one fluid cell.  h: unscaled deviations of f_t at the
 // cell; lt: lamt; E: the field there; wr, wj: its loss weights (used when WIN).
@@ -111,62 +102,129 @@ __host__ __device__ constexpr int shell_rep(int s) {
 //   d/dv       = rho [Bp M1 + 2 Cp M2 v + 2 K0 v],
 //   sum lt S   = rho [Bp M1.E + 2 Cp u.M2.E + 2 K0 u.E + 2 u.(K1 x B)/c_s],
 // with M0 = sum mu, M1 = sum mu e, M2 = sum mu e e^T, K0 = sum mu k2,
-// K1 = sum mu k2 e.  Since w_a and k2_a are constant on each shell, the
-// per-direction work is only the unweighted shell moments of lt.
+// K1 = sum mu k2 e.  Since w_a and k2_a are constant on each shell (|e|^2 =
+// 1, 2, 3: axes, face diagonals, corners), the per-direction work is only
+// the unweighted shell moments of lt.
 template <class L, int FORCE, bool WIN>
 __device__ __forceinline__ void adjoint_cell(const float* h, const float* lt, const float* E, const KParams& p,
                                              float wr, const float* wj, float* lam, float* gEc, double* acc) {
-    constexpr int kAx = shell_rep<L>(1), kDg = shell_rep<L>(2);
+    constexpr int kR1 = shell_first<L>(1), kR2 = shell_first<L>(2), kR3 = shell_first<L>(3);
     // forward moments of f_t
     float drho = 0.f, j[3] = {0.f, 0.f, 0.f}, lth = 0.f;
-    // shell moments of lt: axis (1) and diagonal (2); the rest shell adds to M0 only
-    float L0a = 0.f, L0d = 0.f, L1a[3] = {0.f, 0.f, 0.f}, L1d[3] = {0.f, 0.f, 0.f};
-    float L2a[3] = {0.f, 0.f, 0.f};                     // axis shell: diagonal of sum lt e e^T
-    float L2d[3] = {0.f, 0.f, 0.f}, L2o[3] = {0.f, 0.f, 0.f};  // diagonal shell: diagonal; (xy, xz, yz)
+    float rho, inv_rho, u[3], M0, K0, M1[3], K1[3], Mxx, Myy, Mzz, Mxy, Mxz, Myz;
+    if constexpr (kR1 > 0 && kR2 > 0 && kR3 < 0) {
+        // two moving shells (D2V9, D3V19): axis and diagonal
+        constexpr int kAx = kR1, kDg = kR2;
+        // shell moments of lt: axis (1) and diagonal (2); the rest shell adds to M0 only
+        float L0a = 0.f, L0d = 0.f, L1a[3] = {0.f, 0.f, 0.f}, L1d[3] = {0.f, 0.f, 0.f};
+        float L2a[3] = {0.f, 0.f, 0.f};                     // axis shell: diagonal of sum lt e e^T
+        float L2d[3] = {0.f, 0.f, 0.f}, L2o[3] = {0.f, 0.f, 0.f};  // diagonal shell: diagonal; (xy, xz, yz)
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) {
-        const int ex = L::c(a, 0), ey = L::c(a, 1), ez = L::c(a, 2);
-        drho += h[a];
-        j[0] += ex * h[a];
-        j[1] += ey * h[a];
-        j[2] += ez * h[a];
-        lth = fmaf(lt[a], h[a], lth);
-        const int sh = dev::esq<L>(a);
-        if (sh == 1) {
-            L0a += lt[a];
-            if (ex) { L1a[0] += ex * lt[a]; L2a[0] += lt[a]; }
-            if (ey) { L1a[1] += ey * lt[a]; L2a[1] += lt[a]; }
-            if (ez) { L1a[2] += ez * lt[a]; L2a[2] += lt[a]; }
-        } else if (sh == 2) {
-            L0d += lt[a];
-            if (ex) { L1d[0] += ex * lt[a]; L2d[0] += lt[a]; }
-            if (ey) { L1d[1] += ey * lt[a]; L2d[1] += lt[a]; }
-            if (ez) { L1d[2] += ez * lt[a]; L2d[2] += lt[a]; }
-            if (ex * ey) L2o[0] += ex * ey * lt[a];
-            if (ex * ez) L2o[1] += ex * ez * lt[a];
-            if (ey * ez) L2o[2] += ey * ez * lt[a];
+        for (int a = 0; a < L::Q; ++a) {
+            const int ex = L::c(a, 0), ey = L::c(a, 1), ez = L::c(a, 2);
+            drho += h[a];
+            j[0] += ex * h[a];
+            j[1] += ey * h[a];
+            j[2] += ez * h[a];
+            lth = fmaf(lt[a], h[a], lth);
+            const int sh = esq_of<L>(a);
+            if (sh == 1) {
+                L0a += lt[a];
+                if (ex) { L1a[0] += ex * lt[a]; L2a[0] += lt[a]; }
+                if (ey) { L1a[1] += ey * lt[a]; L2a[1] += lt[a]; }
+                if (ez) { L1a[2] += ez * lt[a]; L2a[2] += lt[a]; }
+            } else if (sh == 2) {
+                L0d += lt[a];
+                if (ex) { L1d[0] += ex * lt[a]; L2d[0] += lt[a]; }
+                if (ey) { L1d[1] += ey * lt[a]; L2d[1] += lt[a]; }
+                if (ez) { L1d[2] += ez * lt[a]; L2d[2] += lt[a]; }
+                if (ex * ey) L2o[0] += ex * ey * lt[a];
+                if (ex * ez) L2o[1] += ex * ez * lt[a];
+                if (ey * ez) L2o[2] += ey * ez * lt[a];
+            }
+        }
+        j[0] *= p.cs_inv;
+        j[1] *= p.cs_inv;
+        j[2] = (L::D == 3) ? j[2] * p.cs_inv : 0.f;
+        rho = p.rho0 + drho;
+        inv_rho = 1.0f / rho;
+        u[0] = j[0] * inv_rho;
+        u[1] = j[1] * inv_rho;
+        u[2] = j[2] * inv_rho;
+        // weighted moments
+        const float w0 = p.w[0], w1 = p.w[kAx], w2 = p.w[kDg];
+        const float k1 = p.k2[kAx], k2d = p.k2[kDg];
+        M0 = w0 * lt[0] + w1 * L0a + w2 * L0d;
+        K0 = w0 * p.k2[0] * lt[0] + w1 * k1 * L0a + w2 * k2d * L0d;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            M1[d] = w1 * L1a[d] + w2 * L1d[d];
+            K1[d] = w1 * k1 * L1a[d] + w2 * k2d * L1d[d];
+        }
+        // M2 = w1 diag(L2a) + w2 [L2d on the diagonal, L2o off it]
+        Mxx = w1 * L2a[0] + w2 * L2d[0];
+        Myy = w1 * L2a[1] + w2 * L2d[1];
+        Mzz = w1 * L2a[2] + w2 * L2d[2];
+        Mxy = w2 * L2o[0];
+        Mxz = w2 * L2o[1];
+        Myz = w2 * L2o[2];
+    } else {
+        // unweighted moments of lt per shell s = |e|^2: sum lt, sum lt e, the
+        // diagonal of sum lt e e^T, and its (xy, xz, yz) entries; the rest
+        // direction adds to M0 and K0 only
+        float L0[4] = {0.f, 0.f, 0.f, 0.f}, L1[4][3] = {}, L2[4][3] = {}, L2o[4][3] = {};
+#pragma unroll
+        for (int a = 0; a < L::Q; ++a) {
+            const int ex = L::c(a, 0), ey = L::c(a, 1), ez = L::c(a, 2);
+            drho += h[a];
+            j[0] += ex * h[a];
+            j[1] += ey * h[a];
+            j[2] += ez * h[a];
+            lth = fmaf(lt[a], h[a], lth);
+            const int sh = esq_of<L>(a);
+            if (sh == 0) continue;
+            L0[sh] += lt[a];
+            if (ex) { L1[sh][0] += ex * lt[a]; L2[sh][0] += lt[a]; }
+            if (ey) { L1[sh][1] += ey * lt[a]; L2[sh][1] += lt[a]; }
+            if (ez) { L1[sh][2] += ez * lt[a]; L2[sh][2] += lt[a]; }
+            if (ex * ey) L2o[sh][0] += ex * ey * lt[a];
+            if (ex * ez) L2o[sh][1] += ex * ez * lt[a];
+            if (ey * ez) L2o[sh][2] += ey * ez * lt[a];
+        }
+        j[0] *= p.cs_inv;
+        j[1] *= p.cs_inv;
+        j[2] = (L::D == 3) ? j[2] * p.cs_inv : 0.f;
+        rho = p.rho0 + drho;
+        inv_rho = 1.0f / rho;
+        u[0] = j[0] * inv_rho;
+        u[1] = j[1] * inv_rho;
+        u[2] = j[2] * inv_rho;
+        // weighted moments: shell s contributes with w_s and w_s k2_s
+        M0 = p.w[0] * lt[0];
+        K0 = p.w[0] * p.k2[0] * lt[0];
+        M1[0] = M1[1] = M1[2] = 0.f;
+        K1[0] = K1[1] = K1[2] = 0.f;
+        Mxx = Myy = Mzz = Mxy = Mxz = Myz = 0.f;
+#pragma unroll
+        for (int sh = 1; sh <= 3; ++sh) {
+            const int r = sh == 1 ? kR1 : (sh == 2 ? kR2 : kR3);
+            if (r < 0) continue;
+            const float ws = p.w[r], wk = p.w[r] * p.k2[r];
+            M0 += ws * L0[sh];
+            K0 += wk * L0[sh];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                M1[d] += ws * L1[sh][d];
+                K1[d] += wk * L1[sh][d];
+            }
+            Mxx += ws * L2[sh][0];
+            Myy += ws * L2[sh][1];
+            Mzz += ws * L2[sh][2];
+            Mxy += ws * L2o[sh][0];
+            Mxz += ws * L2o[sh][1];
+            Myz += ws * L2o[sh][2];
         }
     }
-    j[0] *= p.cs_inv;
-    j[1] *= p.cs_inv;
-    j[2] = (L::D == 3) ? j[2] * p.cs_inv : 0.f;
-    const float rho = p.rho0 + drho;
-    const float inv_rho = 1.0f / rho;
-    const float u[3] = {j[0] * inv_rho, j[1] * inv_rho, j[2] * inv_rho};
-    // weighted moments
-    const float w0 = p.w[0], w1 = p.w[kAx], w2 = p.w[kDg];
-    const float k1 = p.k2[kAx], k2d = p.k2[kDg];
-    const float M0 = w0 * lt[0] + w1 * L0a + w2 * L0d;
-    const float K0 = w0 * p.k2[0] * lt[0] + w1 * k1 * L0a + w2 * k2d * L0d;
-    float M1[3], K1[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        M1[d] = w1 * L1a[d] + w2 * L1d[d];
-        K1[d] = w1 * k1 * L1a[d] + w2 * k2d * L1d[d];
-    }
-    // M2 = w1 diag(L2a) + w2 [L2d on the diagonal, L2o off it]
-    const float Mxx = w1 * L2a[0] + w2 * L2d[0], Myy = w1 * L2a[1] + w2 * L2d[1], Mzz = w1 * L2a[2] + w2 * L2d[2];
-    const float Mxy = w2 * L2o[0], Mxz = w2 * L2o[1], Myz = w2 * L2o[2];
     auto m2v = [&](const float* v, float* out) {
         out[0] = Mxx * v[0] + Mxy * v[1] + Mxz * v[2];
         out[1] = Mxy * v[0] + Myy * v[1] + Myz * v[2];
@@ -637,6 +695,8 @@ inline Launch grid_of(const KParams& p) {
 template <class F>
 int dispatch_lattice(int vel, F&& f) {
     if (vel == LBM_D2V9) return f(LatD2V9{});
+    if (vel == LBM_D3V27) return f(LatD3V27{});
+    if (vel == LBM_D1V3) return f(LatD1V3{});
     return f(LatD3V19{});
 }
 

@@ -150,6 +150,16 @@ bool is_device_ptr(const void* p) {
 
 size_t pop_elem_bytes(int storage) { return storage == LBM_F32 ? 4 : 2; }
 
+// |e_a|^2 of direction a of a lattice (the velocity tables of lbm_internal.h)
+int lattice_esq(int vel, int a) {
+    switch (vel) {
+        case LBM_D2V9: return lbm::esq_of<lbm::LatD2V9>(a);
+        case LBM_D3V27: return lbm::esq_of<lbm::LatD3V27>(a);
+        case LBM_D1V3: return lbm::esq_of<lbm::LatD1V3>(a);
+        default: return lbm::esq_of<lbm::LatD3V19>(a);
+    }
+}
+
 }  // namespace
 
 lbm::KParams lbm::make_params(const lbm_ctx* c) {
@@ -170,7 +180,7 @@ lbm::KParams lbm::make_params(const lbm_ctx* c) {
     p.cs = (float)c->cs;
     p.cs_inv = (float)(1.0 / c->cs);
     for (int a = 0; a < c->Q; ++a) {
-        const int e2 = (a == 0) ? 0 : (c->Q == 9 ? (a <= 4 ? 1 : 2) : (a <= 6 ? 1 : 2));
+        const int e2 = lattice_esq(c->lat.vel, a);
         p.w[a] = (float)c->w[a];
         p.k2[a] = (float)(c->G * e2 / (c->cs * c->cs) + c->H);
         // W1_a = w_a Bp / c_s = w_a / (I2 c_s^2) as a double-float pair
@@ -203,6 +213,10 @@ void sanitize_fields(lbm_ctx* c) {
     if (c->D == 2) {  // only in-plane E and B_z act in 2D
         c->E[2] = 0.0;
         c->B[0] = c->B[1] = 0.0;
+    }
+    if (c->D == 1) {  // only E_x acts in 1D (xi x B has no x component)
+        c->E[1] = c->E[2] = 0.0;
+        c->B[0] = c->B[1] = c->B[2] = 0.0;
     }
 }
 
@@ -346,7 +360,8 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_lattice* lat, const int64_t dims[
                       const double B[3], int storage, void* cuda_stream) {
     if (!out || !lat || !dims) return LBM_ERR_INVALID_ARG;
     *out = nullptr;
-    if (lat->vel != LBM_D2V9 && lat->vel != LBM_D3V19) return LBM_ERR_INVALID_ARG;
+    if (lat->vel != LBM_D2V9 && lat->vel != LBM_D3V19 && lat->vel != LBM_D3V27 && lat->vel != LBM_D1V3)
+        return LBM_ERR_INVALID_ARG;
     if (lat->stat < LBM_FD || lat->stat > LBM_MB) return LBM_ERR_INVALID_ARG;
     if (lat->force != LBM_FORCE_SHIFT && lat->force != LBM_FORCE_TERM) return LBM_ERR_INVALID_ARG;
     if (storage < LBM_F32 || storage > LBM_BF16_DEV) return LBM_ERR_INVALID_ARG;
@@ -355,13 +370,14 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_lattice* lat, const int64_t dims[
     for (int d = 0; d < 3; ++d)
         if (dims[d] < 1 || dims[d] > (1 << 20)) return LBM_ERR_INVALID_ARG;
     if (lat->vel == LBM_D2V9 && dims[2] != 1) return LBM_ERR_INVALID_ARG;
+    if (lat->vel == LBM_D1V3 && (dims[1] != 1 || dims[2] != 1)) return LBM_ERR_INVALID_ARG;
     if (dims[1] * dims[2] > 0x7fffffffLL || dims[0] > 0x7fffffffLL) return LBM_ERR_INVALID_ARG;
 
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return LBM_ERR_OOM;
     c->lat = *lat;
-    c->D = lat->vel == LBM_D2V9 ? 2 : 3;
-    c->Q = lat->vel == LBM_D2V9 ? 9 : 19;
+    c->D = lat->vel == LBM_D2V9 ? 2 : (lat->vel == LBM_D1V3 ? 1 : 3);
+    c->Q = lat->vel == LBM_D2V9 ? 9 : (lat->vel == LBM_D1V3 ? 3 : (lat->vel == LBM_D3V27 ? 27 : 19));
     c->nx = dims[0];
     c->ny = dims[1];
     c->nz = dims[2];
@@ -405,12 +421,23 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_lattice* lat, const int64_t dims[
     c->Cc = 1.0 / (2.0 * I4);
     c->G = (Delta2sq - 1.0) / (2.0 * D * I4);
     c->H = -I2 * Delta2sq / (2.0 * I0 * I4);
-    // lattice (Sec. 8.2 D2V9; Table lattices-tab D3V19); c_s = sqrt(I2/(3 I4))
+    // lattice (Sec. 8.1 D1V3, Sec. 8.2 D2V9, Table lattices-tab D3V19 and
+    // D3V27); c_s = sqrt(I2/(3 I4)) for all four
     c->cs = std::sqrt(I2 / (3.0 * I4));
     if (lat->vel == LBM_D2V9) {
         c->w[0] = I0 * (1.0 - 5.0 * c->J2 / 9.0);
         for (int a = 1; a <= 4; ++a) c->w[a] = I0 * c->J2 / 9.0;
         for (int a = 5; a <= 8; ++a) c->w[a] = I0 * c->J2 / 36.0;
+    } else if (lat->vel == LBM_D1V3) {
+        c->w[0] = I0 * (1.0 - c->J2 / 3.0);
+        c->w[1] = c->w[2] = I0 * c->J2 / 6.0;
+    } else if (lat->vel == LBM_D3V27) {
+        // the shells' weights need I6 (fourth-order isotropy on three shells)
+        const double I6 = c->I[3], I4c = I4 * I4 * I4;
+        c->w[0] = I0 - 2.0 * I2 * I2 / (3.0 * I4) - I6 * I2 * I2 * I2 / (27.0 * I4c);
+        for (int a = 1; a <= 6; ++a) c->w[a] = (3.0 * I2 * I2 * I4 * I4 + I6 * I2 * I2 * I2) / (54.0 * I4c);
+        for (int a = 7; a <= 18; ++a) c->w[a] = (3.0 * I4 * I4 * I2 * I2 - I6 * I2 * I2 * I2) / (108.0 * I4c);
+        for (int a = 19; a <= 26; ++a) c->w[a] = I2 * I2 * I2 * I6 / (216.0 * I4c);
     } else {
         c->w[0] = I0 * (1.0 - 2.0 * c->J2 / 3.0);
         for (int a = 1; a <= 6; ++a) c->w[a] = I0 * c->J2 / 18.0;

@@ -14,7 +14,7 @@
 
 namespace lbm {
 
-constexpr int kMaxQ = 19;
+constexpr int kMaxQ = 27;
 // Per-cell link mask: bit a set when x - e_a is solid (a >= 1), i.e. the link
 // that streams into x along e_a bounces back; kSolidBit when x itself is solid.
 constexpr uint32_t kSolidBit = 0x80000000u;
@@ -44,8 +44,9 @@ __host__ __device__ __forceinline__ uint32_t link_slot(uint32_t base, uint32_t o
 }
 
 // ---------------------------------------------------------------------------
-// Lattices (Sec. 8.2 and Table lattices-tab).  Order: rest vector, then
-// opposite pairs (a odd, a + 1 = -e_a), as documented in lbm.h.
+// Lattices (Sec. 8.1 D1V3, Sec. 8.2 D2V9, Table lattices-tab D3V19 and D3V27).
+// Order: rest vector, then opposite pairs (a odd, a + 1 = -e_a), as
+// documented in lbm.h.
 // ---------------------------------------------------------------------------
 struct LatD2V9 {
     static constexpr int D = 2;
@@ -69,7 +70,40 @@ struct LatD3V19 {
     }
 };
 
+struct LatD3V27 {
+    static constexpr int D = 3;
+    static constexpr int Q = 27;
+    __host__ __device__ static constexpr int c(int a, int d) {
+        constexpr signed char t[27][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},  {0, 0, 1},
+                                          {0, 0, -1}, {1, 1, 0},   {-1, -1, 0}, {1, -1, 0},  {-1, 1, 0},  {1, 0, 1},
+                                          {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},  {0, 1, 1},   {0, -1, -1}, {0, 1, -1},
+                                          {0, -1, 1}, {1, 1, 1},   {-1, -1, -1}, {1, 1, -1}, {-1, -1, 1}, {1, -1, 1},
+                                          {-1, 1, -1}, {-1, 1, 1}, {1, -1, -1}};
+        return t[a][d];
+    }
+};
+
+struct LatD1V3 {
+    static constexpr int D = 1;
+    static constexpr int Q = 3;
+    __host__ __device__ static constexpr int c(int a, int d) { return d == 0 ? (a == 1 ? 1 : (a == 2 ? -1 : 0)) : 0; }
+};
+
 __host__ __device__ constexpr int opposite(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
+
+// The moving directions fall into shells of equal |e|^2 (1: axes, 2: face
+// diagonals, 3: corners), on which w_a and k2_a are constant.  shell_first(s)
+// is the first direction of shell s, or -1 when the lattice has none.
+template <class L>
+__host__ __device__ constexpr int esq_of(int a) {
+    return L::c(a, 0) * L::c(a, 0) + L::c(a, 1) * L::c(a, 1) + L::c(a, 2) * L::c(a, 2);
+}
+template <class L>
+__host__ __device__ constexpr int shell_first(int s) {
+    for (int a = 1; a < L::Q; ++a)
+        if (esq_of<L>(a) == s) return a;
+    return -1;
+}
 
 // ---------------------------------------------------------------------------
 // Population storage.  Row r = z ny + y keeps its Q directions one after
@@ -104,7 +138,7 @@ __host__ __device__ constexpr int key_count(int k) {
     return s;
 }
 // slot(a) for a direction known only at run time: 5 bits per direction,
-// directions 0 .. 11 in the first word, 12 .. in the second
+// directions 12 k .. 12 k + 11 in word k
 template <class L>
 __host__ __device__ constexpr unsigned long long packed_slots(int word) {
     unsigned long long v = 0;
@@ -114,8 +148,11 @@ __host__ __device__ constexpr unsigned long long packed_slots(int word) {
 }
 template <class L>
 __host__ __device__ __forceinline__ int slot_of(int a) {
-    constexpr unsigned long long lo = packed_slots<L>(0), hi = packed_slots<L>(1);
-    return (int)((a < 12 ? (lo >> (5 * a)) : (hi >> (5 * (a - 12)))) & 31ull);
+    constexpr unsigned long long w0 = packed_slots<L>(0), w1 = packed_slots<L>(1), w2 = packed_slots<L>(2);
+    if constexpr (L::Q <= 24)
+        return (int)((a < 12 ? (w0 >> (5 * a)) : (w1 >> (5 * (a - 12)))) & 31ull);
+    else
+        return (int)((a < 12 ? (w0 >> (5 * a)) : (a < 24 ? (w1 >> (5 * (a - 12))) : (w2 >> (5 * (a - 24))))) & 31ull);
 }
 
 // ---------------------------------------------------------------------------

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kBlock) k_init(typename S::T* __restrict__ P, 
     auto fields = [&](uint32_t cell, float& r, float* uu) {
         r = rho ? rho[cell] : p.rho0;
         uu[0] = u ? u[cell] : 0.f;
-        uu[1] = u ? u[p.N + cell] : 0.f;
+        uu[1] = (u && L::D >= 2) ? u[p.N + cell] : 0.f;
         uu[2] = (u && L::D == 3) ? u[2 * p.N + cell] : 0.f;
     };
     float r0, u0[3];
@@ -322,6 +322,8 @@ Launch grid_of(const KParams& p) {
 template <class F>
 int dispatch_lattice(int vel, F&& f) {
     if (vel == LBM_D2V9) return f(LatD2V9{});
+    if (vel == LBM_D3V27) return f(LatD3V27{});
+    if (vel == LBM_D1V3) return f(LatD1V3{});
     return f(LatD3V19{});
 }
 

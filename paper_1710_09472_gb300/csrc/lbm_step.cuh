@@ -31,23 +31,13 @@ using dev::kBlock;
 // exactly: h~*_0 = sum_a h~_a - sum_{a>0} h~*_a.
 // ---------------------------------------------------------------------------
 // The weights w_a, k2_a and W1_a depend on the shell |e_a|^2 only (axis 1,
-// diagonal 2), so the per-cell factors are folded per shell first:
+// face diagonal 2, corner 3; each lattice has some of them), so the per-cell
+// factors are folded per shell first:
 //   even_a = w_s (c0 + k2_s Ku) + w_s Cp s rho (e.u*) (w (e.u*) + 2 (e.E)),
 //            c0 = w A drho~, Ku = s rho (w u*^2 + 2 u.E)        (the E terms: FORCE 1)
 //   odd_a  = e_a . V_s,  V_s = W1_s v + 2 s rho w_s k2_s (B x u) / c_s  (B term: FORCE 1),
 // with v = w j~ + s c_s rho E (FORCE 1) or w j~ + s c_s rho a (FORCE 0), and
 // W1_s applied as its double-float pair once per cell.
-template <class L>
-struct Shells {
-    static constexpr int kAx = 1;  // first axis direction
-    __host__ __device__ static constexpr int diag() {
-        int r = 0;
-        for (int a = L::Q - 1; a > 0; --a)
-            if (L::c(a, 0) * L::c(a, 0) + L::c(a, 1) * L::c(a, 1) + L::c(a, 2) * L::c(a, 2) == 2) r = a;
-        return r;
-    }
-};
-
 // Arithmetic helpers of the value type V of collide_emit (float here).
 __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ float vdiv(float c, float x) { return c / x; }
@@ -72,7 +62,7 @@ __device__ __forceinline__ V vedot(int a, const V* v) {
 template <class L, int FORCE, class V, class Emit, class EmitRest>
 __device__ __forceinline__ void collide_emit(const V* h, const V* E, const KParams& p, Emit&& emit,
                                              EmitRest&& emit_rest) {
-    constexpr int kAx = Shells<L>::kAx, kDg = Shells<L>::diag();
+    constexpr int kR1 = shell_first<L>(1), kR2 = shell_first<L>(2), kR3 = shell_first<L>(3);
     V drho = h[0], j[3] = {V(0.f), V(0.f), V(0.f)};
 #pragma unroll
     for (int a = 1; a < L::Q; a += 2) {
@@ -120,31 +110,62 @@ __device__ __forceinline__ void collide_emit(const V* h, const V* E, const KPara
         cq = srho * V(p.Cp);
     }
     const V c0 = V(p.omega * p.A) * drho;
-    // per shell: the even constant, the (e.u) coefficient and the odd vector
-    const V e0a = V(p.w[kAx]) * vfma(V(p.k2[kAx]), Ku, c0), e0d = V(p.w[kDg]) * vfma(V(p.k2[kDg]), Ku, c0);
-    const V cqa = V(p.w[kAx]) * cq, cqd = V(p.w[kDg]) * cq;
-    V Va[3], Vd[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        Va[d] = vfma(V(p.W1lo[kAx]), v[d], V(p.W1hi[kAx]) * v[d]);
-        Vd[d] = vfma(V(p.W1lo[kDg]), v[d], V(p.W1hi[kDg]) * v[d]);
-        if (FORCE == 1) {
-            Va[d] = vfma(V(p.w[kAx] * p.k2[kAx]), bu[d], Va[d]);
-            Vd[d] = vfma(V(p.w[kDg] * p.k2[kDg]), bu[d], Vd[d]);
-        }
-    }
     V rest = drho;
+    if constexpr (kR1 > 0 && kR2 > 0 && kR3 < 0) {
+        // two moving shells (D2V9, D3V19): axis and diagonal
+        constexpr int kAx = kR1, kDg = kR2;
+        // per shell: the even constant, the (e.u) coefficient and the odd vector
+        const V e0a = V(p.w[kAx]) * vfma(V(p.k2[kAx]), Ku, c0), e0d = V(p.w[kDg]) * vfma(V(p.k2[kDg]), Ku, c0);
+        const V cqa = V(p.w[kAx]) * cq, cqd = V(p.w[kDg]) * cq;
+        V Va[3], Vd[3];
 #pragma unroll
-    for (int a = 1; a < L::Q; a += 2) {
-        const bool ax = dev::esq<L>(a) == 1;
-        const V eu = vedot<L>(a, ue);
-        const V g = (FORCE == 1) ? vfma(om, eu, V(2.f) * vedot<L>(a, E)) : eu;
-        const V even = vfma(ax ? cqa : cqd, eu * g, ax ? e0a : e0d);
-        const V odd = vedot<L>(a, ax ? Va : Vd);
-        const V ha = vfma(omm, h[a], even) + odd;
-        const V hb = vfma(omm, h[a + 1], even) - odd;
-        rest -= ha + hb;
-        emit(a, ha, hb);
+        for (int d = 0; d < 3; ++d) {
+            Va[d] = vfma(V(p.W1lo[kAx]), v[d], V(p.W1hi[kAx]) * v[d]);
+            Vd[d] = vfma(V(p.W1lo[kDg]), v[d], V(p.W1hi[kDg]) * v[d]);
+            if (FORCE == 1) {
+                Va[d] = vfma(V(p.w[kAx] * p.k2[kAx]), bu[d], Va[d]);
+                Vd[d] = vfma(V(p.w[kDg] * p.k2[kDg]), bu[d], Vd[d]);
+            }
+        }
+#pragma unroll
+        for (int a = 1; a < L::Q; a += 2) {
+            const bool ax = esq_of<L>(a) == 1;
+            const V eu = vedot<L>(a, ue);
+            const V g = (FORCE == 1) ? vfma(om, eu, V(2.f) * vedot<L>(a, E)) : eu;
+            const V even = vfma(ax ? cqa : cqd, eu * g, ax ? e0a : e0d);
+            const V odd = vedot<L>(a, ax ? Va : Vd);
+            const V ha = vfma(omm, h[a], even) + odd;
+            const V hb = vfma(omm, h[a + 1], even) - odd;
+            rest -= ha + hb;
+            emit(a, ha, hb);
+        }
+    } else {
+        // per shell s (index s = |e|^2): the even constant, the (e.u) coefficient and the odd vector
+        V e0[4], cqs[4], Vs[4][3];
+#pragma unroll
+        for (int sh = 1; sh <= 3; ++sh) {
+            const int r = sh == 1 ? kR1 : (sh == 2 ? kR2 : kR3);
+            if (r < 0) continue;
+            e0[sh] = V(p.w[r]) * vfma(V(p.k2[r]), Ku, c0);
+            cqs[sh] = V(p.w[r]) * cq;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                Vs[sh][d] = vfma(V(p.W1lo[r]), v[d], V(p.W1hi[r]) * v[d]);
+                if (FORCE == 1) Vs[sh][d] = vfma(V(p.w[r] * p.k2[r]), bu[d], Vs[sh][d]);
+            }
+        }
+#pragma unroll
+        for (int a = 1; a < L::Q; a += 2) {
+            const int sh = esq_of<L>(a);
+            const V eu = vedot<L>(a, ue);
+            const V g = (FORCE == 1) ? vfma(om, eu, V(2.f) * vedot<L>(a, E)) : eu;
+            const V even = vfma(cqs[sh], eu * g, e0[sh]);
+            const V odd = vedot<L>(a, Vs[sh]);
+            const V ha = vfma(omm, h[a], even) + odd;
+            const V hb = vfma(omm, h[a + 1], even) - odd;
+            rest -= ha + hb;
+            emit(a, ha, hb);
+        }
     }
     emit_rest(rest);
 }
@@ -181,6 +202,7 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
 // storage rounding alone stays near 1e-6).
 template <class L, int FORCE>
 __device__ __forceinline__ void collide_acc(const float* h, const float* E, const KParams& p, float* out) {
+    constexpr int kR1 = shell_first<L>(1), kR2 = shell_first<L>(2), kR3 = shell_first<L>(3);
     float drho = h[0], drho_lo = 0.f, j[3] = {0.f, 0.f, 0.f}, jl[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int a = 1; a < L::Q; a += 2) {
@@ -239,35 +261,41 @@ __device__ __forceinline__ void collide_acc(const float* h, const float* E, cons
         two_sum(pp, scr * F[d], vh[d], e);
         vl[d] = e + ep + om * jl[d];
     }
-    // per shell (axis, diagonal): V_s = W1_s v as a double-float product, plus
-    // the B term 2 s rho w_s k2_s (B x u) / c_s (FORCE 1) in the low part; the
+    // per shell s = |e|^2: V_s = W1_s v as a double-float product, plus the
+    // B term 2 s rho w_s k2_s (B x u) / c_s (FORCE 1) in the low part; the
     // even constant and the (e.u) coefficient, as in collide()
-    constexpr int kAx = Shells<L>::kAx, kDg = Shells<L>::diag();
-    float Vh[2][3], Vl[2][3];
+    float Vh[4][3], Vl[4][3];
 #pragma unroll
-    for (int sh = 0; sh < 2; ++sh) {
-        const int rep = sh == 0 ? kAx : kDg;
+    for (int sh = 1; sh <= 3; ++sh) {
+        const int r = sh == 1 ? kR1 : (sh == 2 ? kR2 : kR3);
+        if (r < 0) continue;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             float e;
-            two_prod(p.W1hi[rep], vh[d], Vh[sh][d], e);
-            Vl[sh][d] = e + p.W1hi[rep] * vl[d] + p.W1lo[rep] * vh[d];
-            if (FORCE == 1) Vl[sh][d] += p.w[rep] * p.k2[rep] * bu[d];
+            two_prod(p.W1hi[r], vh[d], Vh[sh][d], e);
+            Vl[sh][d] = e + p.W1hi[r] * vl[d] + p.W1lo[r] * vh[d];
+            if (FORCE == 1) Vl[sh][d] += p.w[r] * p.k2[r] * bu[d];
         }
     }
     const float u2 = ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2];
     const float c0 = om * p.A * drho_f;
     const float Ku = (FORCE == 1) ? srho * (om * u2 + 2.f * uE) : om * srho * u2;
     const float cq = (FORCE == 1) ? srho * p.Cp : om * srho * p.Cp;
-    const float e0a = p.w[kAx] * (c0 + p.k2[kAx] * Ku), e0d = p.w[kDg] * (c0 + p.k2[kDg] * Ku);
-    const float cqa = p.w[kAx] * cq, cqd = p.w[kDg] * cq;
+    float e0[4], cqs[4];
+#pragma unroll
+    for (int sh = 1; sh <= 3; ++sh) {
+        const int r = sh == 1 ? kR1 : (sh == 2 ? kR2 : kR3);
+        if (r < 0) continue;
+        e0[sh] = p.w[r] * (c0 + p.k2[r] * Ku);
+        cqs[sh] = p.w[r] * cq;
+    }
     float rest = drho, rest_lo = drho_lo;
 #pragma unroll
     for (int a = 1; a < L::Q; a += 2) {
-        const int sh = dev::esq<L>(a) == 1 ? 0 : 1;
+        const int sh = esq_of<L>(a);
         const float eu = dev::edot<L>(a, ue);
         const float g = (FORCE == 1) ? fmaf(om, eu, 2.f * dev::edot<L>(a, E)) : eu;
-        const float even = fmaf(sh == 0 ? cqa : cqd, eu * g, sh == 0 ? e0a : e0d);
+        const float even = fmaf(cqs[sh], eu * g, e0[sh]);
         // odd = e . V_s in double-float
         float oh = 0.f, ol = 0.f;
 #pragma unroll
@@ -349,7 +377,7 @@ __device__ __forceinline__ void load_E(const float* __restrict__ Ef, bool ef, co
                                        float* E) {
     if (ef) {
         E[0] = __ldg(Ef + cell);
-        E[1] = __ldg(Ef + p.N + cell);
+        E[1] = (L::D >= 2) ? __ldg(Ef + p.N + cell) : 0.f;
         E[2] = (L::D == 3) ? __ldg(Ef + 2 * p.N + cell) : 0.f;
     } else {
         E[0] = p.E[0];
@@ -750,9 +778,13 @@ int launch_storage(int vel, int force, bool efield, bool sr, const void* fin, vo
                    const float* Ef, const KParams& p, cudaStream_t s) {
     if (HAS_SR && sr) {
         if (vel == LBM_D2V9) return launch_lat<LatD2V9, S, HAS_SR>(force, efield, fin, fout, nbr, Ef, p, s);
+        if (vel == LBM_D3V27) return launch_lat<LatD3V27, S, HAS_SR>(force, efield, fin, fout, nbr, Ef, p, s);
+        if (vel == LBM_D1V3) return launch_lat<LatD1V3, S, HAS_SR>(force, efield, fin, fout, nbr, Ef, p, s);
         return launch_lat<LatD3V19, S, HAS_SR>(force, efield, fin, fout, nbr, Ef, p, s);
     }
     if (vel == LBM_D2V9) return launch_lat<LatD2V9, S, false>(force, efield, fin, fout, nbr, Ef, p, s);
+    if (vel == LBM_D3V27) return launch_lat<LatD3V27, S, false>(force, efield, fin, fout, nbr, Ef, p, s);
+    if (vel == LBM_D1V3) return launch_lat<LatD1V3, S, false>(force, efield, fin, fout, nbr, Ef, p, s);
     return launch_lat<LatD3V19, S, false>(force, efield, fin, fout, nbr, Ef, p, s);
 }
 

@@ -64,7 +64,7 @@ def _vec3(v):
 class LBM:
     """A semiclassical LBM box on the current CUDA device.
 
-    vel: "D2V9" | "D3V19"; dims: (nx, ny) or (nx, ny, nz); storage: "f32" |
+    vel: "D2V9" | "D3V19" | "D3V27" | "D1V3"; dims: (nx,), (nx, ny) or (nx, ny, nz); storage: "f32" |
     "f16" | "bf16" (deviations from the rest equilibrium, collision in FP32);
     force: "term" (explicit Lorentz term) | "shift" (velocity shift);
     stat: "fd" | "be" | "mb" weight with (theta, mu)."""
@@ -115,7 +115,7 @@ class LBM:
         _lib.check(_lib.load().lbm_constants(self._h, out, 40), self._h, "lbm_constants")
         keys = ["I0", "I2", "I4", "c0", "c1", "c2", "cbar2", "cprime2", "thetabar", "J2", "Delta2", "cs"]
         c = dict(zip(keys, list(out)[:12]))
-        q = 9 if self.vel == "D2V9" else 19
+        q = self.Q
         c["w"] = np.array(list(out)[12: 12 + q])
         return c
 
