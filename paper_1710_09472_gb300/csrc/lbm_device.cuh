@@ -67,11 +67,6 @@ __device__ __forceinline__ float edot(int a, const float* v) {
     return r;
 }
 
-template <class L>
-__device__ __forceinline__ constexpr int esq(int a) {
-    return L::c(a, 0) * L::c(a, 0) + L::c(a, 1) * L::c(a, 1) + L::c(a, 2) * L::c(a, 2);
-}
-
 __device__ __forceinline__ void cross3(const float* a, const float* b, float* c) {
     c[0] = a[1] * b[2] - a[2] * b[1];
     c[1] = a[2] * b[0] - a[0] * b[2];
