@@ -20,7 +20,7 @@ def _moments(m, f):
     return rho, j, P
 
 
-@pytest.mark.parametrize("vel", ["D2V9", "D3V19"])
+@pytest.mark.parametrize("vel", ["D1V3", "D2V9", "D3V19", "D3V27"])
 def test_equilibrium_moments(vel):
     """sum f^eq = rho, sum f^eq xi = rho u, sum f^eq xi xi = rho (thetabar delta + u u)
     (Sec. 2 Eqs. rho-def-eq, vel-def-eq, theta-bar-def-eq; Sec. 6 pi_ij)."""
@@ -41,7 +41,7 @@ def test_equilibrium_moments(vel):
         assert np.max(np.abs(P - expect)) < 1e-14
 
 
-@pytest.mark.parametrize("vel", ["D2V9", "D3V19"])
+@pytest.mark.parametrize("vel", ["D1V3", "D2V9", "D3V19", "D3V27"])
 def test_equilibrium_printed_forms_agree(vel):
     """The reduced EDF the paper simulates (Sec. 9.1) equals the full second-order
     EDF (Sec. 4, Eq. edf-second-order-exp-eq, discrete) with thetabar = I2/I0, and
@@ -88,12 +88,13 @@ def test_hermite_limit_is_textbook_bgk():
         assert np.max(np.abs(f - textbook)) < 1e-14
 
 
-@pytest.mark.parametrize("vel", ["D2V9", "D3V19"])
+@pytest.mark.parametrize("vel", ["D1V3", "D2V9", "D3V19", "D3V27"])
 def test_force_term_moments(vel):
     """Sec. 7: the explicit term conserves mass and injects momentum rho a;
     for the magnetic part rho (u x B) via the identity J2 Delta2^2 -
-    (D+2)(Delta2^2 - 1)/D = 1 (Eq. force-eq1, force-eq2)."""
-    m = oracle.Model(vel, "fd", THETA, 1.0, tau=0.8, B=(0.0, 0.0, 3e-3) if vel == "D2V9" else (1e-3, -2e-3, 3e-3))
+    (D+2)(Delta2^2 - 1)/D = 1 (Eq. force-eq1, force-eq2).  In 1D only E_x acts."""
+    B = {"D1V3": (0.0, 0.0, 0.0), "D2V9": (0.0, 0.0, 3e-3)}.get(vel, (1e-3, -2e-3, 3e-3))
+    m = oracle.Model(vel, "fd", THETA, 1.0, tau=0.8, B=B)
     D = m.D
     r = _rng()
     for _ in range(10):
