@@ -435,11 +435,12 @@ __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict
 //    block of consecutive slots per neighbouring row, at most 9 copies), its
 //    cell order and its ranges of the link buffer and of the link
 //    descriptors arrive by bulk asynchronous copies into a ring of STAGES
-//    stages, STAGES - 1 rows ahead of the row being computed.  One thread, lane 0 of the last warp,
-//    arms the stage's mbarrier with the byte count and issues the copies.  A
-//    bulk copy holds its issuing thread for many cycles, so the issuer is the
-//    warp with the least cell work (the order puts the solid cells, and the
-//    cells of a second pass, on the first warps);
+//    stages, STAGES - 1 rows ahead of the row being computed.  One thread,
+//    lane 0 of the last warp, arms the stage's mbarrier with the byte count
+//    and issues the copies.  A bulk copy holds its issuing thread for many
+//    cycles, so the issuer is the warp with the least cell work (the order
+//    puts the solid cells, and the cells of a second pass, on the first
+//    warps);
 //  - one pass over the row's links writes each bounced value f*_b(x) into the
 //    staged slot that the pull of direction bbar at x reads (the slot of the
 //    solid neighbour), so the cells pull without link logic;
