@@ -57,3 +57,24 @@ def test_library_weight_integrals_host_only(D, fname):
     assert abs(I[0] ** -0.5 / g["c0"] - 1) < 1e-14
     assert abs(I[1] ** -0.5 / g["c1"] - 1) < 1e-14
     assert abs(I[2] ** -0.5 / g["c2"] - 1) < 1e-14
+
+
+def _enum_values(name):
+    """{enumerator: value} of the typedef enum `name` in include/lbm.h."""
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    m = re.search(r"typedef enum\s*\{([^}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    return {k: int(v) for k, v in re.findall(r"(LBM_[A-Z0-9_]+)\s*=\s*(\d+)", m.group(1))}
+
+
+def test_binding_enums_match_header():
+    """The binding's name -> value tables use the header's enumerator values."""
+    from paper_1710_09472_gb300 import _lib
+
+    vel = _enum_values("lbm_velset")
+    assert {f"LBM_{k}": v for k, v in _lib.VEL.items()} == vel
+    stat = _enum_values("lbm_stat")
+    assert {f"LBM_{k.upper()}": v for k, v in _lib.STAT.items()} == stat
+    force = _enum_values("lbm_force")
+    assert {f"LBM_FORCE_{k.upper()}": v for k, v in _lib.FORCE.items()} == force
