@@ -17,6 +17,20 @@ int launch_adjoint_step_f16(int, int, bool, bool, const void*, const float*, flo
 int launch_adjoint_step_bf16(int, int, bool, bool, const void*, const float*, float*, const uint32_t*, const float*,
                              const float*, const float*, double*, double*, const KParams&, cudaStream_t);
 
+// the same for D3V27 and D1V3 (lbm_adjoint_*_x.cu)
+int launch_adjoint_seed_f32_x(int, const void*, const uint32_t*, const float*, const float*, float*, double*, bool,
+                              const KParams&, cudaStream_t);
+int launch_adjoint_step_f32_x(int, int, bool, bool, const void*, const float*, float*, const uint32_t*, const float*,
+                              const float*, const float*, double*, double*, const KParams&, cudaStream_t);
+int launch_adjoint_seed_f16_x(int, const void*, const uint32_t*, const float*, const float*, float*, double*, bool,
+                              const KParams&, cudaStream_t);
+int launch_adjoint_step_f16_x(int, int, bool, bool, const void*, const float*, float*, const uint32_t*, const float*,
+                              const float*, const float*, double*, double*, const KParams&, cudaStream_t);
+int launch_adjoint_seed_bf16_x(int, const void*, const uint32_t*, const float*, const float*, float*, double*, bool,
+                               const KParams&, cudaStream_t);
+int launch_adjoint_step_bf16_x(int, int, bool, bool, const void*, const float*, float*, const uint32_t*, const float*,
+                               const float*, const float*, double*, double*, const KParams&, cudaStream_t);
+
 int64_t adjoint_slot_count(const KParams& p) {
     Launch l = adjk::grid_of(p);
     return (int64_t)l.grid.x * l.grid.y * adjk::kSlots;
@@ -25,6 +39,13 @@ int64_t adjoint_slot_count(const KParams& p) {
 int launch_adjoint_seed(int vel, int storage, const void* P, const uint32_t* nbr, const float* w_rho,
                         const float* w_j, float* lam, double* slots, bool in_window, const KParams& p,
                         cudaStream_t s) {
+    if (vel == LBM_D3V27 || vel == LBM_D1V3) {
+        if (storage == LBM_F16_DEV)
+            return launch_adjoint_seed_f16_x(vel, P, nbr, w_rho, w_j, lam, slots, in_window, p, s);
+        if (storage == LBM_BF16_DEV)
+            return launch_adjoint_seed_bf16_x(vel, P, nbr, w_rho, w_j, lam, slots, in_window, p, s);
+        return launch_adjoint_seed_f32_x(vel, P, nbr, w_rho, w_j, lam, slots, in_window, p, s);
+    }
     if (storage == LBM_F16_DEV) return launch_adjoint_seed_f16(vel, P, nbr, w_rho, w_j, lam, slots, in_window, p, s);
     if (storage == LBM_BF16_DEV)
         return launch_adjoint_seed_bf16(vel, P, nbr, w_rho, w_j, lam, slots, in_window, p, s);
@@ -35,6 +56,16 @@ int launch_adjoint_step(int vel, int storage, int force, bool efield, bool in_wi
                         const float* lam_in, float* lam_out, const uint32_t* nbr, const float* Ef,
                         const float* w_rho, const float* w_j, double* gE, double* slots, const KParams& p,
                         cudaStream_t s) {
+    if (vel == LBM_D3V27 || vel == LBM_D1V3) {
+        if (storage == LBM_F16_DEV)
+            return launch_adjoint_step_f16_x(vel, force, efield, in_window, P, lam_in, lam_out, nbr, Ef, w_rho, w_j,
+                                             gE, slots, p, s);
+        if (storage == LBM_BF16_DEV)
+            return launch_adjoint_step_bf16_x(vel, force, efield, in_window, P, lam_in, lam_out, nbr, Ef, w_rho, w_j,
+                                              gE, slots, p, s);
+        return launch_adjoint_step_f32_x(vel, force, efield, in_window, P, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE,
+                                         slots, p, s);
+    }
     if (storage == LBM_F16_DEV)
         return launch_adjoint_step_f16(vel, force, efield, in_window, P, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE,
                                        slots, p, s);

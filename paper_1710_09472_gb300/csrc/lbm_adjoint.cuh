@@ -692,12 +692,16 @@ inline Launch grid_of(const KParams& p) {
     return l;
 }
 
-template <class F>
+// GROUP 0: D2V9 and D3V19; GROUP 1: D3V27 and D1V3 (separate translation units)
+template <int GROUP, class F>
 int dispatch_lattice(int vel, F&& f) {
-    if (vel == LBM_D2V9) return f(LatD2V9{});
-    if (vel == LBM_D3V27) return f(LatD3V27{});
-    if (vel == LBM_D1V3) return f(LatD1V3{});
-    return f(LatD3V19{});
+    if constexpr (GROUP == 0) {
+        if (vel == LBM_D2V9) return f(LatD2V9{});
+        return f(LatD3V19{});
+    } else {
+        if (vel == LBM_D1V3) return f(LatD1V3{});
+        return f(LatD3V27{});
+    }
 }
 
 
@@ -769,23 +773,25 @@ template <class L, class S, int FORCE, bool EF, bool WIN>
 bool launch_rows(const void* P, const float* lam_in, float* lam_out, const uint32_t* nbr, const float* Ef,
                  const float* w_rho, const float* w_j, double* gE, double* slots, int64_t slot_blocks,
                  const KParams& p, cudaStream_t s) {
-    if (p.nx == 256)
-        return launch_rows_rs<L, S, FORCE, EF, WIN, 256>(P, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE, slots,
-                                                          slot_blocks, p, s);
-    if (p.nx == 512)
-        return launch_rows_rs<L, S, FORCE, EF, WIN, 512>(P, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE, slots,
-                                                          slot_blocks, p, s);
+    // the compile-time strides only for the benchmarked lattices (D2V9, D3V19)
+    constexpr bool kFixed = L::Q == 9 || L::Q == 19;
+    if (kFixed && p.nx == 256)
+        return launch_rows_rs<L, S, FORCE, EF, WIN, kFixed ? 256 : 0>(P, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE,
+                                                                       slots, slot_blocks, p, s);
+    if (kFixed && p.nx == 512)
+        return launch_rows_rs<L, S, FORCE, EF, WIN, kFixed ? 512 : 0>(P, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE,
+                                                                       slots, slot_blocks, p, s);
     return launch_rows_rs<L, S, FORCE, EF, WIN, 0>(P, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE, slots, slot_blocks,
                                                     p, s);
 }
 
 // Launchers for one storage type (instantiated in one translation unit per
 // storage).
-template <class S>
+template <class S, int GROUP>
 int seed_storage(int vel, const void* P, const uint32_t* nbr, const float* w_rho, const float* w_j, float* lam,
                  double* slots, bool in_window, const KParams& p, cudaStream_t s) {
     Launch l = grid_of(p);
-    return dispatch_lattice(vel, [&](auto lat) {
+    return dispatch_lattice<GROUP>(vel, [&](auto lat) {
         using L = decltype(lat);
         k_adjoint_seed<L, S><<<l.grid, l.block, 0, s>>>((const typename S::T*)P, nbr, w_rho, w_j, lam, slots,
                                                        in_window ? 1 : 0, p);
@@ -793,13 +799,13 @@ int seed_storage(int vel, const void* P, const uint32_t* nbr, const float* w_rho
     });
 }
 
-template <class S>
+template <class S, int GROUP>
 int step_storage(int vel, int force, bool efield, bool in_window, const void* P, const float* lam_in,
                  float* lam_out, const uint32_t* nbr, const float* Ef, const float* w_rho, const float* w_j,
                  double* gE, double* slots, const KParams& p, cudaStream_t s) {
     Launch l = grid_of(p);
     const int64_t slot_blocks = (int64_t)l.grid.x * l.grid.y;
-    return dispatch_lattice(vel, [&](auto lat) {
+    return dispatch_lattice<GROUP>(vel, [&](auto lat) {
         using L = decltype(lat);
         const auto* Pt = (const typename S::T*)P;
 #define LBM_ADJ(F, EFV, W)                                                                                    \

@@ -118,24 +118,64 @@ __host__ __device__ constexpr int pop_key(int a) {
     return (L::c(a, 1) + 1) * 3 + (L::c(a, 2) + 1);
 }
 template <class L>
-__host__ __device__ constexpr int pop_slot(int a) {
+__host__ __device__ constexpr int pop_slot_calc(int a) {
     int s = 0;
     for (int b = 0; b < L::Q; ++b)
         if (pop_key<L>(b) < pop_key<L>(a) || (pop_key<L>(b) == pop_key<L>(a) && b < a)) ++s;
     return s;
 }
-// first slot and number of directions with key k (0 .. 8)
+// the slots as a table built at compile time, so that a use with a known
+// direction folds to a constant without re-running the count (for the
+// 27-direction lattice, whose unrolled counts made compilation slow)
+template <class L>
+struct SlotTable {
+    int s[L::Q];
+    __host__ __device__ constexpr SlotTable() : s() {
+        for (int a = 0; a < L::Q; ++a) s[a] = pop_slot_calc<L>(a);
+    }
+};
+template <class L>
+__host__ __device__ constexpr int pop_slot(int a) {
+    if constexpr (L::Q > 19) {
+        constexpr SlotTable<L> t{};
+        return t.s[a];
+    } else {
+        return pop_slot_calc<L>(a);
+    }
+}
+// first slot and number of directions with key k (0 .. 8), tabulated at compile time
+template <class L>
+struct KeyTable {
+    int first[9], count[9];
+    __host__ __device__ constexpr KeyTable() : first(), count() {
+        for (int k = 0; k < 9; ++k)
+            for (int b = 0; b < L::Q; ++b) {
+                first[k] += pop_key<L>(b) < k ? 1 : 0;
+                count[k] += pop_key<L>(b) == k ? 1 : 0;
+            }
+    }
+};
 template <class L>
 __host__ __device__ constexpr int key_first(int k) {
-    int s = 0;
-    for (int b = 0; b < L::Q; ++b) s += pop_key<L>(b) < k ? 1 : 0;
-    return s;
+    if constexpr (L::Q > 19) {
+        constexpr KeyTable<L> t{};
+        return t.first[k];
+    } else {
+        int s = 0;
+        for (int b = 0; b < L::Q; ++b) s += pop_key<L>(b) < k ? 1 : 0;
+        return s;
+    }
 }
 template <class L>
 __host__ __device__ constexpr int key_count(int k) {
-    int s = 0;
-    for (int b = 0; b < L::Q; ++b) s += pop_key<L>(b) == k ? 1 : 0;
-    return s;
+    if constexpr (L::Q > 19) {
+        constexpr KeyTable<L> t{};
+        return t.count[k];
+    } else {
+        int s = 0;
+        for (int b = 0; b < L::Q; ++b) s += pop_key<L>(b) == k ? 1 : 0;
+        return s;
+    }
 }
 // slot(a) for a direction known only at run time: 5 bits per direction,
 // directions 12 k .. 12 k + 11 in word k
@@ -143,7 +183,7 @@ template <class L>
 __host__ __device__ constexpr unsigned long long packed_slots(int word) {
     unsigned long long v = 0;
     for (int a = 12 * word; a < L::Q && a < 12 * (word + 1); ++a)
-        v |= (unsigned long long)pop_slot<L>(a) << (5 * (a - 12 * word));
+        v |= (unsigned long long)pop_slot_calc<L>(a) << (5 * (a - 12 * word));
     return v;
 }
 template <class L>
@@ -290,6 +330,13 @@ int launch_step_f16(int vel, int force, bool efield, bool sr, const void* fin, v
                     const float* Ef, const KParams& p, cudaStream_t s);
 int launch_step_bf16(int vel, int force, bool efield, bool sr, const void* fin, void* fout, const uint32_t* nbr,
                      const float* Ef, const KParams& p, cudaStream_t s);
+// the same for D3V27 and D1V3 (translation units lbm_step_*_x.cu)
+int launch_step_f32_x(int vel, int force, bool efield, bool sr, const void* fin, void* fout, const uint32_t* nbr,
+                      const float* Ef, const KParams& p, cudaStream_t s);
+int launch_step_f16_x(int vel, int force, bool efield, bool sr, const void* fin, void* fout, const uint32_t* nbr,
+                      const float* Ef, const KParams& p, cudaStream_t s);
+int launch_step_bf16_x(int vel, int force, bool efield, bool sr, const void* fin, void* fout, const uint32_t* nbr,
+                       const float* Ef, const KParams& p, cudaStream_t s);
 int launch_moments(int vel, int storage, const void* pop, const uint32_t* nbr, float* rho, float* j,
                    double* partials, int64_t* n_partials, const KParams& p, cudaStream_t s);
 int launch_reduce_partials(const double* partials, int64_t n_partials, double* out4, cudaStream_t s);

@@ -435,6 +435,11 @@ int launch_init(int vel, int storage, void* pop, const uint32_t* nbr, const floa
 
 int launch_step(int vel, int storage, int force, bool efield, bool sr, const void* fin, void* fout,
                 const uint32_t* nbr, const float* Ef, const KParams& p, cudaStream_t s) {
+    if (vel == LBM_D3V27 || vel == LBM_D1V3) {
+        if (storage == LBM_F16_DEV) return launch_step_f16_x(vel, force, efield, sr, fin, fout, nbr, Ef, p, s);
+        if (storage == LBM_BF16_DEV) return launch_step_bf16_x(vel, force, efield, sr, fin, fout, nbr, Ef, p, s);
+        return launch_step_f32_x(vel, force, efield, false, fin, fout, nbr, Ef, p, s);
+    }
     if (storage == LBM_F16_DEV) return launch_step_f16(vel, force, efield, sr, fin, fout, nbr, Ef, p, s);
     if (storage == LBM_BF16_DEV) return launch_step_bf16(vel, force, efield, sr, fin, fout, nbr, Ef, p, s);
     return launch_step_f32(vel, force, efield, false, fin, fout, nbr, Ef, p, s);

@@ -751,10 +751,13 @@ int launch_one(const void* fin, void* fout, const uint32_t* nbr, const float* Ef
     using T = typename S::T;
     const S* tag = nullptr;
     bool done;
-    if (p.nx == 256)
-        done = launch_rows<L, S, FORCE, EF, SR, 256>(tag, fin, fout, nbr, Ef, p, s);
-    else if (p.nx == 512)
-        done = launch_rows<L, S, FORCE, EF, SR, 512>(tag, fin, fout, nbr, Ef, p, s);
+    // the compile-time strides only for the benchmarked lattices (D2V9, D3V19);
+    // the others take the run-time stride (fewer instantiations to compile)
+    constexpr bool kFixed = L::Q == 9 || L::Q == 19;
+    if (kFixed && p.nx == 256)
+        done = launch_rows<L, S, FORCE, EF, SR, kFixed ? 256 : 0>(tag, fin, fout, nbr, Ef, p, s);
+    else if (kFixed && p.nx == 512)
+        done = launch_rows<L, S, FORCE, EF, SR, kFixed ? 512 : 0>(tag, fin, fout, nbr, Ef, p, s);
     else
         done = launch_rows<L, S, FORCE, EF, SR, 0>(tag, fin, fout, nbr, Ef, p, s);
     if (done) return 1;
@@ -774,19 +777,26 @@ int launch_lat(int force, bool efield, const void* fin, void* fout, const uint32
                   : launch_one<L, S, 1, false, SR>(fin, fout, nbr, Ef, p, s);
 }
 
-template <class S, bool HAS_SR>
+// GROUP 0: D2V9 and D3V19; GROUP 1: D3V27 and D1V3 (compiled in translation
+// units of their own, so that the build runs them in parallel)
+template <class S, bool HAS_SR, int GROUP>
 int launch_storage(int vel, int force, bool efield, bool sr, const void* fin, void* fout, const uint32_t* nbr,
                    const float* Ef, const KParams& p, cudaStream_t s) {
-    if (HAS_SR && sr) {
-        if (vel == LBM_D2V9) return launch_lat<LatD2V9, S, HAS_SR>(force, efield, fin, fout, nbr, Ef, p, s);
-        if (vel == LBM_D3V27) return launch_lat<LatD3V27, S, HAS_SR>(force, efield, fin, fout, nbr, Ef, p, s);
-        if (vel == LBM_D1V3) return launch_lat<LatD1V3, S, HAS_SR>(force, efield, fin, fout, nbr, Ef, p, s);
-        return launch_lat<LatD3V19, S, HAS_SR>(force, efield, fin, fout, nbr, Ef, p, s);
+    if constexpr (GROUP == 0) {
+        if (HAS_SR && sr) {
+            if (vel == LBM_D2V9) return launch_lat<LatD2V9, S, HAS_SR>(force, efield, fin, fout, nbr, Ef, p, s);
+            return launch_lat<LatD3V19, S, HAS_SR>(force, efield, fin, fout, nbr, Ef, p, s);
+        }
+        if (vel == LBM_D2V9) return launch_lat<LatD2V9, S, false>(force, efield, fin, fout, nbr, Ef, p, s);
+        return launch_lat<LatD3V19, S, false>(force, efield, fin, fout, nbr, Ef, p, s);
+    } else {
+        if (HAS_SR && sr) {
+            if (vel == LBM_D1V3) return launch_lat<LatD1V3, S, HAS_SR>(force, efield, fin, fout, nbr, Ef, p, s);
+            return launch_lat<LatD3V27, S, HAS_SR>(force, efield, fin, fout, nbr, Ef, p, s);
+        }
+        if (vel == LBM_D1V3) return launch_lat<LatD1V3, S, false>(force, efield, fin, fout, nbr, Ef, p, s);
+        return launch_lat<LatD3V27, S, false>(force, efield, fin, fout, nbr, Ef, p, s);
     }
-    if (vel == LBM_D2V9) return launch_lat<LatD2V9, S, false>(force, efield, fin, fout, nbr, Ef, p, s);
-    if (vel == LBM_D3V27) return launch_lat<LatD3V27, S, false>(force, efield, fin, fout, nbr, Ef, p, s);
-    if (vel == LBM_D1V3) return launch_lat<LatD1V3, S, false>(force, efield, fin, fout, nbr, Ef, p, s);
-    return launch_lat<LatD3V19, S, false>(force, efield, fin, fout, nbr, Ef, p, s);
 }
 
 }  // namespace stepk
