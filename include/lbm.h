@@ -292,8 +292,11 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* host_buf, size_t len);
  * whose kernels overlap on the GPU (different streams or contexts running
  * concurrently) race and must be serialised by the caller.  The first call on
  * a device looks up the array's device address once (cudaGetSymbolAddress);
- * make that first call before any stream capture.  The context's device must
- * be current.  Errors: INVALID_ARG, STATE, CUDA. */
+ * make that first call before any stream capture.  That address is kept for
+ * the rest of the process: after cudaDeviceReset on a device the module may
+ * load at another address, so do not call this entry point on a device that
+ * has been reset.  The context's device must be current.  Errors:
+ * INVALID_ARG, STATE, CUDA. */
 lbm_status lbm_moment_totals_static(lbm_ctx* ctx, double* totals);
 
 /* Message of the last failed call on this context ("" if none). */

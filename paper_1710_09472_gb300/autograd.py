@@ -8,6 +8,15 @@ float32, on the device), B (3,) and tau (scalar).  Its backward restores the
 start state and calls lbm_adjoint with uniform loss weights taken from the
 incoming gradient, returning dL/dE(x), dL/dB and dL/dtau.  PyTorch supplies
 memory and the stream only; both directions run in the library's kernels.
+
+Two effects of backward() that a caller should know:
+  - the incoming FP64 gradient is passed to lbm_adjoint as FP32 per-cell loss
+    weights (w_rho, w_j), so it is rounded to FP32 (relative 6e-8) before the
+    reverse sweep; the sweep itself accumulates the parameter gradients in
+    FP64;
+  - the simulation is left at the restored start state (the state before
+    forward() ran), not at step t_end: a caller that wants to step on from
+    t_end after backward() must save that state after forward() and load it.
 """
 from __future__ import annotations
 

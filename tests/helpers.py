@@ -8,11 +8,17 @@ import oracle
 
 THETA = 1.0 / 270.0
 
-# Tolerances on rho and j after a run (relative L-inf: max|a-b| / max|b|).
-# FP32 and FP16-deviation storage: the targets 1e-5 and 2e-3.  BF16 keeps 8
-# mantissa bits, so one rounding of a stored deviation is already up to
-# 2^-9 = 2e-3 of it; BF16 is held to 1.5e-2 and its measured error reported.
-TOL = {"f32": 1e-5, "f16": 2e-3, "bf16": 1.5e-2}
+# Tolerances on rho and j after a run (relative L-inf: max|a-b| / max|b|):
+# FP32 storage 1e-5, FP16/BF16-deviation storage 2e-3.  Where the 16-bit
+# format itself cannot reach 2e-3 on a case, the bound is 1.25 times the error
+# of the FP64 oracle whose stored deviations are rounded to that format after
+# every step (storage_floor below), computed in the same test.
+TOL = {"f32": 1e-5, "f16": 2e-3, "bf16": 2e-3}
+FLOOR_FACTOR = 1.25
+
+# Scale of the stored deviation: FP16 keeps 2^12 (f - f0) so that |h| stays in
+# the normal range; BF16 and FP32 keep f - f0.
+STORE_SCALE = {"f32": 1.0, "f16": 4096.0, "bf16": 1.0}
 
 
 def rel_linf(a, b) -> float:
@@ -55,3 +61,191 @@ def oracle_run(vel, shape, solid, tau, steps, force="term", E=(0, 0, 0), B=(0, 0
     m.step(shape, solid, f, steps, None if Efield is None else np.asarray(Efield, dtype=np.float64))
     r, j, tot = m.moments(shape, solid, f)
     return r, j, tot, m, f
+
+
+# ---------------------------------------------------------------------------
+# Format floor of 16-bit deviation storage.  The GPU keeps each post-collision
+# value once per step as h~ = scale (f - f0), f0 = rho0 w_a / I0, rounded to
+# FP16 or BF16 (stochastically by default).  The oracle's state after a step is
+# the post-stream permutation of those values (bounce-back copies them too), so
+# rounding the oracle's state elementwise after every step applies the same
+# roundings.  The initial equilibrium is stored with round-to-nearest.
+# ---------------------------------------------------------------------------
+def round_f16(x, rng=None):
+    """FP64 -> FP32 -> FP16 (nearest even, or stochastic when rng is given:
+    up in magnitude with probability equal to the dropped fraction)."""
+    x32 = np.asarray(x, dtype=np.float64).astype(np.float32)
+    t = x32.astype(np.float16)
+    if rng is None:
+        return t.astype(np.float64)
+    tf = t.astype(np.float32)
+    below = tf < x32  # nearest is below x: the other neighbour is above
+    other = np.where(below, np.nextafter(t, np.float16(np.inf)), np.nextafter(t, np.float16(-np.inf)))
+    of = other.astype(np.float32)
+    lo = np.where(below, tf, of).astype(np.float64)
+    hi = np.where(below, of, tf).astype(np.float64)
+    x64 = x32.astype(np.float64)
+    exact = tf == x32
+    width = np.where(exact, 1.0, hi - lo)
+    p_hi = np.where(exact, 0.0, (x64 - lo) / width)
+    out = np.where(rng.random(x64.shape) < p_hi, hi, lo)
+    return np.where(exact, x64, out)
+
+
+def round_bf16(x, rng=None):
+    """FP64 -> FP32 -> BF16 (the high 16 bits of FP32): nearest even, or
+    stochastic (the magnitude moves up one BF16 ulp with probability equal to
+    the dropped low 16 bits / 2^16)."""
+    x32 = np.ascontiguousarray(np.asarray(x, dtype=np.float64).astype(np.float32))
+    b = x32.view(np.uint32).astype(np.uint64)
+    low = b & 0xFFFF
+    trunc = b & 0xFFFF0000
+    if rng is None:
+        up = (low > 0x8000) | ((low == 0x8000) & ((trunc >> 16) & 1 == 1))
+    else:
+        up = rng.random(x32.shape) * 65536.0 < low
+    out = (trunc + np.where(up, 0x10000, 0)).astype(np.uint32)
+    return out.view(np.float32).astype(np.float64)
+
+
+def storage_floor(vel, shape, solid, tau, steps, storage, force="term", E=(0, 0, 0), B=(0, 0, 0), rho=None,
+                  u=None, Efield=None, seed=12345, reference=None, stat="fd", theta=THETA, mu=1.0):
+    """Relative L-inf error (rho, j) of the FP64 oracle whose stored deviations
+    are rounded to `storage` (stochastic rounding, seeded) after every step,
+    against the unrounded oracle `reference` = (rho, j) of the same case."""
+    rnd = {"f16": round_f16, "bf16": round_bf16}[storage]
+    s = STORE_SCALE[storage]
+    rng = np.random.default_rng(seed)
+    m = oracle.Model(vel, stat, theta, mu, tau=tau, E=E, B=B, force=force)
+    rho0 = np.ones(shape) if rho is None else np.asarray(rho, dtype=np.float64)
+    f = m.init_equilibrium(shape, solid, rho0, None if u is None else np.asarray(u, dtype=np.float64))
+    N = int(np.prod(shape))
+    f0 = (m.w / m.const["I0"])[:, None]
+    fluid = np.ones(N, dtype=bool) if solid is None else (np.asarray(solid).reshape(N) == 0)
+    f2 = f.reshape(m.Q, N)
+    f2[:, fluid] = f0 + rnd(s * (f2[:, fluid] - f0)) / s
+    Ef = None if Efield is None else np.asarray(Efield, dtype=np.float64)
+    for _ in range(steps):
+        m.step(shape, solid, f, 1, Ef)
+        f2[:, fluid] = f0 + rnd(s * (f2[:, fluid] - f0), rng) / s
+    r, j, _ = m.moments(shape, solid, f)
+    if reference is None:
+        ro, jo, _, _, _ = oracle_run(vel, shape, solid, tau, steps, force, E, B, rho, u, Efield)
+    else:
+        ro, jo = reference
+    return rel_linf(r, ro), rel_linf(j, jo)
+
+
+def bound_16bit(storage, floor):
+    """The 2e-3 target where the format reaches it; otherwise 1.25 x the
+    format floor of the same case."""
+    if storage == "f32":
+        return TOL["f32"]
+    return TOL[storage] if floor < TOL[storage] else FLOOR_FACTOR * floor
+
+
+def check_storage_error(storage, errs, floor_args, seeds=(1, 2, 3), label=""):
+    """Assert the GPU's (rho, j) errors against the storage's bound.
+
+    FP32: 1e-5.  FP16/BF16: 2e-3 where the error is within it; otherwise the
+    format floor of the same case (storage_floor, the largest over `seeds`) is
+    computed and the bound is 2e-3 if that floor is below 2e-3 (the format
+    reaches the target, so the GPU must too) and 1.25 x the floor otherwise.
+    floor_args: the keyword arguments of storage_floor for this case.
+    Returns (bound, floor or None) for the caller's report."""
+    er, ej = errs
+    if storage == "f32" or max(er, ej) <= TOL[storage]:
+        assert er <= TOL[storage] and ej <= TOL[storage], (label, storage, er, ej)
+        return TOL[storage], None
+    floors = [storage_floor(storage=storage, seed=sd, **floor_args) for sd in seeds]
+    fr = max(f[0] for f in floors)
+    fj = max(f[1] for f in floors)
+    br, bj = bound_16bit(storage, fr), bound_16bit(storage, fj)
+    print(f"{label} {storage}: rho {er:.3e} (floor {fr:.3e}, bound {br:.3e}) j {ej:.3e} (floor {fj:.3e}, "
+          f"bound {bj:.3e})")
+    assert er <= br and ej <= bj, (label, storage, er, ej, fr, fj)
+    return (br, bj), (fr, fj)
+
+
+# ---------------------------------------------------------------------------
+# Checks at full problem sizes, where the oracle cannot run the whole box.
+# ---------------------------------------------------------------------------
+def deviations_on_device(sim):
+    """The stored deviations h_a(x) = f_a(x) - f0_a as a [Q, N] FP32 device tensor."""
+    import torch
+
+    h = torch.empty(sim.Q * sim.N, dtype=torch.float32, device="cuda")
+    sim.populations(h, deviation=True)
+    return h.view(sim.Q, sim.N)
+
+
+def one_step_sampled(m, dims, solid_flat, h_t, h_t1, cells, E_cell=None):
+    """Collide-and-stream by the oracle at sampled fluid cells.
+
+    h_t, h_t1: [Q, N] device tensors of the stored deviations before and after
+    one GPU step.  For each sampled cell x the oracle collides f(x - e_a, t)
+    (or f(x, t) when x - e_a is solid: halfway bounce-back) and the expected
+    f_a(x, t + 1) is compared with the GPU's.  Returns (max abs error, max abs
+    expected deviation)."""
+    import torch
+
+    nx, ny, nz = dims
+    Q = m.Q
+    f0 = m.w / m.const["I0"]
+    src_cells = set()
+    plan = []
+    for cell in cells:
+        x, y, z = cell % nx, (cell // nx) % ny, cell // (nx * ny)
+        row = []
+        for a in range(Q):
+            ex, ey, ez = m.e[a]
+            src = (((z - ez) % nz) * ny + (y - ey) % ny) * nx + (x - ex) % nx
+            if solid_flat[src]:
+                row.append((cell, m.opp[a]))
+                src_cells.add(cell)
+            else:
+                row.append((src, a))
+                src_cells.add(src)
+        plan.append(row)
+    src_list = np.array(sorted(src_cells), dtype=np.int64)
+    idx = torch.from_numpy(src_list).cuda()
+    before = h_t[:, idx].cpu().numpy().astype(np.float64)
+    after = h_t1[:, torch.from_numpy(np.asarray(cells, dtype=np.int64)).cuda()].cpu().numpy().astype(np.float64)
+    col = {int(c): k for k, c in enumerate(src_list)}
+    post = {}
+    err = 0.0
+    scale = 0.0
+    for k, row in enumerate(plan):
+        expect = np.empty(Q)
+        for a, (sc, comp) in enumerate(row):
+            if sc not in post:
+                E = None if E_cell is None else E_cell(sc)
+                post[sc] = m.collide_cell(before[:, col[sc]] + f0, E) - f0
+            expect[a] = post[sc][comp]
+        err = max(err, float(np.max(np.abs(after[:, k] - expect))))
+        scale = max(scale, float(np.max(np.abs(expect))))
+    return err, scale
+
+
+def light_cone_oracle(m, solid, corner, block, steps, Efield=None):
+    """FP64 oracle moments (rho, j) on a block of cells after `steps` steps of
+    a periodic box that starts at rest (rho0 = 1), computed on a sub-box only.
+
+    The sub-box holds the block plus a margin of steps + 1 cells on every
+    side, wrapped periodically from the full mask.  Its own periodic wrap is
+    wrong only at its edges, and the error moves inward one cell per step, so
+    after `steps` steps the block still holds exactly the full box's values.
+    corner: the block's first (z, y, x); block: its edge in cells."""
+    margin = steps + 1
+    D = solid.ndim
+    idx = [np.arange(corner[d] - margin, corner[d] + block + margin) % solid.shape[d] for d in range(D)]
+    sub = np.ascontiguousarray(solid[np.ix_(*idx)])
+    shape = sub.shape
+    Ef = None
+    if Efield is not None:
+        Ef = np.ascontiguousarray(Efield[(slice(None),) + np.ix_(*idx)], dtype=np.float64)
+    f = m.init_equilibrium(shape, sub, np.ones(shape))
+    m.step(shape, sub, f, steps, Ef)
+    r, j, _ = m.moments(shape, sub, f)
+    inner = tuple(slice(margin, margin + block) for _ in range(D))
+    return r[inner], j[(slice(None),) + inner], sub[inner]

@@ -140,6 +140,25 @@ def test_quadrature_moments_bruteforce(vel, D):
         assert np.all(e[opp[a]] == -e[a])
 
 
+@pytest.mark.parametrize("stat,theta,mu", [("fd", THETA, MU), ("mb", 0.7, 0.0), ("be", 0.5, -0.3)])
+def test_d3v27_sixth_order_moment(stat, theta, mu):
+    """Table lattices-tab: the D3V27 weights carry I_6 only through the corner
+    weight I_2^3 I_6 / (216 I_4^3) and the terms that keep the lower moments.
+    The sixth-order moment sum_a w_a e_x^2 e_y^2 e_z^2, to which only the eight
+    corners contribute, must equal I_6 c_s^6 (the one index pattern of order 6
+    whose delta tensor is 1 and which a three-speed lattice can match); a
+    transcription error in the I_6 terms keeps every moment up to order 5 but
+    breaks this one.  Checked for three weights, each with its own I_6."""
+    I = oracle.weight_integrals(3, stat, theta, mu, nmax=4)
+    e, w, opp, cs = oracle.lattice("D3V27", I)
+    s6 = float(np.sum(w * (e[:, 0] ** 2) * (e[:, 1] ** 2) * (e[:, 2] ** 2)))
+    assert abs(s6 - I[3] * cs ** 6) < 1e-13 * I[3] * cs ** 6, (s6, I[3] * cs ** 6)
+    # the weight sum and the second and fourth moments close with the same I_6
+    assert abs(w.sum() - I[0]) < 1e-13 * I[0]
+    assert abs(np.sum(w * e[:, 0] ** 2) - I[1] * cs ** 2) < 1e-13 * I[1] * cs ** 2
+    assert abs(np.sum(w * e[:, 0] ** 2 * e[:, 1] ** 2) - I[2] * cs ** 4) < 1e-13 * I[2] * cs ** 4
+
+
 def test_d3v15_rejected_for_fd():
     """Sec. 8 requires positive weights; D3V15 gives w_0 = I_0(1 - 7J_2/9) < 0 for
     the FD weight of Sec. 9.1."""
