@@ -15,6 +15,14 @@ Functions and the passages they follow:
   Model.step         Sec. 9.1 discrete Boltzmann equation (collide, then stream)
   Model.adjoint      reverse sweep of Model.step (chain rule of the above)
 
+Fourth-order equilibrium and the 1D thermal model (``lbm_oracle4.c``):
+  coefficients4      Sec. 3 (c_K for K <= 4, c'_K, cbar_K, d_4, d'_4, dbar_4)
+  polynomials        Sec. 3 (P_0 .. P_4 as dense tensors)
+  projections        Sec. 4 (A_0 .. A_4 of an isotropic EDF shifted by u)
+  edf                Sec. 4, Eq. feq-4order-01 (the contraction to order N)
+  lattice1d          Table lattices-tab (D1V5 a/b), App. A (D1V7)
+  Thermal            the 1D thermal model on D1V5/D1V7 (readings in lbm_oracle4.c)
+
 Every function is pinned in tests/ against something other than itself.
 """
 from __future__ import annotations
@@ -27,6 +35,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
+_SRC4 = os.path.join(_HERE, "lbm_oracle4.c")
 _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "liblbm_oracle.so")
 
@@ -41,11 +50,11 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
     os.makedirs(_BUILD_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC4))):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+           "-ffp-contract=off", "-fno-fast-math", _SRC, _SRC4, "-o", tmp, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -81,6 +90,22 @@ def _load():
     lib.or_adjoint.argtypes = [vp, i64p, u8p, dp, dp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp,
                                dp, dp, dp]
     lib.or_num_threads.restype = ctypes.c_int
+    lib.or_coefficients4.argtypes = [ctypes.c_int, dp, dp]
+    lib.or_polynomials.argtypes = [ctypes.c_int, dp, dp, dp]
+    lib.or_projections.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, ctypes.c_double, ctypes.c_double, dp]
+    lib.or_edf.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, dp, ctypes.c_double, dp,
+                           ctypes.c_double, ctypes.c_double]
+    lib.or_edf.restype = ctypes.c_double
+    lib.or_lattice1d.argtypes = [ctypes.c_int, dp, ip, dp, dp]
+    lib.or_thermal_size.restype = ctypes.c_int
+    lib.or_thermal_init.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    lib.or_thermal_constants.argtypes = [vp, dp]
+    lib.or_thermal_equilibrium.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+    lib.or_thermal_collide_cell.argtypes = [vp, dp, ctypes.c_double, dp]
+    lib.or_thermal_step.argtypes = [vp, ctypes.c_int64, dp, dp, dp, ctypes.c_int64]
+    lib.or_thermal_init_state.argtypes = [vp, ctypes.c_int64, dp, dp, dp, dp]
+    lib.or_thermal_moments.argtypes = [vp, ctypes.c_int64, dp, dp, dp, dp, dp]
     _lib = lib
     return lib
 
@@ -288,3 +313,129 @@ class Model:
                            _dp(gE), _dp(gB), _dp(gtau), _dp(loss))
         return {"loss": float(loss[0]), "lam0": lam0, "gE": gE.reshape((self.D,) + tuple(shape)),
                 "gB": gB, "gtau": float(gtau[0])}
+
+
+# ---------------------------------------------------------------------------
+# Fourth-order EDF and the 1D thermal model (lbm_oracle4.c).
+# ---------------------------------------------------------------------------
+COEF4_KEYS = ["c0", "c1", "c2", "c3", "c4", "cp2", "cp3", "cp4", "cb2", "cb3", "cb4", "d4", "d4p", "d4b",
+              "Delta2", "Delta4", "Delta6"]
+LATTICE1D = {"D1V5a": 0, "D1V5b": 1, "D1V7": 2, "D1V7r1": 3, "D1V7r2": 4}
+
+
+def coefficients4(D: int, I: np.ndarray) -> np.ndarray:
+    """The 17 coefficients of Sec. 3 up to K = 4 (order of COEF4_KEYS)."""
+    I = np.ascontiguousarray(I[:5], dtype=np.float64)
+    out = np.zeros(17)
+    if _load().or_coefficients4(D, _dp(I), _dp(out)) != 0:
+        raise ValueError("coefficients undefined for these weight integrals")
+    return out
+
+
+def _split(D, flat):
+    out, off = [], 0
+    for N in range(5):
+        n = D ** N
+        out.append(flat[off: off + n].reshape((D,) * N))
+        off += n
+    return out
+
+
+def polynomials(D: int, co: np.ndarray, xi) -> list:
+    """[P_0, P_i, P_ij, P_ijk, P_ijkl] at xi (Sec. 3)."""
+    x = np.ascontiguousarray(np.asarray(xi, dtype=np.float64).reshape(D))
+    flat = np.zeros(sum(D ** N for N in range(5)))
+    _load().or_polynomials(D, _dp(np.ascontiguousarray(co, dtype=np.float64)), _dp(x), _dp(flat))
+    return _split(D, flat)
+
+
+def projections(D: int, co: np.ndarray, rho: float, u, thetabar: float, g: float) -> list:
+    """[A_0, A_i, ..., A_ijkl] of Sec. 4."""
+    uu = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(D))
+    flat = np.zeros(sum(D ** N for N in range(5)))
+    _load().or_projections(D, _dp(np.ascontiguousarray(co, dtype=np.float64)), float(rho), _dp(uu),
+                           float(thetabar), float(g), _dp(flat))
+    return _split(D, flat)
+
+
+def edf(D: int, order: int, co: np.ndarray, w_a: float, xi_a, rho: float, u, thetabar: float, g: float) -> float:
+    """Eq. feq-4order-01 truncated at `order`, at one lattice vector."""
+    x = np.ascontiguousarray(np.asarray(xi_a, dtype=np.float64).reshape(D))
+    uu = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(D))
+    return float(_load().or_edf(D, order, _dp(np.ascontiguousarray(co, dtype=np.float64)), float(w_a), _dp(x),
+                                float(rho), _dp(uu), float(thetabar), float(g)))
+
+
+def lattice1d(kind: str, I: np.ndarray):
+    """(e[Q], w[Q], c_s) of D1V5a/D1V5b (Table lattices-tab) or D1V7 with root
+    0 (the printed closed form), 1 or 2 of its cubic (App. A)."""
+    I = np.ascontiguousarray(I[:5], dtype=np.float64)
+    e = np.zeros(7, dtype=np.int32)
+    w = np.zeros(7)
+    cs = np.zeros(1)
+    q = _load().or_lattice1d(LATTICE1D[kind], _dp(I), e.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(w),
+                             _dp(cs))
+    if q == -2:
+        raise ValueError("unstable")
+    if q < 0:
+        raise ValueError("bad lattice")
+    return e[:q].copy(), w[:q].copy(), float(cs[0])
+
+
+class Thermal:
+    """The 1D thermal model: fourth-order EDF (order 4 by default) with local
+    thetabar on D1V5/D1V7, velocity-shift force E, periodic box."""
+
+    def __init__(self, kind: str = "D1V7", stat: str = "fd", theta: float = 1.0 / 270.0, mu: float = 1.0,
+                 tau: float = 0.8, E: float = 0.0, order: int = 4):
+        lib = _load()
+        self._buf = ctypes.create_string_buffer(lib.or_thermal_size())
+        rc = lib.or_thermal_init(self._buf, LATTICE1D[kind], STAT[stat], theta, mu, tau, E, order)
+        if rc == -2:
+            raise ValueError("unstable lattice (a weight or c_s is not positive)")
+        if rc != 0:
+            raise ValueError("bad thermal-model arguments")
+        out = np.zeros(24 + 7)
+        self.Q = lib.or_thermal_constants(self._buf, _dp(out))
+        self.I = out[:5].copy()
+        self.cs = float(out[5])
+        self.g = float(out[6])
+        self.co = out[7:24].copy()
+        self.w = out[24: 24 + self.Q].copy()
+        self.e = {5: np.array([0, 1, -1, 3, -3]), 7: np.array([0, 1, -1, 2, -2, 3, -3])}[self.Q]
+        self.xi = self.e / self.cs
+        self.tau, self.E, self.order = tau, E, order
+
+    def equilibrium(self, rho: float, u: float, thetabar: float) -> np.ndarray:
+        out = np.zeros(self.Q)
+        _load().or_thermal_equilibrium(self._buf, float(rho), float(u), float(thetabar), _dp(out))
+        return out
+
+    def collide_cell(self, f, E=None) -> np.ndarray:
+        out = np.zeros(self.Q)
+        _load().or_thermal_collide_cell(self._buf, _dp(np.ascontiguousarray(f, dtype=np.float64)),
+                                        float(self.E if E is None else E), _dp(out))
+        return out
+
+    def init_state(self, rho, u, thetabar) -> np.ndarray:
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        n = rho.size
+        uu = np.ascontiguousarray(np.broadcast_to(u, (n,)), dtype=np.float64)
+        th = np.ascontiguousarray(np.broadcast_to(thetabar, (n,)), dtype=np.float64)
+        f = np.zeros(self.Q * n)
+        _load().or_thermal_init_state(self._buf, n, _dp(rho), _dp(uu), _dp(th), _dp(f))
+        return f
+
+    def step(self, f: np.ndarray, nsteps: int, Efield=None) -> np.ndarray:
+        n = f.size // self.Q
+        E_a = None if Efield is None else np.ascontiguousarray(Efield, dtype=np.float64)
+        tmp = np.empty_like(f)
+        _load().or_thermal_step(self._buf, n, _dp(E_a), _dp(f), _dp(tmp), int(nsteps))
+        return f
+
+    def moments(self, f: np.ndarray):
+        """(rho[n], j[n], energy[n], totals[3]); energy = sum_a f_a xi_a^2."""
+        n = f.size // self.Q
+        rho, j, en, tot = np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(3)
+        _load().or_thermal_moments(self._buf, n, _dp(np.ascontiguousarray(f)), _dp(rho), _dp(j), _dp(en), _dp(tot))
+        return rho, j, en, tot
