@@ -204,6 +204,7 @@ lbm::KParams lbm::make_params(const lbm_ctx* c) {
     p.lorder = c->lorder;
     p.lgofs = 0;
     p.status = c->status_dev;
+    p.seed = c->rseed;
     return p;
 }
 
@@ -479,6 +480,9 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_lattice* lat, const int64_t dims[
         lbm_destroy(c);
         return st;
     }
+    // cudaHostAlloc does not clear the word (a reused pinned page keeps the
+    // bytes of its previous owner), and a nonzero word reports a timeout
+    *(volatile int*)c->status_host = 0;
     // default geometry: all fluid
     if ((st = cuda_check(c, cudaMemsetAsync(c->mask_dev, 0, c->N, c->stream), "memset mask")) != LBM_OK) {
         lbm_destroy(c);
@@ -576,6 +580,12 @@ lbm_status lbm_set_rounding(lbm_ctx* c, int stochastic) {
     if (stochastic && c->storage == LBM_F32)
         return fail(c, LBM_ERR_INVALID_ARG, "stochastic rounding applies to FP16/BF16 storage only");
     c->stochastic = stochastic != 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_rounding_seed(lbm_ctx* c, uint32_t seed) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    c->rseed = seed;
     return LBM_OK;
 }
 
