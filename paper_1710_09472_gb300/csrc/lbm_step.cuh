@@ -194,12 +194,14 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
 }
 
 // Compensated collision for FP32 storage.  Same formulas as collide(), but the
-// moments, the momentum-carrying odd parts (w j~ + s c_s rho E, times W1) and
-// the final combination (1 - w) h + even + odd are carried as double-float
-// (hi + lo) and rounded once when stored.  With plain FP32 these steps add
-// several roundings of size eps |h| per population and step, which over
-// thousands of steps exceed the 1e-5 target for FP32 storage (the FP32
-// storage rounding alone stays near 1e-6).
+// moments and the momentum-carrying odd parts (w j~ + s c_s rho E, times W1,
+// and e_a . V) are carried as double-float (hi + lo); the final combination
+// (1 - w) h + even + odd is plain FP32.  With plain FP32 moments and momentum
+// chain each collision adds roundings of size eps |h| to the momentum, which
+// over thousands of steps exceed the 1e-5 target for FP32 storage (measured:
+// 5.9e-5 after 5000 Poiseuille steps, 7.8e-5 after 2000 Riemann steps); with
+// both compensated the errors are 6e-7 and 6e-6, within 1.1x of also
+// compensating the final sum, which costs another 28% of the step.
 template <class L, int FORCE>
 __device__ __forceinline__ void collide_acc(const float* h, const float* E, const KParams& p, float* out) {
     constexpr int kR1 = shell_first<L>(1), kR2 = shell_first<L>(2), kR3 = shell_first<L>(3);
@@ -289,7 +291,8 @@ __device__ __forceinline__ void collide_acc(const float* h, const float* E, cons
         e0[sh] = p.w[r] * (c0 + p.k2[r] * Ku);
         cqs[sh] = p.w[r] * cq;
     }
-    float rest = drho, rest_lo = drho_lo;
+    float rest = drho;
+    const float rest_lo = drho_lo;
 #pragma unroll
     for (int a = 1; a < L::Q; a += 2) {
         const int sh = esq_of<L>(a);
@@ -310,23 +313,13 @@ __device__ __forceinline__ void collide_acc(const float* h, const float* E, cons
                 ol += e - Vl[sh][d];
             }
         }
-        // (1 - w) h + even +/- odd, rounded once
-        float pa, ea, pb, eb, sa, sb, e1, e2;
-        two_prod(omm, h[a], pa, ea);
-        two_prod(omm, h[a + 1], pb, eb);
-        two_sum(pa, even, sa, e1);
-        two_sum(pb, even, sb, e2);
-        float ta, tb2, e3, e4;
-        two_sum(sa, oh, ta, e3);
-        two_sum(sb, -oh, tb2, e4);
-        const float ha = ta + (ea + e1 + e3 + ol);
-        const float hb = tb2 + (eb + e2 + e4 - ol);
+        // (1 - w) h + even +/- odd
+        const float o = oh + ol;
+        const float ha = fmaf(omm, h[a], even) + o;
+        const float hb = fmaf(omm, h[a + 1], even) - o;
         out[a] = ha;
         out[a + 1] = hb;
-        float e5, e6;
-        two_sum(rest, -ha, rest, e5);
-        two_sum(rest, -hb, rest, e6);
-        rest_lo += e5 + e6;
+        rest -= ha + hb;
     }
     out[0] = rest + rest_lo;
 }
