@@ -152,6 +152,13 @@ lbm_status lbm_set_E_field(lbm_ctx* ctx, const float* E);
  * a flow at u ~ 3e-3).  Errors: INVALID_ARG (FP32 storage with stochastic). */
 lbm_status lbm_set_rounding(lbm_ctx* ctx, int stochastic);
 
+/* Seed of the stochastic-rounding stream (default 0).  Two runs that differ
+ * only in this seed differ only by their rounding noise, which estimates the
+ * rounding floor of 16-bit storage on problems too large for an FP64
+ * reference.  A replayed step uses the seed in force when it is replayed, so
+ * keep it fixed within one lbm_adjoint call.  Errors: INVALID_ARG. */
+lbm_status lbm_set_rounding_seed(lbm_ctx* ctx, uint32_t seed);
+
 /* Change tau, the uniform E and B between steps without reallocating.
  * E or B may be NULL (unchanged).  Errors: INVALID_ARG (tau <= 1/2). */
 lbm_status lbm_set_params(lbm_ctx* ctx, double tau, const double E[3], const double B[3]);
@@ -298,6 +305,74 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* host_buf, size_t len);
  * has been reset.  The context's device must be current.  Errors:
  * INVALID_ARG, STATE, CUDA. */
 lbm_status lbm_moment_totals_static(lbm_ctx* ctx, double* totals);
+
+/* ------------------------------------------------------------------------- */
+/* One-dimensional thermal model with the fourth-order equilibrium.          */
+/* The EDF is Eq. feq-4order-01 (Sec. 4): f^eq_a = w_a sum_{N <= order}      */
+/* A_N . P_N(xi_a) / N!, with the polynomials and coefficients of Sec. 3      */
+/* (c_K up to K = 4, c'_K, cbar_K, d_4, d'_4, dbar_4) and the projections     */
+/* A_N(rho, u, thetabar, g) of Sec. 4.  thetabar(x) is local: rho (thetabar   */
+/* + u^2) = sum_a f_a xi_a^2, so the collision keeps mass, momentum and       */
+/* energy; g is held at the weight's value I0 I4 / I2^2.  The lattice is      */
+/* D1V5 (roots a and b of Table lattices-tab) or D1V7 (App. A; root 0 is the  */
+/* printed closed form, the largest positive root of its cubic, roots 1 and   */
+/* 2 the next smaller positive ones).  A uniform force E acts by the velocity */
+/* shift u* = u + tau E (Sec. 7, Eq. u-update-force-term-eq).  The box is     */
+/* periodic, with no solid cells.                                             */
+/* Populations are stored as the deviation h_a = f_a - rho0 w_a / I0, FP32,   */
+/* FP16 (scaled by 2^12) or BF16, direction-major h[a * nx + x]; the         */
+/* collision is FP32; FP16/BF16 stores round stochastically by default.      */
+/* ------------------------------------------------------------------------- */
+typedef struct lbm_thermal lbm_thermal;  /* opaque; owns its device memory */
+typedef enum {
+    LBM_T_D1V5A = 0,   /* e = 0, +-1, +-3; c_s^2 with the + sign */
+    LBM_T_D1V5B = 1,   /* the - sign */
+    LBM_T_D1V7 = 2,    /* e = 0, +-1, +-2, +-3; root 0 of the App. A cubic */
+    LBM_T_D1V7_R1 = 3, /* root 1 */
+    LBM_T_D1V7_R2 = 4  /* root 2 */
+} lbm_thermal_lattice;
+
+/* stat, theta, mu: the weight (as lbm_lattice); nx cells; tau > 1/2; E the
+ * uniform force (xi units); order 2, 3 or 4 (terms of the EDF kept);
+ * storage an lbm_dtype; stream a cudaStream_t or NULL.  Rho0 = 1.  Errors:
+ * INVALID_ARG, UNSTABLE_LATTICE (no such root, or a weight or c_s not
+ * positive, Sec. 8), OOM, CUDA. */
+lbm_status lbm_thermal_create(lbm_thermal** out, int lattice, int stat, double theta, double mu, int64_t nx,
+                              double tau, double E, int order, int storage, void* stream);
+void lbm_thermal_destroy(lbm_thermal* t);
+
+/* out[0..4] I_0..I_8, out[5] c_s, out[6] g, out[7..11] c_0..c_4,
+ * out[12..14] c'_2..c'_4, out[15..17] cbar_2..cbar_4, out[18..20] d_4, d'_4,
+ * dbar_4, out[21] thetabar of the weight (I2/I0), out[22] Q, out[23] tau,
+ * out[24..24+Q) the weights; n >= 24 + Q.  Errors: INVALID_ARG. */
+lbm_status lbm_thermal_constants(const lbm_thermal* t, double* out, int n);
+
+/* Stochastic (default for FP16/BF16) or nearest rounding of the stores, and
+ * the seed of the stochastic stream.  Errors: INVALID_ARG (FP32 with
+ * stochastic). */
+lbm_status lbm_thermal_set_rounding(lbm_thermal* t, int stochastic, uint32_t seed);
+
+/* f(x, 0) = f^eq(rho(x), u(x), thetabar(x)) (no force shift): each of rho,
+ * u, thetabar is nx FP32 values, host or device, or NULL (rho0 = 1, u = 0,
+ * thetabar = I2/I0).  Asynchronous.  Errors: INVALID_ARG, CUDA. */
+lbm_status lbm_thermal_init(lbm_thermal* t, const float* rho, const float* u, const float* thetabar);
+
+/* n collide-and-stream steps (Sec. 9.1 discrete Boltzmann equation),
+ * asynchronous on the stream.  Errors: INVALID_ARG, STATE, CUDA. */
+lbm_status lbm_thermal_step(lbm_thermal* t, int64_t n);
+
+/* Per-cell rho, j = sum f xi and energy sum f xi^2 = rho (thetabar + u^2)
+ * (nx FP32 each, device, any may be NULL), and, when totals is not NULL,
+ * their FP64 sums over the box on the host (synchronises).  Errors:
+ * INVALID_ARG, STATE, NONFINITE, CUDA. */
+lbm_status lbm_thermal_moments(lbm_thermal* t, float* rho, float* j, float* energy, double totals[3]);
+
+/* f_a(x) (or h_a(x) when deviation != 0) into f[Q * nx] FP32, device,
+ * direction-major.  Errors: INVALID_ARG, STATE, CUDA. */
+lbm_status lbm_thermal_populations(lbm_thermal* t, float* f, int deviation);
+
+const char* lbm_thermal_last_error(const lbm_thermal* t);
+int64_t lbm_thermal_launch_count(const lbm_thermal* t);
 
 /* Message of the last failed call on this context ("" if none). */
 const char* lbm_last_error(const lbm_ctx* ctx);

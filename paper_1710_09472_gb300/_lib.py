@@ -34,6 +34,17 @@ SIGNATURES = {
     "lbm_set_E_field": (_i, [_vp, _vp]),
     "lbm_set_params": (_i, [_vp, _d, _vp, _vp]),
     "lbm_set_rounding": (_i, [_vp, _i]),
+    "lbm_set_rounding_seed": (_i, [_vp, ctypes.c_uint32]),
+    "lbm_thermal_create": (_i, [ctypes.POINTER(_vp), _i, _i, _d, _d, _i64, _d, _d, _i, _i, _vp]),
+    "lbm_thermal_destroy": (None, [_vp]),
+    "lbm_thermal_constants": (_i, [_vp, _vp, _i]),
+    "lbm_thermal_set_rounding": (_i, [_vp, _i, ctypes.c_uint32]),
+    "lbm_thermal_init": (_i, [_vp, _vp, _vp, _vp]),
+    "lbm_thermal_step": (_i, [_vp, _i64]),
+    "lbm_thermal_moments": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "lbm_thermal_populations": (_i, [_vp, _vp, _i]),
+    "lbm_thermal_last_error": (ctypes.c_char_p, [_vp]),
+    "lbm_thermal_launch_count": (_i64, [_vp]),
     "lbm_init_equilibrium": (_i, [_vp, _vp, _vp]),
     "lbm_step": (_i, [_vp, _i64]),
     "lbm_moments": (_i, [_vp, _vp, _vp, _vp, _vp]),
@@ -84,9 +95,13 @@ def load():
     return lib
 
 
-def check(status: int, ctx=None, what: str = ""):
+THERMAL_LATTICE = {"D1V5a": 0, "D1V5b": 1, "D1V7": 2, "D1V7r1": 3, "D1V7r2": 4}
+
+
+def check(status: int, ctx=None, what: str = "", thermal: bool = False):
     if status != LBM_OK:
         msg = ""
         if ctx:
-            msg = (load().lbm_last_error(ctx) or b"").decode()
+            getter = load().lbm_thermal_last_error if thermal else load().lbm_last_error
+            msg = (getter(ctx) or b"").decode()
         raise LBMError(status, f"{what}: {msg}" if what else msg)

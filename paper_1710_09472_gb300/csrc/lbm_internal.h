@@ -391,6 +391,7 @@ struct lbm_ctx {
     int64_t n_fluid = 0;
     int storage = 0;
     bool stochastic = false;  // stochastic rounding of FP16/BF16 stores
+    uint32_t rseed = 0;       // seed of the stochastic-rounding stream
     double tau = 1.0;
     double E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
     // host-side constants (FP64)

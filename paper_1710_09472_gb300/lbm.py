@@ -144,6 +144,11 @@ class LBM:
         """Stochastic (default for f16/bf16) or round-to-nearest stores."""
         _lib.check(_lib.load().lbm_set_rounding(self._h, int(bool(stochastic))), self._h, "lbm_set_rounding")
 
+    def set_rounding_seed(self, seed: int):
+        """Seed of the stochastic-rounding stream (lbm_set_rounding_seed)."""
+        _lib.check(_lib.load().lbm_set_rounding_seed(self._h, int(seed) & 0xFFFFFFFF), self._h,
+                   "lbm_set_rounding_seed")
+
     def init_equilibrium(self, rho=None, u=None):
         _lib.check(_lib.load().lbm_init_equilibrium(self._h, _ptr(rho, np.float32, self.N, "rho"),
                                                     _ptr(u, np.float32, self.D * self.N, "u")), self._h,
@@ -236,3 +241,74 @@ class LBM:
     def load_state(self, blob: bytes):
         buf = ctypes.create_string_buffer(blob, len(blob))
         _lib.check(_lib.load().lbm_load_state(self._h, buf, len(blob)), self._h, "lbm_load_state")
+
+
+class Thermal:
+    """The 1D thermal model with the fourth-order EDF (lbm_thermal_*).
+
+    lattice: "D1V5a" | "D1V5b" | "D1V7" | "D1V7r1" | "D1V7r2"; nx cells,
+    periodic; E the uniform force (velocity shift); order 2, 3 or 4; storage
+    "f32" | "f16" | "bf16".  Fields are nx FP32 device tensors."""
+
+    def __init__(self, lattice: str, nx: int, tau: float, E: float = 0.0, order: int = 4, storage: str = "f32",
+                 stat: str = "fd", theta: float = 1.0 / 270.0, mu: float = 1.0, stream=None):
+        lib = _lib.load()
+        h = ctypes.c_void_p()
+        st = None
+        if stream is not None:
+            st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        _lib.check(lib.lbm_thermal_create(ctypes.byref(h), _lib.THERMAL_LATTICE[lattice], _lib.STAT[stat],
+                                          float(theta), float(mu), int(nx), float(tau), float(E), int(order),
+                                          _lib.STORAGE[storage], st), None, "lbm_thermal_create")
+        self._h = h
+        self.nx = int(nx)
+        out = (ctypes.c_double * 31)()
+        _lib.check(lib.lbm_thermal_constants(self._h, out, 31), self._h, "lbm_thermal_constants", thermal=True)
+        v = list(out)
+        self.Q = int(v[22])
+        keys = ["I0", "I2", "I4", "I6", "I8", "cs", "g", "c0", "c1", "c2", "c3", "c4", "cp2", "cp3", "cp4",
+                "cb2", "cb3", "cb4", "d4", "d4p", "d4b", "thetabar_w", "Q", "tau"]
+        self.const = dict(zip(keys, v[:24]))
+        self.w = np.array(v[24: 24 + self.Q])
+
+    def close(self):
+        if self._h:
+            _lib.load().lbm_thermal_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_rounding(self, stochastic: bool, seed: int = 0):
+        _lib.check(_lib.load().lbm_thermal_set_rounding(self._h, int(bool(stochastic)), int(seed) & 0xFFFFFFFF),
+                   self._h, "lbm_thermal_set_rounding", thermal=True)
+
+    def init(self, rho=None, u=None, thetabar=None):
+        n = self.nx
+        _lib.check(_lib.load().lbm_thermal_init(self._h, _ptr(rho, np.float32, n, "rho"), _ptr(u, np.float32, n, "u"),
+                                                _ptr(thetabar, np.float32, n, "thetabar")), self._h,
+                   "lbm_thermal_init", thermal=True)
+
+    def step(self, n: int = 1):
+        _lib.check(_lib.load().lbm_thermal_step(self._h, int(n)), self._h, "lbm_thermal_step", thermal=True)
+
+    def moments(self, rho=None, j=None, energy=None, totals: bool = True):
+        n = self.nx
+        tot = (ctypes.c_double * 3)() if totals else None
+        _lib.check(_lib.load().lbm_thermal_moments(self._h, _ptr(rho, np.float32, n, "rho"),
+                                                   _ptr(j, np.float32, n, "j"),
+                                                   _ptr(energy, np.float32, n, "energy"), tot), self._h,
+                   "lbm_thermal_moments", thermal=True)
+        return np.array(list(tot)) if totals else None
+
+    def populations(self, out, deviation: bool = False):
+        _lib.check(_lib.load().lbm_thermal_populations(self._h, _ptr(out, np.float32, self.Q * self.nx, "f"),
+                                                       int(bool(deviation))), self._h, "lbm_thermal_populations",
+                   thermal=True)
+        return out
+
+    def launch_count(self) -> int:
+        return int(_lib.load().lbm_thermal_launch_count(self._h))
