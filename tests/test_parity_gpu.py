@@ -26,6 +26,15 @@ def _built():
     build()
 
 
+def _rerun(vel, shape, solid, tau, T, storage, force, E, B, rho, u, Ef, ro, jo):
+    """gpu_rerun for check_storage_error: the same case with another rounding seed."""
+    def run(seed):
+        rg, jg, _, sim = gpu_run(vel, shape, solid, tau, T, storage, force, E, B, rho, u, Ef, seed=seed)
+        sim.close()
+        return rel_linf(rg, ro), rel_linf(jg, jo)
+    return run
+
+
 def _fields(shape, D, seed, amp_u=0.01, amp_rho=0.02):
     N = int(np.prod(shape))
     rho = (1.0 + amp_rho * (wl.uniform01(seed, N) - 0.5)).reshape(shape).astype(np.float32)
@@ -74,7 +83,8 @@ def test_parity_2d(storage, force, efield, shape):
     print(f"2d {shape} {storage} {force} efield={efield}: rho {er:.3e} j {ej:.3e}")
     check_storage_error(storage, (er, ej), dict(vel="D2V9", shape=shape, solid=solid, tau=0.7, steps=T, force=force,
                                                 E=E, B=B, rho=rho, u=u, Efield=Ef, reference=(ro, jo)),
-                        label=f"2d {shape} {force} efield={efield}")
+                        label=f"2d {shape} {force} efield={efield}",
+                        gpu_rerun=_rerun("D2V9", shape, solid, 0.7, T, storage, force, E, B, rho, u, Ef, ro, jo))
     assert abs(totg[0] / toto[0] - 1) < (1e-6 if storage != "bf16" else 1e-4)
     sim.close()
 
@@ -93,7 +103,8 @@ def test_parity_row_strides(storage, shape):
     er, ej = rel_linf(rg, ro), rel_linf(jg, jo)
     print(f"strides {shape} {storage}: rho {er:.3e} j {ej:.3e}")
     check_storage_error(storage, (er, ej), dict(vel="D2V9", shape=shape, solid=solid, tau=0.7, steps=40, force="term",
-                                                E=E, B=B, rho=rho, u=u, reference=(ro, jo)), label=f"strides {shape}")
+                                                E=E, B=B, rho=rho, u=u, reference=(ro, jo)), label=f"strides {shape}",
+                        gpu_rerun=_rerun("D2V9", shape, solid, 0.7, 40, storage, "term", E, B, rho, u, None, ro, jo))
     sim.close()
 
 
@@ -120,7 +131,8 @@ def test_parity_3d(storage, force, efield, shape):
     print(f"3d {shape} {storage} {force} efield={efield}: rho {er:.3e} j {ej:.3e}")
     check_storage_error(storage, (er, ej), dict(vel="D3V19", shape=shape, solid=solid, tau=0.8, steps=T, force=force,
                                                 E=E, B=B, rho=rho, u=u, Efield=Ef, reference=(ro, jo)),
-                        label=f"3d {shape} {force} efield={efield}")
+                        label=f"3d {shape} {force} efield={efield}",
+                        gpu_rerun=_rerun("D3V19", shape, solid, 0.8, T, storage, force, E, B, rho, u, Ef, ro, jo))
     sim.close()
 
 
@@ -156,7 +168,9 @@ def test_config_poiseuille_32x64(force):
     for storage, e in errs.items():
         check_storage_error(storage, e, dict(vel="D2V9", shape=w["shape"], solid=w["solid"], tau=w["tau"],
                                              steps=w["steps"], force=force, E=w["E"], reference=(ro, jo)),
-                            label=f"poiseuille {force}")
+                            label=f"poiseuille {force}",
+                            gpu_rerun=_rerun("D2V9", w["shape"], w["solid"], w["tau"], w["steps"], storage, force,
+                                             w["E"], (0, 0, 0), None, None, None, ro, jo))
 
 
 def test_config_riemann_4096x8():
@@ -173,7 +187,9 @@ def test_config_riemann_4096x8():
     for storage, e in errs.items():
         check_storage_error(storage, e, dict(vel="D2V9", shape=w["shape"], solid=w["solid"], tau=w["tau"],
                                              steps=w["steps"], force="term", rho=rho, reference=(ro, jo)),
-                            label="riemann")
+                            label="riemann",
+                            gpu_rerun=_rerun("D2V9", w["shape"], w["solid"], w["tau"], w["steps"], storage, "term",
+                                             (0, 0, 0), (0, 0, 0), rho, None, None, ro, jo))
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
@@ -190,8 +206,10 @@ def test_porous_long_3d(storage):
     er, ej = rel_linf(rg, ro), rel_linf(jg, jo)
     print(f"porous32 {storage}: rho {er:.3e} j {ej:.3e}")
     check_storage_error(storage, (er, ej), dict(vel="D3V19", shape=shape, solid=solid, tau=0.8, steps=2000,
-                                                force="term", E=E, B=B, reference=(ro, jo)), seeds=(1,),
-                        label="porous32")
+                                                force="term", E=E, B=B, reference=(ro, jo)), seeds=(1, 2, 3),
+                        label="porous32",
+                        gpu_rerun=_rerun("D3V19", shape, solid, 0.8, 2000, storage, "term", E, B, None, None, None,
+                                         ro, jo))
     sim.close()
 
 
