@@ -22,6 +22,8 @@ Fourth-order equilibrium and the 1D thermal model (``lbm_oracle4.c``):
   edf                Sec. 4, Eq. feq-4order-01 (the contraction to order N)
   lattice1d          Table lattices-tab (D1V5 a/b), App. A (D1V7)
   Thermal            the 1D thermal model on D1V5/D1V7 (readings in lbm_oracle4.c)
+  fd_integral        Sec. 4 (g_nu of the FD/BE EDF)
+  density_of_mu      Sec. 9.1, Eq. rho-def-eq; mu_of_density its inverse (Sec. 9.1.2)
 
 Every function is pinned in tests/ against something other than itself.
 """
@@ -106,6 +108,12 @@ def _load():
     lib.or_thermal_step.argtypes = [vp, ctypes.c_int64, dp, dp, dp, ctypes.c_int64]
     lib.or_thermal_init_state.argtypes = [vp, ctypes.c_int64, dp, dp, dp, dp]
     lib.or_thermal_moments.argtypes = [vp, ctypes.c_int64, dp, dp, dp, dp, dp]
+    lib.or_fd_integral.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    lib.or_fd_integral.restype = ctypes.c_double
+    lib.or_density_of_mu.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    lib.or_density_of_mu.restype = ctypes.c_double
+    lib.or_mu_of_density.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    lib.or_mu_of_density.restype = ctypes.c_double
     _lib = lib
     return lib
 
@@ -439,3 +447,21 @@ class Thermal:
         rho, j, en, tot = np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(3)
         _load().or_thermal_moments(self._buf, n, _dp(np.ascontiguousarray(f)), _dp(rho), _dp(j), _dp(en), _dp(tot))
         return rho, j, en, tot
+
+
+BE_STAT = {"fd": 0, "be": 1}
+
+
+def fd_integral(nu: float, eta: float, stat: str = "fd") -> float:
+    """g_nu(e^eta) of the FD (or BE) distribution (Sec. 4)."""
+    return float(_load().or_fd_integral(float(nu), float(eta), BE_STAT[stat]))
+
+
+def density_of_mu(D: int, theta: float, mu: float, stat: str = "fd") -> float:
+    """rho = (pi theta)^{D/2} g_{D/2}(e^{mu/theta}) (Sec. 9.1, Eq. rho-def-eq)."""
+    return float(_load().or_density_of_mu(int(D), BE_STAT[stat], float(theta), float(mu)))
+
+
+def mu_of_density(D: int, theta: float, rho: float, stat: str = "fd") -> float:
+    """The inverse of density_of_mu (Sec. 9.1.2), by bisection."""
+    return float(_load().or_mu_of_density(int(D), BE_STAT[stat], float(theta), float(rho)))

@@ -113,6 +113,17 @@ static void or_gl_init(void) {
     or_gl_ready = 1;
 }
 
+/* the 16 Gauss-Legendre nodes and weights on [-1, 1] (also used by the FD
+ * integrals of lbm_oracle4.c) */
+void or_gauss_legendre16(double* x, double* w) {
+    int i;
+    or_gl_init();
+    for (i = 0; i < OR_GL_N; ++i) {
+        x[i] = or_gl_x[i];
+        w[i] = or_gl_w[i];
+    }
+}
+
 static double or_gl_panel(const or_integrand* p, double a, double b) {
     double h = 0.5 * (b - a), m = 0.5 * (a + b), s = 0.0;
     int i;

@@ -460,3 +460,86 @@ void or_thermal_moments(const or_thermal* m, int64_t n, const double* f, double*
         totals[2] += e2;
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Density and chemical potential of the FD/BE equilibrium (Sec. 4 before    */
+/* Eq. rho-fd-be-eq; Sec. 9.1 Eq. rho-def-eq and the inverse of Sec. 9.1.2). */
+/*   g_nu(z) = 1/Gamma(nu) int_0^inf x^{nu-1} / (z^{-1} e^x + s) dx,          */
+/*   s = +1 (FD) or -1 (BE), z = e^eta; with x = t^2                          */
+/*   g_nu = 2/Gamma(nu) int_0^inf t^{2 nu - 1} / (e^{t^2 - eta} + s) dt.      */
+/*   rho(mu) = (pi theta)^{D/2} g_{D/2}(e^{mu/theta}) for the non-dimensional  */
+/*   EDF of Eq. fd-dist-non-dim-eq (exponent (xi - u)^2 / theta).             */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    double nu, eta;
+    int s;
+} or4_gnu;
+
+static double or4_gnu_f(const or4_gnu* p, double t) {
+    double y = t * t - p->eta, den;
+    if (p->s > 0) { /* 1/(e^y + 1) without overflow */
+        if (y > 0.0) {
+            double e = exp(-y);
+            return pow(t, 2.0 * p->nu - 1.0) * e / (1.0 + e);
+        }
+        return pow(t, 2.0 * p->nu - 1.0) / (exp(y) + 1.0);
+    }
+    den = expm1(y); /* BE: eta < 0 so y > 0 */
+    return pow(t, 2.0 * p->nu - 1.0) / den;
+}
+
+/* composite 16-point Gauss-Legendre on panels of width <= 0.01 in t, which
+ * resolve the Fermi edge (width about 1/(2 sqrt(eta)) in t) to round-off */
+extern void or_gauss_legendre16(double* x, double* w);
+
+/* stat 0 = FD, 1 = BE (eta < 0); returns NaN for bad arguments */
+double or_fd_integral(double nu, double eta, int stat) {
+    or4_gnu p;
+    double x[16], w[16], top, h, s = 0.0;
+    int k, i, n;
+    if (!(nu > 0.0) || (stat == 1 && !(eta < 0.0)) || stat < 0 || stat > 1) return NAN;
+    or_gauss_legendre16(x, w);
+    p.nu = nu;
+    p.eta = eta;
+    p.s = stat == 0 ? 1 : -1;
+    top = sqrt((eta > 0.0 ? eta : 0.0) + 800.0);
+    n = (int)ceil(top / 0.01);
+    h = top / n;
+    for (k = 0; k < n; ++k) {
+        double a = k * h, m = a + 0.5 * h, ps = 0.0;
+        for (i = 0; i < 16; ++i) ps += w[i] * or4_gnu_f(&p, m + 0.5 * h * x[i]);
+        s += 0.5 * h * ps;
+    }
+    return 2.0 * s / tgamma(nu);
+}
+
+double or_density_of_mu(int D, int stat, double theta, double mu) {
+    if (D < 1 || D > 3 || !(theta > 0.0)) return NAN;
+    return pow(M_PI * theta, 0.5 * D) * or_fd_integral(0.5 * D, mu / theta, stat);
+}
+
+/* the inverse by bisection on eta = mu / theta (rho increases with eta) */
+double or_mu_of_density(int D, int stat, double theta, double rho) {
+    double lo = -60.0, hi = stat == 1 ? -1e-12 : 1.0;
+    int it;
+    if (D < 1 || D > 3 || !(theta > 0.0) || !(rho > 0.0)) return NAN;
+    /* 100 halvings of a bracket of width <= 2^23 reach the spacing of doubles */
+    if (!(or_density_of_mu(D, stat, theta, lo * theta) < rho)) return NAN;
+    if (stat == 1) {
+        if (!(or_density_of_mu(D, stat, theta, hi * theta) > rho)) return NAN;
+    } else {
+        while (!(or_density_of_mu(D, stat, theta, hi * theta) > rho)) {
+            hi *= 2.0;
+            if (hi > 1e7) return NAN;
+        }
+    }
+    for (it = 0; it < 100; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        if (or_density_of_mu(D, stat, theta, mid * theta) < rho)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return 0.5 * (lo + hi) * theta;
+}
