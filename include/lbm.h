@@ -374,6 +374,24 @@ lbm_status lbm_thermal_populations(lbm_thermal* t, float* f, int deviation);
 const char* lbm_thermal_last_error(const lbm_thermal* t);
 int64_t lbm_thermal_launch_count(const lbm_thermal* t);
 
+/* ------------------------------------------------------------------------- */
+/* Density <-> chemical potential of the Fermi-Dirac equilibrium, as field   */
+/* conversions (the paper uses them to set initial conditions and to report  */
+/* fields, Sec. 9.1.2):                                                       */
+/*   rho = (pi theta)^{D/2} g_{D/2}(e^{mu/theta})          (Sec. 9.1, Eq. rho-def-eq) */
+/*   mu  = theta ln g_{D/2}^{-1}(rho / (pi theta)^{D/2})    (Sec. 9.1.2)      */
+/* with the complete FD integral g_nu of Sec. 4 (before Eq. rho-fd-be-eq), in */
+/* the non-dimensional units of Eq. fd-dist-non-dim-eq.  mu / rho: n FP32     */
+/* values in device memory (the input is only read), computed in FP64 on the  */
+/* stream (cudaStream_t or NULL), asynchronous.  A non-positive or infinite   */
+/* density gives NaN.  The first call on a device for a dimension D builds a  */
+/* 144 KB table of ln g_{D/2} on that device (and synchronises the stream);   */
+/* the table stays until the process exits.  D in 1..3, theta > 0.            */
+/* Errors: INVALID_ARG (bad D, theta, n or a host pointer), OOM, CUDA.        */
+/* ------------------------------------------------------------------------- */
+lbm_status lbm_density_from_mu(int D, double theta, const float* mu, float* rho, int64_t n, void* stream);
+lbm_status lbm_mu_from_density(int D, double theta, const float* rho, float* mu, int64_t n, void* stream);
+
 /* Message of the last failed call on this context ("" if none). */
 const char* lbm_last_error(const lbm_ctx* ctx);
 

@@ -45,6 +45,8 @@ SIGNATURES = {
     "lbm_thermal_populations": (_i, [_vp, _vp, _i]),
     "lbm_thermal_last_error": (ctypes.c_char_p, [_vp]),
     "lbm_thermal_launch_count": (_i64, [_vp]),
+    "lbm_density_from_mu": (_i, [_i, _d, _vp, _vp, _i64, _vp]),
+    "lbm_mu_from_density": (_i, [_i, _d, _vp, _vp, _i64, _vp]),
     "lbm_init_equilibrium": (_i, [_vp, _vp, _vp]),
     "lbm_step": (_i, [_vp, _i64]),
     "lbm_moments": (_i, [_vp, _vp, _vp, _vp, _vp]),

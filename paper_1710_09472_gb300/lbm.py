@@ -52,6 +52,29 @@ def weight_integrals(D: int, stat: str = "fd", theta: float = 1.0 / 270.0, mu: f
     return np.array(list(out))
 
 
+def density_from_mu(D: int, theta: float, mu, rho=None, stream=None):
+    """rho = (pi theta)^{D/2} g_{D/2}(e^{mu/theta}) per element (FD weight),
+    mu and rho float32 CUDA tensors (lbm_density_from_mu)."""
+    if rho is None:
+        rho = torch.empty_like(mu)
+    st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _lib.check(_lib.load().lbm_density_from_mu(int(D), float(theta), _ptr(mu, np.float32, mu.numel(), "mu"),
+                                               _ptr(rho, np.float32, mu.numel(), "rho"), mu.numel(), st), None,
+               "lbm_density_from_mu")
+    return rho
+
+
+def mu_from_density(D: int, theta: float, rho, mu=None, stream=None):
+    """The inverse of density_from_mu (lbm_mu_from_density)."""
+    if mu is None:
+        mu = torch.empty_like(rho)
+    st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _lib.check(_lib.load().lbm_mu_from_density(int(D), float(theta), _ptr(rho, np.float32, rho.numel(), "rho"),
+                                               _ptr(mu, np.float32, rho.numel(), "mu"), rho.numel(), st), None,
+               "lbm_mu_from_density")
+    return mu
+
+
 def _vec3(v):
     if v is None:
         return None
