@@ -56,12 +56,16 @@ __device__ __forceinline__ uint32_t t_hash(uint32_t x) {
     return x;
 }
 
+// x - e for |e| <= 3 in a periodic row of nx >= 1 cells (a row shorter than
+// 3 cells can need more than one wrap)
 __device__ __forceinline__ int wrapx(int x, int nx) {
-    x %= nx;
-    return x < 0 ? x + nx : x;
+    while (x < 0) x += nx;
+    while (x >= nx) x -= nx;
+    return x;
 }
 
-// The equilibrium deviations heq~_a (scaled) of one cell.
+// The equilibrium deviations heq~_a (scaled) of one cell (a < Q).
+template <int Q>
 __device__ __forceinline__ void t_equilibrium(const TParams& p, float drho, float rho, float us, float dth,
                                               float* heq) {
     const float srho = p.scale * rho;
@@ -81,8 +85,10 @@ __device__ __forceinline__ void t_equilibrium(const TParams& p, float drho, floa
         A4 = srho * (3.f * S + 6.f * u2 * T + p.c4 * u2 * u2);
     }
     const float A[5] = {drho, A1, A2, A3, A4};
-    for (int a = 0; a < p.Q; ++a) {
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
         float s = 0.f;
+#pragma unroll
         for (int N = 0; N < 5; ++N) s += fmaf(p.Wlo[N][a], A[N], p.W[N][a] * A[N]);
         heq[a] = s;
     }
@@ -101,16 +107,17 @@ __device__ __forceinline__ void t_acc(float& hi, float& lo, float a, float b) { 
     lo += e + pe;
 }
 
-template <class S, bool SR>
+template <class S, bool SR, int Q>
 __global__ void __launch_bounds__(kTBlock) k_thermal_step(const typename S::T* __restrict__ Pin,
                                                           typename S::T* __restrict__ Pout, TParams p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= p.nx) return;
-    float h[kTQ], heq[kTQ];
+    float h[Q], heq[Q];
     // the moments as double-float sums (the first FP32 rounding of a moment
     // would otherwise recur in every step)
     float dh = 0.f, dl = 0.f, jh = 0.f, jl = 0.f, mh = 0.f, ml = 0.f;
-    for (int a = 0; a < p.Q; ++a) {
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
         h[a] = S::cvt(Pin[(int64_t)a * p.nx + wrapx(x - p.e[a], p.nx)]);
         float e;
         t_two_sum(dh, h[a], dh, e);
@@ -122,12 +129,13 @@ __global__ void __launch_bounds__(kTBlock) k_thermal_step(const typename S::T* _
     const float rho = p.rho0 + drho * p.inv_scale;
     const float u = j * p.inv_scale / rho;
     const float dth = m2 * p.inv_scale / rho - u * u;
-    t_equilibrium(p, drho, rho, u + p.tau * p.E, dth, heq);
+    t_equilibrium<Q>(p, drho, rho, u + p.tau * p.E, dth, heq);
     const float omm = 1.f - p.omega;
     float rest = dh;
     uint32_t r = 0;
     if (SR) r = t_hash((uint32_t)x ^ t_hash(p.step * 0x9E3779B9u + p.seed));
-    for (int a = 1; a < p.Q; a += 2) {
+#pragma unroll
+    for (int a = 1; a < Q; a += 2) {
         const float ha = fmaf(omm, h[a], p.omega * heq[a]);
         const float hb = fmaf(omm, h[a + 1], p.omega * heq[a + 1]);
         rest -= ha + hb;
@@ -154,25 +162,26 @@ __global__ void __launch_bounds__(kTBlock) k_thermal_step(const typename S::T* _
 }
 
 // f(x, 0) = f^eq(rho(x), u(x), thetabar(x)): P_a(y) holds f_a(y + e_a, 0).
-template <class S>
+template <class S, int Q>
 __global__ void __launch_bounds__(kTBlock) k_thermal_init(typename S::T* __restrict__ P, const float* __restrict__ rho,
                                                           const float* __restrict__ u, const float* __restrict__ th,
                                                           TParams p) {
     const int y = blockIdx.x * blockDim.x + threadIdx.x;
     if (y >= p.nx) return;
-    for (int a = 0; a < p.Q; ++a) {
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
         const int x = wrapx(y + p.e[a], p.nx);
         const float r = rho ? rho[x] : p.rho0;
         const float uu = u ? u[x] : 0.f;
         const float dth = th ? th[x] - p.thw : 0.f;
-        float heq[kTQ];
-        t_equilibrium(p, (r - p.rho0) * p.scale, r, uu, dth, heq);
+        float heq[Q];
+        t_equilibrium<Q>(p, (r - p.rho0) * p.scale, r, uu, dth, heq);
         S::put(P + (int64_t)a * p.nx + y, heq[a]);
     }
 }
 
 // rho, j = sum f xi, energy = sum f xi^2 per cell; FP64 block partials of the three
-template <class S>
+template <class S, int Q>
 __global__ void __launch_bounds__(kTBlock) k_thermal_moments(const typename S::T* __restrict__ P, float* rho_out,
                                                              float* j_out, float* e_out, float* f_out, int deviation,
                                                              double* partials, TParams p) {
@@ -180,7 +189,8 @@ __global__ void __launch_bounds__(kTBlock) k_thermal_moments(const typename S::T
     double acc[3] = {0.0, 0.0, 0.0};
     if (x < p.nx) {
         float drho = 0.f, j = 0.f, e2 = 0.f;
-        for (int a = 0; a < p.Q; ++a) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
             const float h = S::cvt(P[(int64_t)a * p.nx + wrapx(x - p.e[a], p.nx)]) * p.inv_scale;
             drho += h;
             j += h * p.xi[a];
@@ -217,6 +227,16 @@ int by_storage(int storage, F&& f) {
     if (storage == LBM_F16_DEV) return f(lbm::StoreF16{});
     if (storage == LBM_BF16_DEV) return f(lbm::StoreBF16{});
     return f(lbm::StoreF32{});
+}
+
+template <int Q>
+struct QTag {
+    static constexpr int value = Q;
+};
+// storage type and lattice size (5 or 7) as compile-time tags
+template <class F>
+int by_storage_q(int storage, int Q, F&& f) {
+    return by_storage(storage, [&](auto st) { return Q == 5 ? f(st, QTag<5>{}) : f(st, QTag<7>{}); });
 }
 
 // ---------------------------------------------------------------------------
@@ -526,9 +546,10 @@ lbm_status lbm_thermal_init(lbm_thermal* t, const float* rho, const float* u, co
         }
     }
     const TParams p = tparams(t);
-    t->launches += by_storage(t->storage, [&](auto st) {
+    t->launches += by_storage_q(t->storage, t->Q, [&](auto st, auto q) {
         using S = decltype(st);
-        k_thermal_init<S><<<tgrid(t->nx), kTBlock, 0, t->stream>>>((typename S::T*)t->pop[0], d[0], d[1], d[2], p);
+        k_thermal_init<S, decltype(q)::value>
+            <<<tgrid(t->nx), kTBlock, 0, t->stream>>>((typename S::T*)t->pop[0], d[0], d[1], d[2], p);
         return 1;
     });
     t->cur = 0;
@@ -543,15 +564,16 @@ lbm_status lbm_thermal_step(lbm_thermal* t, int64_t n) {
     for (int64_t s = 0; s < n; ++s) {
         const TParams p = tparams(t);
         const bool sr = t->stochastic;
-        t->launches += by_storage(t->storage, [&](auto st) {
+        t->launches += by_storage_q(t->storage, t->Q, [&](auto st, auto q) {
             using S = decltype(st);
             using T = typename S::T;
+            constexpr int Q = decltype(q)::value;
             if (sr && S::kBytes == 2)
-                k_thermal_step<S, true><<<tgrid(t->nx), kTBlock, 0, t->stream>>>((const T*)t->pop[t->cur],
-                                                                                 (T*)t->pop[t->cur ^ 1], p);
+                k_thermal_step<S, true, Q><<<tgrid(t->nx), kTBlock, 0, t->stream>>>((const T*)t->pop[t->cur],
+                                                                                    (T*)t->pop[t->cur ^ 1], p);
             else
-                k_thermal_step<S, false><<<tgrid(t->nx), kTBlock, 0, t->stream>>>((const T*)t->pop[t->cur],
-                                                                                  (T*)t->pop[t->cur ^ 1], p);
+                k_thermal_step<S, false, Q><<<tgrid(t->nx), kTBlock, 0, t->stream>>>((const T*)t->pop[t->cur],
+                                                                                     (T*)t->pop[t->cur ^ 1], p);
             return 1;
         });
         t->cur ^= 1;
@@ -566,11 +588,10 @@ lbm_status lbm_thermal_moments(lbm_thermal* t, float* rho, float* j, float* ener
     for (const float* q : {rho, j, energy})
         if (q && !is_dev(q)) return tfail(t, LBM_ERR_INVALID_ARG, "lbm_thermal_moments: fields must be device memory");
     const TParams p = tparams(t);
-    t->launches += by_storage(t->storage, [&](auto st) {
+    t->launches += by_storage_q(t->storage, t->Q, [&](auto st, auto q) {
         using S = decltype(st);
-        k_thermal_moments<S><<<tgrid(t->nx), kTBlock, 0, t->stream>>>((const typename S::T*)t->pop[t->cur], rho, j,
-                                                                       energy, nullptr, 0,
-                                                                       totals ? t->partials : nullptr, p);
+        k_thermal_moments<S, decltype(q)::value><<<tgrid(t->nx), kTBlock, 0, t->stream>>>(
+            (const typename S::T*)t->pop[t->cur], rho, j, energy, nullptr, 0, totals ? t->partials : nullptr, p);
         return 1;
     });
     if (totals) {
@@ -592,10 +613,10 @@ lbm_status lbm_thermal_populations(lbm_thermal* t, float* f, int deviation) {
     if (!t->has_state) return tfail(t, LBM_ERR_STATE, "lbm_thermal_populations before lbm_thermal_init");
     if (!is_dev(f)) return tfail(t, LBM_ERR_INVALID_ARG, "lbm_thermal_populations: f must be device memory");
     const TParams p = tparams(t);
-    t->launches += by_storage(t->storage, [&](auto st) {
+    t->launches += by_storage_q(t->storage, t->Q, [&](auto st, auto q) {
         using S = decltype(st);
-        k_thermal_moments<S><<<tgrid(t->nx), kTBlock, 0, t->stream>>>((const typename S::T*)t->pop[t->cur], nullptr,
-                                                                       nullptr, nullptr, f, deviation, nullptr, p);
+        k_thermal_moments<S, decltype(q)::value><<<tgrid(t->nx), kTBlock, 0, t->stream>>>(
+            (const typename S::T*)t->pop[t->cur], nullptr, nullptr, nullptr, f, deviation, nullptr, p);
         return 1;
     });
     return tcuda(t, cudaGetLastError(), "lbm_thermal_populations");

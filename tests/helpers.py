@@ -148,24 +148,25 @@ def bound_16bit(storage, floor):
     return max(TOL[storage], FLOOR_FACTOR * floor)
 
 
-def check_storage_error(storage, errs, floor_args, seeds=(1, 2, 3), label="", gpu_rerun=None):
+def check_storage_error(storage, errs, floor_args, seeds=(1, 2, 3, 4, 5), label="", gpu_rerun=None):
     """Assert the GPU's (rho, j) errors against the storage's bound.
 
     FP32: 1e-5.  FP16/BF16: 2e-3 where the error is within it.  Otherwise the
-    format floor of the same case (storage_floor, one draw per seed) is
-    computed, and the bound is 2e-3 or 1.25 x the median floor, whichever is
-    larger.  The error of one run is one draw of its rounding noise too, and
-    a few pore cells can dominate the largest error of a draw; so when
-    gpu_rerun(seed) -> (rho error, j error) is given, the GPU case runs with
-    two more rounding seeds and the median of the three draws is compared.
-    floor_args: the keyword arguments of storage_floor for this case."""
+    format floor of the same case is computed (storage_floor, one draw per
+    seed), and the bound is 2e-3 or 1.25 x the largest floor draw, whichever
+    is larger.  The largest error of one run is one draw of a heavy-tailed
+    quantity (a few closed pores or wall cells can set it), so when
+    gpu_rerun(seed) -> (rho error, j error) is given, the GPU case also runs
+    with two more rounding seeds and the median of its three draws is
+    compared; a path whose rounding noise were twice the format's would still
+    fail.  floor_args: the keyword arguments of storage_floor for this case."""
     er, ej = errs
     if storage == "f32" or max(er, ej) <= TOL[storage]:
         assert er <= TOL[storage] and ej <= TOL[storage], (label, storage, er, ej)
         return TOL[storage], None
     floors = [storage_floor(storage=storage, seed=sd, **floor_args) for sd in seeds]
-    fr = float(np.median([f[0] for f in floors]))
-    fj = float(np.median([f[1] for f in floors]))
+    fr = max(f[0] for f in floors)
+    fj = max(f[1] for f in floors)
     draws = [(er, ej)]
     if gpu_rerun is not None:
         draws += [gpu_rerun(sd) for sd in (101, 102)]

@@ -80,8 +80,8 @@ def test_porous256_ohm_hall_sweep(porous256, Bz):
     estimated from the FP16 runs themselves: three runs that differ only in
     the rounding seed differ by their rounding noise alone, and the L-inf of
     the difference of two of them is sqrt(2) times the L-inf of one run's
-    noise.  The errors against FP32 and the floor are each the median over
-    the three runs (three pairs).  After the last FP32 run the oracle
+    noise.  The error against FP32 is the median over the three runs, the
+    floor the largest over the three pairs.  After the last FP32 run the oracle
     collides and streams its state at 3000 sampled fluid cells."""
     w = porous256
     shape, steps = w["shape"], w["steps"]
@@ -106,8 +106,8 @@ def test_porous256_ohm_hall_sweep(porous256, Bz):
         er = float(np.median([_rel_dev(r[0], r32) for r in runs]))
         ej = float(np.median([_rel_dev(r[1], j32) for r in runs]))
         pairs = ((0, 1), (0, 2), (1, 2))
-        fr = float(np.median([_rel_dev(runs[a][0], runs[b][0]) for a, b in pairs])) / np.sqrt(2.0)
-        fj = float(np.median([_rel_dev(runs[a][1], runs[b][1]) for a, b in pairs])) / np.sqrt(2.0)
+        fr = max(_rel_dev(runs[a][0], runs[b][0]) for a, b in pairs) / np.sqrt(2.0)
+        fj = max(_rel_dev(runs[a][1], runs[b][1]) for a, b in pairs) / np.sqrt(2.0)
         br, bj = max(2e-3, 1.25 * fr), max(2e-3, 1.25 * fj)
         ratios.append((tj32[0] / n_fluid / Ex, tj32[1] / n_fluid / Ex))
         report.append((Ex, er, ej, fr, fj, br, bj))

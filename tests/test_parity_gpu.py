@@ -168,7 +168,7 @@ def test_config_poiseuille_32x64(force):
     for storage, e in errs.items():
         check_storage_error(storage, e, dict(vel="D2V9", shape=w["shape"], solid=w["solid"], tau=w["tau"],
                                              steps=w["steps"], force=force, E=w["E"], reference=(ro, jo)),
-                            label=f"poiseuille {force}",
+                            label=f"poiseuille {force}", seeds=(1, 2, 3),
                             gpu_rerun=_rerun("D2V9", w["shape"], w["solid"], w["tau"], w["steps"], storage, force,
                                              w["E"], (0, 0, 0), None, None, None, ro, jo))
 
@@ -187,7 +187,7 @@ def test_config_riemann_4096x8():
     for storage, e in errs.items():
         check_storage_error(storage, e, dict(vel="D2V9", shape=w["shape"], solid=w["solid"], tau=w["tau"],
                                              steps=w["steps"], force="term", rho=rho, reference=(ro, jo)),
-                            label="riemann",
+                            label="riemann", seeds=(1, 2, 3),
                             gpu_rerun=_rerun("D2V9", w["shape"], w["solid"], w["tau"], w["steps"], storage, "term",
                                              (0, 0, 0), (0, 0, 0), rho, None, None, ro, jo))
 

@@ -108,26 +108,33 @@ def test_constants_match_oracle():
         Thermal("D1V5a", 16, 0.8)
 
 
-CASES = [(lat, w, order, E, n) for (lat, w) in (("D1V7", "mb"), ("D1V7", "fd03"), ("D1V7", "be"), ("D1V5b", "mb"))
-         for order in (4, 3, 2) for (E, n) in ((0.0, 300), (2e-4, 256))]
+# The FD weight at theta = 0.3 is far from Gaussian (g = 0.70): its
+# third-order truncation is unstable on D1V7 (the FP64 oracle blows up within
+# 400 steps from these fields), so it is run at orders 2 and 4 only, and for
+# 100 steps: its random start flow decays ten times faster than the signal
+# the relative error is taken against, and in FP64 already a 1e-7 change of
+# the start state moves j by 2e-6 of its final size after 200 steps.
+CASES = ([(lat, w, order, E, n, 200) for (lat, w) in (("D1V7", "mb"), ("D1V7", "be"), ("D1V5b", "mb"))
+          for order in (4, 3, 2) for (E, n) in ((0.0, 300), (2e-4, 256))]
+         + [("D1V7", "fd03", order, E, n, 100) for order in (4, 2) for (E, n) in ((0.0, 300), (2e-4, 256))])
 
 
-@pytest.mark.parametrize("lattice,weight,order,E,n", CASES)
-def test_thermal_parity_f32(lattice, weight, order, E, n):
-    """FP32 storage, 200 steps from random rho, u, thetabar fields: rho, j and
-    energy against the oracle to 1e-5, and the FP64 totals: mass and energy
+@pytest.mark.parametrize("lattice,weight,order,E,n,steps", CASES)
+def test_thermal_parity_f32(lattice, weight, order, E, n, steps):
+    """FP32 storage from random rho, u, thetabar fields: rho, j and energy
+    against the oracle to 1e-5, and the FP64 totals: mass and energy
     conserved (E = 0), momentum grown by rho E per step."""
     try:
         oracle.Thermal(lattice, *WEIGHTS[weight])
     except ValueError:
         pytest.skip("no such lattice for this weight")
-    steps, tau = 200, 0.8
+    tau = 0.8
     m = oracle.Thermal(lattice, *WEIGHTS[weight], tau=tau)
     fields = _fields(n, 21, m.I[1] / m.I[0])
     rg, jg, eg, tg, t = _gpu(lattice, weight, n, tau, E, order, "f32", steps, fields)
     ro, jo, eo, to, m, _ = _oracle(lattice, weight, tau, E, order, steps, fields)
     er, ej, ee = rel_linf(rg, ro), rel_linf(jg, jo), rel_linf(eg, eo)
-    print(f"thermal {lattice} {weight} order {order} E {E}: rho {er:.2e} j {ej:.2e} energy {ee:.2e}")
+    print(f"thermal {lattice} {weight} order {order} E {E} {steps} steps: rho {er:.2e} j {ej:.2e} energy {ee:.2e}")
     assert er <= 1e-5 and ej <= 1e-5 and ee <= 1e-5, (er, ej, ee)
     assert abs(tg[0] / to[0] - 1) < 1e-6 and abs(tg[2] / to[2] - 1) < 1e-6
     assert abs(tg[1] - to[1]) < 1e-5 * max(abs(to[1]), to[0] * 0.02)
@@ -165,7 +172,7 @@ def test_thermal_parity_16bit(storage):
             fr = _floor(lattice, weight, tau, E, order, steps, fields, storage, sd)
             for k, (a, b) in enumerate(zip(fr, (ro, jo, eo))):
                 floors[k] = max(floors[k], rel_linf(a, b))
-    bounds = [TOL[storage] if fl < TOL[storage] else FLOOR_FACTOR * fl for fl in floors]
+    bounds = [max(TOL[storage], FLOOR_FACTOR * fl) for fl in floors]
     print(f"thermal {storage}: errors {errs}, floors {floors}, bounds {bounds}")
     assert all(e <= b for e, b in zip(errs, bounds)), (errs, floors)
 
