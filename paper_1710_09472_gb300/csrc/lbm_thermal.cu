@@ -64,8 +64,26 @@ __device__ __forceinline__ int wrapx(int x, int nx) {
     return x;
 }
 
-// The equilibrium deviations heq~_a (scaled) of one cell (a < Q).
+// Lattice velocities as compile-time constants: rest, then opposite pairs
+// (D1V5: 0, +-1, +-3; D1V7: 0, +-1, +-2, +-3), as lbm_thermal_create sets them.
 template <int Q>
+__host__ __device__ constexpr int t_e(int a) {
+    return a == 0 ? 0 : ((a & 1) ? 1 : -1) * (Q == 5 ? (a <= 2 ? 1 : 3) : (a + 1) / 2);
+}
+// x - e_a with periodic wrap, for rows of at least 3 cells
+template <int Q>
+__device__ __forceinline__ int t_src(int x, int a, int nx) {
+    int s = x - t_e<Q>(a);
+    s = s < 0 ? s + nx : s;
+    return s >= nx ? s - nx : s;
+}
+
+// The equilibrium deviations heq~_a (scaled) of one cell (a < Q).  The
+// lattice pairs a, a + 1 have xi_{a+1} = -xi_a, so W_N,a+1 = (-1)^N W_N,a
+// (checked on the host): heq_a = even + odd and heq_{a+1} = even - odd with
+// even = sum over N = 0, 2, 4 and odd = sum over N = 1, 3; the rest
+// population has no odd part.  With kLo the hi + lo weight pairs are used.
+template <int Q, bool kLo>
 __device__ __forceinline__ void t_equilibrium(const TParams& p, float drho, float rho, float us, float dth,
                                               float* heq) {
     const float srho = p.scale * rho;
@@ -85,12 +103,14 @@ __device__ __forceinline__ void t_equilibrium(const TParams& p, float drho, floa
         A4 = srho * (3.f * S + 6.f * u2 * T + p.c4 * u2 * u2);
     }
     const float A[5] = {drho, A1, A2, A3, A4};
+    auto term = [&](int N, int a) { return kLo ? fmaf(p.Wlo[N][a], A[N], p.W[N][a] * A[N]) : p.W[N][a] * A[N]; };
+    heq[0] = term(0, 0) + term(2, 0) + term(4, 0);
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        float s = 0.f;
-#pragma unroll
-        for (int N = 0; N < 5; ++N) s += fmaf(p.Wlo[N][a], A[N], p.W[N][a] * A[N]);
-        heq[a] = s;
+    for (int a = 1; a < Q; a += 2) {
+        const float even = term(0, a) + term(2, a) + term(4, a);
+        const float odd = term(1, a) + term(3, a);
+        heq[a] = even + odd;
+        heq[a + 1] = even - odd;
     }
 }
 
@@ -112,24 +132,48 @@ __global__ void __launch_bounds__(kTBlock) k_thermal_step(const typename S::T* _
                                                           typename S::T* __restrict__ Pout, TParams p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= p.nx) return;
+    // FP32 storage: the moments as double-float sums (the first FP32
+    // rounding of a moment would otherwise recur in every step) and the
+    // hi + lo equilibrium weights; 16-bit storage rounds far coarser, so
+    // there plain FP32 sums over the pairs a, a + 1 suffice.
+    constexpr bool kExact = sizeof(typename S::T) == 4;
     float h[Q], heq[Q];
-    // the moments as double-float sums (the first FP32 rounding of a moment
-    // would otherwise recur in every step)
     float dh = 0.f, dl = 0.f, jh = 0.f, jl = 0.f, mh = 0.f, ml = 0.f;
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        h[a] = S::cvt(Pin[(int64_t)a * p.nx + wrapx(x - p.e[a], p.nx)]);
-        float e;
-        t_two_sum(dh, h[a], dh, e);
-        dl += e;
-        t_acc(jh, jl, h[a], p.xi[a]);
-        t_acc(mh, ml, h[a], p.xim[a]);
+    for (int a = 0; a < Q; ++a)
+        h[a] = S::cvt(Pin[(int64_t)a * p.nx + (p.nx >= 3 ? t_src<Q>(x, a, p.nx) : wrapx(x - p.e[a], p.nx))]);
+    if (kExact) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            float e;
+            t_two_sum(dh, h[a], dh, e);
+            dl += e;
+            t_acc(jh, jl, h[a], p.xi[a]);
+            t_acc(mh, ml, h[a], p.xim[a]);
+        }
+    } else {
+        dh = h[0];
+        mh = p.xim[0] * h[0];
+#pragma unroll
+        for (int a = 1; a < Q; a += 2) {
+            const float sa = h[a] + h[a + 1], da = h[a] - h[a + 1];
+            dh += sa;
+            jh = fmaf(p.xi[a], da, jh);
+            mh = fmaf(p.xim[a], sa, mh);
+        }
     }
     const float drho = dh + dl, j = jh + jl, m2 = mh + ml;
     const float rho = p.rho0 + drho * p.inv_scale;
-    const float u = j * p.inv_scale / rho;
-    const float dth = m2 * p.inv_scale / rho - u * u;
-    t_equilibrium<Q>(p, drho, rho, u + p.tau * p.E, dth, heq);
+    float u, dth;
+    if (kExact) {
+        u = j * p.inv_scale / rho;
+        dth = m2 * p.inv_scale / rho - u * u;
+    } else {
+        const float ir = p.inv_scale / rho;
+        u = j * ir;
+        dth = m2 * ir - u * u;
+    }
+    t_equilibrium<Q, kExact>(p, drho, rho, u + p.tau * p.E, dth, heq);
     const float omm = 1.f - p.omega;
     float rest = dh;
     uint32_t r = 0;
@@ -175,7 +219,7 @@ __global__ void __launch_bounds__(kTBlock) k_thermal_init(typename S::T* __restr
         const float uu = u ? u[x] : 0.f;
         const float dth = th ? th[x] - p.thw : 0.f;
         float heq[Q];
-        t_equilibrium<Q>(p, (r - p.rho0) * p.scale, r, uu, dth, heq);
+        t_equilibrium<Q, sizeof(typename S::T) == 4>(p, (r - p.rho0) * p.scale, r, uu, dth, heq);
         S::put(P + (int64_t)a * p.nx + y, heq[a]);
     }
 }
@@ -473,6 +517,8 @@ lbm_status lbm_thermal_create(lbm_thermal** out, int lattice, int stat, double t
     }
     bool ok = x > 0.0;
     for (int a = 0; a < t->Q; ++a) ok = ok && t->w[a] > 0.0;
+    for (int a = 0; a < t->Q; ++a)  // the kernels' compile-time velocities
+        ok = ok && t->e[a] == (t->Q == 5 ? t_e<5>(a) : t_e<7>(a));
     if (!ok) {
         delete t;
         return LBM_ERR_UNSTABLE_LATTICE;
@@ -480,6 +526,19 @@ lbm_status lbm_thermal_create(lbm_thermal** out, int lattice, int stat, double t
     t->cs = std::sqrt(x);
     t->thw = I2 / I0;
     t->g = I0 * I4 / (I2 * I2);
+    {  // the pair symmetry the equilibrium kernel relies on: W_N,a+1 = (-1)^N W_N,a, no odd rest term
+        const TParams tp = tparams(t);
+        bool sym = tp.W[1][0] == 0.f && tp.W[3][0] == 0.f && tp.Wlo[1][0] == 0.f && tp.Wlo[3][0] == 0.f;
+        for (int a = 1; a < t->Q; a += 2)
+            for (int N = 0; N <= 4; ++N) {
+                const float sg = (N & 1) ? -1.f : 1.f;
+                sym = sym && tp.W[N][a + 1] == sg * tp.W[N][a] && tp.Wlo[N][a + 1] == sg * tp.Wlo[N][a];
+            }
+        if (!sym) {
+            delete t;
+            return LBM_ERR_INVALID_ARG;
+        }
+    }
     const size_t elem = storage == LBM_F32 ? 4 : 2;
     const size_t bytes = (size_t)t->Q * (size_t)nx * elem;
     const int64_t nb = tgrid(nx);
