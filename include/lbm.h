@@ -163,6 +163,25 @@ lbm_status lbm_set_rounding_seed(lbm_ctx* ctx, uint32_t seed);
  * E or B may be NULL (unchanged).  Errors: INVALID_ARG (tau <= 1/2). */
 lbm_status lbm_set_params(lbm_ctx* ctx, double tau, const double E[3], const double B[3]);
 
+/* Local chemical-potential model (enable != 0; 0 switches back).  The
+ * collision uses the second-order EDF of Sec. 9.1, Eq. feq-exp-2nd-order-eq,
+ * with the thetabar terms that Sec. 9.1 freezes at the weight's value taken
+ * per cell: thetabar(x) = I_2/I_0 = theta g_{D/2+1}(z) / (2 g_{D/2}(z)) at the
+ * chemical potential of the cell's density (Eq. rho-def-eq, inverted as in
+ * Sec. 9.1.2), i.e. the weight-equals-EDF choice of Sec. 5, Eq. omega-feq,
+ * for the density while the lattice (c_s, w_a) stays the weight's.  Densities
+ * are in units where rho0 is the weight's own density I_0(mu): a cell of
+ * density rho has I_0(mu(x)) = (rho / rho0) I_0(mu).  thetabar comes from a
+ * table over rho / rho0 in [1/4, 4] (3841 nodes, cubic Hermite; outside that
+ * range the end value is used), built on the device when the model is
+ * enabled (FD weight; with the MB weight thetabar does not depend on mu and
+ * the model equals the default one).  The steps of this model run on the
+ * general step kernel.  lbm_init_equilibrium keeps the default EDF; the
+ * local thetabar enters from the first collision.
+ * Errors: INVALID_ARG (D3V27, D1V3 or the BE weight: not built), OOM, CUDA.
+ * lbm_adjoint returns STATE while the model is enabled (no reverse step). */
+lbm_status lbm_set_local_mu(lbm_ctx* ctx, int enable);
+
 /* Start state f(x, 0) = f^eq(rho(x), u(x)) on fluid cells (Sec. 9.1 EDF, no
  * force shift).  rho[N] FP32 (NULL = rho0 everywhere) and u[D * N] FP32 in
  * xi units (NULL = 0), host or device.  Sets the step counter to 0.

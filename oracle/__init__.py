@@ -12,6 +12,10 @@ Functions and the passages they follow:
   Model              Sec. 8 + Table lattices-tab (lattices), Sec. 9.1 (EDF, step)
   Model.equilibrium  Sec. 9.1, Eq. feq-reduced-applied-electrons-in-metals-eq
   Model.force_term   Sec. 7, Eq. forcing-term-integrals-eq
+  Model.equilibrium_thetabar, Model.step_local_mu
+                     Sec. 9.1, Eq. feq-exp-2nd-order-eq with the cell's own
+                     thetabar = I_2/I_0 at its chemical potential (Sec. 5, Eq.
+                     omega-feq; the lattice stays the weight's)
   Model.step         Sec. 9.1 discrete Boltzmann equation (collide, then stream)
   Model.adjoint      reverse sweep of Model.step (chain rule of the above)
 
@@ -85,6 +89,9 @@ def _load():
     lib.or_equilibrium.argtypes = [vp, ctypes.c_double, dp, dp]
     lib.or_force_term.argtypes = [vp, ctypes.c_double, dp, dp, dp]
     lib.or_collide_cell.argtypes = [vp, dp, dp, dp]
+    lib.or_equilibrium_thetabar.argtypes = [vp, ctypes.c_double, dp, ctypes.c_double, dp]
+    lib.or_collide_cell_thetabar.argtypes = [vp, dp, dp, ctypes.c_double, dp]
+    lib.or_step_thetabar.argtypes = [vp, i64p, u8p, dp, dp, dp, dp]
     lib.or_init_equilibrium.argtypes = [vp, i64p, u8p, dp, dp, dp]
     lib.or_step.argtypes = [vp, i64p, u8p, dp, dp, dp, ctypes.c_int64]
     lib.or_moments.argtypes = [vp, i64p, u8p, dp, dp, dp, dp]
@@ -191,6 +198,7 @@ class Model:
         if rc != 0:
             raise ValueError("bad model arguments")
         self.vel, self.stat, self.force, self.tau = vel, stat, force, tau
+        self.theta, self.mu = theta, mu
         self.D = {"D1V3": 1, "D2V9": 2}.get(vel, 3)
         self.E = E3.copy()
         self.B = B3.copy()
@@ -216,6 +224,25 @@ class Model:
         u3[: len(u)] = u
         out = np.zeros(self.Q)
         _load().or_equilibrium(self._buf, float(rho), _dp(u3), _dp(out))
+        return out
+
+    def equilibrium_thetabar(self, rho: float, u, thetabar: float) -> np.ndarray:
+        """Eq. feq-exp-2nd-order-eq with the reduced temperature as an argument."""
+        u3 = np.zeros(3)
+        u3[: len(u)] = u
+        out = np.zeros(self.Q)
+        _load().or_equilibrium_thetabar(self._buf, float(rho), _dp(u3), float(thetabar), _dp(out))
+        return out
+
+    def collide_cell_thetabar(self, fc: np.ndarray, thetabar: float, E=None) -> np.ndarray:
+        fc = np.ascontiguousarray(fc, dtype=np.float64)
+        E3 = np.zeros(3)
+        if E is None:
+            E3[:] = self._uniform_E()
+        else:
+            E3[: len(E)] = E
+        out = np.zeros(self.Q)
+        _load().or_collide_cell_thetabar(self._buf, _dp(fc), _dp(E3), float(thetabar), _dp(out))
         return out
 
     def force_term(self, rho: float, u, E) -> np.ndarray:
@@ -286,6 +313,33 @@ class Model:
         _load().or_moments(self._buf, n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _u8p(solid_a),
                            _dp(np.ascontiguousarray(f)), _dp(rho), _dp(j), _dp(tot))
         return rho.reshape(shape), j.reshape((self.D,) + tuple(shape)), tot
+
+    def local_thetabar(self, rho, rho_ref: float | None = None) -> np.ndarray:
+        """thetabar(x) = I_2/I_0 at the chemical potential mu(x) of the cell:
+        I_0(mu(x)) = rho(x) I_0(mu_w) / rho_ref (Sec. 9.1, Eq. rho-def-eq; the
+        density is in units where rho_ref is the weight's own density, by
+        default rho_ref = I_0(mu_w), i.e. physical units)."""
+        return thetabar_of_density(self.D, self.stat, self.theta, self.mu, rho, rho_ref)
+
+    def step_local_mu(self, shape, solid, f: np.ndarray, nsteps: int, Efield=None,
+                      rho_ref: float | None = None) -> np.ndarray:
+        """Advance f in place by nsteps steps of the model with the local
+        thetabar: before each collision every fluid cell takes thetabar from
+        its own density (local_thetabar), then Eq. feq-exp-2nd-order-eq."""
+        n = self._dims(shape)
+        N = int(np.prod(n))
+        assert f.shape == (self.Q * N,)
+        solid_a = None if solid is None else np.ascontiguousarray(solid, dtype=np.uint8).reshape(N)
+        E_a = None if Efield is None else np.ascontiguousarray(Efield, dtype=np.float64).reshape(self.D * N)
+        fluid = np.ones(N, dtype=bool) if solid_a is None else solid_a == 0
+        tmp = np.empty_like(f)
+        for _ in range(nsteps):
+            rho = self.moments(shape, solid, f)[0].reshape(N)
+            thb = np.full(N, self.const["thetabar"])
+            thb[fluid] = self.local_thetabar(rho[fluid], rho_ref)
+            _load().or_step_thetabar(self._buf, n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _u8p(solid_a),
+                                     _dp(E_a), _dp(thb), _dp(f), _dp(tmp))
+        return f
 
     def trajectory(self, shape, solid, f0: np.ndarray, nsteps: int, Efield=None) -> np.ndarray:
         """States f_0..f_T stacked as (T+1, Q*N)."""
@@ -465,3 +519,49 @@ def density_of_mu(D: int, theta: float, mu: float, stat: str = "fd") -> float:
 def mu_of_density(D: int, theta: float, rho: float, stat: str = "fd") -> float:
     """The inverse of density_of_mu (Sec. 9.1.2), by bisection."""
     return float(_load().or_mu_of_density(int(D), BE_STAT[stat], float(theta), float(rho)))
+
+
+def thetabar_of_mu(D: int, theta: float, mu: float, stat: str = "fd") -> float:
+    """thetabar = I_2 / I_0 of the FD/BE/MB distribution at (theta, mu)
+    (Sec. 9.1; the weight integrals of Sec. 3, Eq. i2n-cont2)."""
+    I = weight_integrals(D, stat, theta, mu, nmax=1)
+    return float(I[1] / I[0])
+
+
+def _thetabar_2d_closed(stat: str, theta: float, mu_w: float, r: np.ndarray) -> np.ndarray:
+    """D = 2 in closed form: I_0 = pi theta g_1(z), I_2 = (theta/2) pi theta
+    g_2(z), so thetabar = theta g_2(z) / (2 g_1(z)) (Sec. 9.1) with
+    g_1 = ln(1 + z), g_2 = -Li_2(-z) (FD) and g_1 = -ln(1 - z), g_2 = Li_2(z)
+    (BE); the cell's g_1 is r times the weight's."""
+    from scipy.special import spence  # spence(x) = Li_2(1 - x)
+
+    eta_w = mu_w / theta
+    if stat == "fd":
+        g1w = np.log1p(np.exp(eta_w)) if eta_w < 30 else eta_w + np.log1p(np.exp(-eta_w))
+        g1 = r * g1w
+        z = np.expm1(g1)
+        g2 = -spence(1.0 + z)
+    else:
+        g1w = -np.log1p(-np.exp(eta_w))
+        g1 = r * g1w
+        z = -np.expm1(-g1)
+        g2 = spence(1.0 - z)
+    return theta * g2 / (2.0 * g1)
+
+
+def thetabar_of_density(D: int, stat: str, theta: float, mu_w: float, rho, rho_ref: float | None = None):
+    """thetabar of cells of density rho: I_2/I_0 at the mu with
+    I_0(mu) = rho I_0(mu_w) / rho_ref (rho_ref defaults to I_0(mu_w)).  MB:
+    thetabar does not depend on mu; D = 2 FD/BE: closed form; otherwise mu by
+    mu_of_density and thetabar by thetabar_of_mu, cell by cell (slow)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    if stat == "mb":
+        return np.full(rho.shape, thetabar_of_mu(D, theta, mu_w, stat))
+    I0w = density_of_mu(D, theta, mu_w, stat)
+    r = rho / (I0w if rho_ref is None else rho_ref)
+    if D == 2:
+        return _thetabar_2d_closed(stat, theta, mu_w, r)
+    out = np.empty(rho.shape)
+    for i, ri in np.ndenumerate(r):
+        out[i] = thetabar_of_mu(D, theta, mu_of_density(D, theta, ri * I0w, stat), stat)
+    return out

@@ -423,6 +423,28 @@ void or_equilibrium(const or_model* m, double rho, const double* u, double* feq)
     }
 }
 
+/* The same discrete EDF before the constant-thetabar approximation of Sec.
+ * 9.1, Eq. feq-exp-2nd-order-eq, with the reduced temperature thetabar as an
+ * argument (the local model of the weight's own EDF with the cell's chemical
+ * potential, Sec. 5 Eq. omega-feq, on the fixed lattice of the weight):
+ *   f^eq_a = rho w_a { c0^2 + c1^2 (xi_a.u) + 1/2 c2 (c2 thetabar + c'2) xi_a^2
+ *            + c2^2/2 (xi_a.u)^2 + 1/2 c2 cbar2 (D thetabar + u^2) xi_a^2
+ *            + 1/2 (cbar2 xi_a^2 + c'2) [D (c2 thetabar + c'2) + c2 u^2
+ *                                        + D cbar2 (D thetabar + u^2)] } */
+void or_equilibrium_thetabar(const or_model* m, double rho, const double* u, double thetabar, double* feq) {
+    int a;
+    const double D = m->D, c2 = m->c2, cb = m->cbar2, cp = m->cprime2;
+    double u2 = or_dot3(u, u);
+    for (a = 0; a < m->Q; ++a) {
+        const double* xi = &m->xi[3 * a];
+        double xu = or_dot3(xi, u), x2 = or_dot3(xi, xi);
+        feq[a] = rho * m->w[a] *
+                 (m->c0 * m->c0 + m->c1 * m->c1 * xu + 0.5 * c2 * (c2 * thetabar + cp) * x2 +
+                  0.5 * c2 * c2 * xu * xu + 0.5 * c2 * cb * (D * thetabar + u2) * x2 +
+                  0.5 * (cb * x2 + cp) * (D * (c2 * thetabar + cp) + c2 * u2 + D * cb * (D * thetabar + u2)));
+    }
+}
+
 /* Explicit forcing term S_a = a_a . grad_u f^eq_a written with the weight
  * integrals (Sec. 7, Eq. forcing-term-integrals-eq):
  *   S_a = rho w_a [ xi_a.a/I2 + (xi_a.u)(xi_a.a)/I4
@@ -461,7 +483,11 @@ void or_cell_moments(const or_model* m, const double* fc, double* rho, double* j
 
 /* BGK collision of one cell, Delta t = 1 (Sec. 9.1, discrete Boltzmann):
  *   f*_a = f_a - (f_a - f^eq_a)/tau (+ S_a for the explicit force term). */
-void or_collide_cell(const or_model* m, const double* fc, const double* E, double* fout) {
+/* thb: NULL for the simulated EDF of Eq. feq-reduced-..., else a pointer to
+ * the cell's thetabar for Eq. feq-exp-2nd-order-eq.  The thetabar terms of the
+ * latter do not depend on u, so the forcing term S_a is the same for both. */
+static void or_collide_cell_th(const or_model* m, const double* fc, const double* E, const double* thb,
+                               double* fout) {
     double rho, j[3], u[3], ueq[3], feq[OR_MAXQ], S[OR_MAXQ];
     int a;
     or_cell_moments(m, fc, &rho, j);
@@ -474,13 +500,29 @@ void or_collide_cell(const or_model* m, const double* fc, const double* E, doubl
         ueq[0] = u[0] + m->tau * (E[0] + uxb[0]);
         ueq[1] = u[1] + m->tau * (E[1] + uxb[1]);
         ueq[2] = u[2] + m->tau * (E[2] + uxb[2]);
-        or_equilibrium(m, rho, ueq, feq);
+        if (thb)
+            or_equilibrium_thetabar(m, rho, ueq, *thb, feq);
+        else
+            or_equilibrium(m, rho, ueq, feq);
         for (a = 0; a < m->Q; ++a) fout[a] = fc[a] - (fc[a] - feq[a]) / m->tau;
     } else {
-        or_equilibrium(m, rho, u, feq);
+        if (thb)
+            or_equilibrium_thetabar(m, rho, u, *thb, feq);
+        else
+            or_equilibrium(m, rho, u, feq);
         or_force_term(m, rho, u, E, S);
         for (a = 0; a < m->Q; ++a) fout[a] = fc[a] - (fc[a] - feq[a]) / m->tau + S[a];
     }
+}
+
+void or_collide_cell(const or_model* m, const double* fc, const double* E, double* fout) {
+    or_collide_cell_th(m, fc, E, NULL, fout);
+}
+
+/* One cell with its own thetabar (Eq. feq-exp-2nd-order-eq). */
+void or_collide_cell_thetabar(const or_model* m, const double* fc, const double* E, double thetabar,
+                              double* fout) {
+    or_collide_cell_th(m, fc, E, &thetabar, fout);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -525,8 +567,23 @@ void or_init_equilibrium(const or_model* m, const int64_t* n, const uint8_t* sol
  * halfway bounce-back: f_a(x, t+1) = f*_a(x - e_a) if x - e_a is fluid,
  * else f*_{abar}(x).  f[Q*N] is updated in place (tmp[Q*N] is scratch).
  * Efield is NULL (uniform m->E) or [D][N]. */
+static void or_step_th(const or_model* m, const int64_t* n, const uint8_t* solid, const double* Efield,
+                       const double* thetabar, double* f, double* tmp, int64_t nsteps);
+
 void or_step(const or_model* m, const int64_t* n, const uint8_t* solid, const double* Efield, double* f,
              double* tmp, int64_t nsteps) {
+    or_step_th(m, n, solid, Efield, NULL, f, tmp, nsteps);
+}
+
+/* One step with a per-cell thetabar[N] (Eq. feq-exp-2nd-order-eq in every
+ * fluid cell); the caller evaluates thetabar from the cells' densities. */
+void or_step_thetabar(const or_model* m, const int64_t* n, const uint8_t* solid, const double* Efield,
+                      const double* thetabar, double* f, double* tmp) {
+    or_step_th(m, n, solid, Efield, thetabar, f, tmp, 1);
+}
+
+static void or_step_th(const or_model* m, const int64_t* n, const uint8_t* solid, const double* Efield,
+                       const double* thetabar, double* f, double* tmp, int64_t nsteps) {
     int64_t N = n[0] * n[1] * n[2], t;
     for (t = 0; t < nsteps; ++t) {
         int64_t c;
@@ -540,7 +597,7 @@ void or_step(const or_model* m, const int64_t* n, const uint8_t* solid, const do
             }
             for (a = 0; a < m->Q; ++a) fc[a] = f[a * N + c];
             or_cell_E(m, Efield, N, c, E);
-            or_collide_cell(m, fc, E, fo);
+            or_collide_cell_th(m, fc, E, thetabar ? &thetabar[c] : NULL, fo);
             for (a = 0; a < m->Q; ++a) tmp[a * N + c] = fo[a];
         }
 #pragma omp parallel for schedule(static)

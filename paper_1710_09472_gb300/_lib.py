@@ -35,6 +35,7 @@ SIGNATURES = {
     "lbm_set_params": (_i, [_vp, _d, _vp, _vp]),
     "lbm_set_rounding": (_i, [_vp, _i]),
     "lbm_set_rounding_seed": (_i, [_vp, ctypes.c_uint32]),
+    "lbm_set_local_mu": (_i, [_vp, _i]),
     "lbm_thermal_create": (_i, [ctypes.POINTER(_vp), _i, _i, _d, _d, _i64, _d, _d, _i, _i, _vp]),
     "lbm_thermal_destroy": (None, [_vp]),
     "lbm_thermal_constants": (_i, [_vp, _vp, _i]),

@@ -162,6 +162,11 @@ int lattice_esq(int vel, int a) {
 
 }  // namespace
 
+// Local chemical-potential table: nodes r = rho / rho0 = 1 + (k - kLmuK1) kLmuDr,
+// k = 0 .. kLmuNodes - 1, i.e. r from 1/4 to 4 in steps of 1/1024.
+constexpr int kLmuK1 = 768, kLmuNodes = 3841;
+constexpr double kLmuDr = 1.0 / 1024.0;
+
 lbm::KParams lbm::make_params(const lbm_ctx* c) {
     KParams p;
     std::memset(&p, 0, sizeof p);
@@ -205,6 +210,16 @@ lbm::KParams lbm::make_params(const lbm_ctx* c) {
     p.lgofs = 0;
     p.status = c->status_dev;
     p.seed = c->rseed;
+    if (c->lmu_tab) {
+        // table coordinate (rho / rho0 - 1) / dr + k1 from the scaled deviation drho~
+        p.lmu_tab = c->lmu_tab;
+        p.lmu_n = kLmuNodes;
+        p.lmu_a = (float)(1.0 / (c->scale * c->lat.rho0 * kLmuDr));
+        p.lmu_b = (float)kLmuK1;
+        const double g = c->c2 + c->D * c->cbar2;
+        for (int sh = 1; sh <= 3; ++sh)
+            p.lmu_K[sh] = (float)(0.5 * g * (g * sh / (c->cs * c->cs) + c->D * c->cprime2));
+    }
     return p;
 }
 
@@ -506,6 +521,7 @@ void lbm_destroy(lbm_ctx* c) {
     ws_release(c);
     cudaFree(c->pop[0]);
     cudaFree(c->pop[1]);
+    cudaFree(c->lmu_tab);
     cudaFree(c->nbr);
     cudaFree(c->lbase);
     cudaFree(c->rowG);
@@ -586,6 +602,44 @@ lbm_status lbm_set_rounding(lbm_ctx* c, int stochastic) {
 lbm_status lbm_set_rounding_seed(lbm_ctx* c, uint32_t seed) {
     if (!c) return LBM_ERR_INVALID_ARG;
     c->rseed = seed;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_local_mu(lbm_ctx* c, int enable) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (!enable) {
+        cudaFree(c->lmu_tab);
+        c->lmu_tab = nullptr;
+        return LBM_OK;
+    }
+    if (c->lat.vel != LBM_D2V9 && c->lat.vel != LBM_D3V19)
+        return fail(c, LBM_ERR_INVALID_ARG, "lbm_set_local_mu: built for D2V9 and D3V19 only");
+    if (c->lat.stat == LBM_BE)
+        return fail(c, LBM_ERR_INVALID_ARG, "lbm_set_local_mu: built for the FD and MB weights only");
+    if (c->lmu_tab) return LBM_OK;
+    float2* tab = nullptr;
+    cudaError_t e = cudaMalloc((void**)&tab, sizeof(float2) * kLmuNodes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "lbm_set_local_mu: %s",
+                    cudaGetErrorString(e));
+    }
+    lbm_status st = LBM_OK;
+    if (c->lat.stat == LBM_MB) {  // thetabar = theta whatever mu: the table is zero
+        e = cudaMemsetAsync(tab, 0, sizeof(float2) * kLmuNodes, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            st = LBM_ERR_CUDA;
+        }
+    } else {
+        st = lbm::build_local_mu_table(c->D, c->lat.theta, c->lat.mu, kLmuNodes, kLmuK1, kLmuDr, tab, c->stream);
+    }
+    if (st != LBM_OK) {
+        cudaFree(tab);
+        return fail(c, st, "lbm_set_local_mu: table build failed");
+    }
+    c->lmu_tab = tab;
     return LBM_OK;
 }
 
@@ -848,6 +902,8 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
     if (!c->has_state) return fail(c, LBM_ERR_STATE, "lbm_adjoint before lbm_init_equilibrium");
     if (t_end < 1 || t_begin < -1 || t_begin >= t_end)
         return fail(c, LBM_ERR_INVALID_ARG, "lbm_adjoint: need -1 <= t_begin < t_end and t_end >= 1");
+    if (c->lmu_tab)
+        return fail(c, LBM_ERR_STATE, "lbm_adjoint: no reverse step for the local-mu model (lbm_set_local_mu)");
 
     if ((dL_dE && !is_device_ptr(dL_dE)) || (dL_df0 && !is_device_ptr(dL_df0)))
         return fail(c, LBM_ERR_INVALID_ARG, "lbm_adjoint: dL_dE and dL_df0 must be device pointers");

@@ -137,16 +137,7 @@ __global__ void k_density_from_mu(FdTable T, double inv_theta, double lnpref, co
 
 // Solve G(eta) = target: G increases with eta.  Newton from the classical or
 // the degenerate estimate, kept inside a bracket that every step narrows.
-__global__ void k_mu_from_density(FdTable T, double theta, double lnpref, const float* __restrict__ rho,
-                                  float* __restrict__ mu, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double r = (double)rho[i];
-    if (!(r > 0.0) || isinf(r)) {
-        mu[i] = nanf("");
-        return;
-    }
-    const double target = log(r) - lnpref;
+__device__ double eta_of_G(const FdTable& T, double target) {
     double lo = -800.0, hi = 1e9;
     double eta = target < 0.0 ? target : exp((target + T.lgam1) / T.nu);
     for (int it = 0; it < 100; ++it) {
@@ -163,12 +154,48 @@ __global__ void k_mu_from_density(FdTable T, double theta, double lnpref, const 
         if (next == eta) break;
         eta = next;
     }
-    mu[i] = (float)(eta * theta);
+    return eta;
+}
+
+__global__ void k_mu_from_density(FdTable T, double theta, double lnpref, const float* __restrict__ rho,
+                                  float* __restrict__ mu, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double r = (double)rho[i];
+    if (!(r > 0.0) || isinf(r)) {
+        mu[i] = nanf("");
+        return;
+    }
+    mu[i] = (float)(eta_of_G(T, log(r) - lnpref) * theta);
+}
+
+// Local chemical-potential table: thetabar = I_2/I_0 = (theta/2) g_{nu+1} / g_nu
+// (Sec. 9.1, nu = D/2) at the eta with ln g_nu(e^eta) = ln r + ln g_nu(e^eta_w)
+// (rho proportional to g_nu, Eq. rho-def-eq), and its r-derivative
+// dthetabar/dr = thetabar (G'_{nu+1} - G'_nu) / (r G'_nu).
+__global__ void k_lmu_table(FdTable Tn, FdTable Tn1, double theta, double eta_w, int n, int k1, double dr,
+                            float2* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double Gw, Gpw, G1w, G1pw;
+    lng(Tn, eta_w, Gw, Gpw);
+    lng(Tn1, eta_w, G1w, G1pw);
+    const double th1 = 0.5 * theta * exp(G1w - Gw);
+    const double r = 1.0 + (k - k1) * dr;
+    const double eta = k == k1 ? eta_w : eta_of_G(Tn, log(r) + Gw);
+    double G, Gp, G1, G1p;
+    lng(Tn, eta, G, Gp);
+    lng(Tn1, eta, G1, G1p);
+    const double th = 0.5 * theta * exp(G1 - G);
+    const double dth = th * (G1p - Gp) / (r * Gp);
+    out[k] = make_float2((float)(th - th1), (float)(dth * dr));
 }
 
 std::mutex g_mu;
-double* g_tab[kMaxDev][4] = {};  // per device and dimension: G then G' (2 kNodes doubles)
+double* g_tab[kMaxDev][6] = {};  // per device and 2 nu = 1..5: G then G' (2 kNodes doubles)
 
+// The table of nu = D/2 (D = 1..5: the densities of D = 1..3 dimensions and
+// the g_{D/2+1} of thetabar).
 lbm_status table_for(int D, cudaStream_t s, FdTable* T) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
@@ -228,6 +255,29 @@ lbm_status convert(int D, double theta, const float* in, float* out, int64_t n, 
 }
 
 }  // namespace
+
+namespace lbm {
+
+lbm_status build_local_mu_table(int D, double theta, double mu_w, int n, int k1, double dr, float2* out,
+                                cudaStream_t s) {
+    if (D < 1 || D > 3 || !(theta > 0.0) || !std::isfinite(mu_w) || n < 2 || k1 < 0 || k1 >= n || !(dr > 0.0) ||
+        !out)
+        return LBM_ERR_INVALID_ARG;
+    FdTable Tn, Tn1;
+    lbm_status st = table_for(D, s, &Tn);
+    if (st == LBM_OK) st = table_for(D + 2, s, &Tn1);
+    if (st != LBM_OK) return st;
+    k_lmu_table<<<(n + 127) / 128, 128, 0, s>>>(Tn, Tn1, theta, mu_w / theta, n, k1, dr, out);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
+}
+
+}  // namespace lbm
 
 extern "C" {
 

@@ -298,6 +298,16 @@ struct KParams {
     // host-mapped status word: a kernel whose bounded wait ran out writes a
     // nonzero code here (read by the next synchronising API call)
     int* status;
+    // Local chemical-potential model (lbm_set_local_mu; null table: off):
+    // dth(r) = thetabar(r) - thetabar_w at r = rho / rho0 as a cubic Hermite
+    // table of (dth, dth' dr) pairs on lmu_n uniform nodes; the table
+    // coordinate is drho~ lmu_a + lmu_b (clamped to the table).  lmu_K[s] is
+    // K_s = 1/2 (c2 + D cbar2) [(c2 + D cbar2) |e|^2 / c_s^2 + D c'2] of the
+    // shell |e|^2 = s: the EDF gains rho w_a K_a dth.
+    const float2* lmu_tab;
+    float lmu_a, lmu_b;
+    int lmu_n;
+    float lmu_K[4];
 };
 
 struct Launch {
@@ -355,6 +365,13 @@ int launch_adjoint_step(int vel, int storage, int force, bool efield, bool in_wi
                         cudaStream_t s);
 int launch_reduce_slots(const double* slots, int64_t n_blocks, int n_slots, double* out, cudaStream_t s);
 int launch_accumulate_totals(const double* partials, int64_t n_partials, double* acc4, cudaStream_t s);
+
+// Local chemical-potential table (lbm_fd.cu): for the FD weight of dimension D
+// at (theta, mu_w), node k of n at r_k = 1 + (k - k1) dr holds
+// (thetabar(r_k) - thetabar(1), dthetabar/dr (r_k) dr), where thetabar(r) =
+// I_2/I_0 at the mu with I_0(mu) = r I_0(mu_w).  Synchronises the stream.
+lbm_status build_local_mu_table(int D, double theta, double mu_w, int n, int k1, double dr, float2* out,
+                                cudaStream_t s);
 
 }  // namespace lbm
 
@@ -424,6 +441,7 @@ struct lbm_ctx {
     AdjWorkspace ws;               // lbm_adjoint buffers kept between calls
     size_t mem_budget = 0;         // device bytes an lbm_adjoint call may allocate (0: free memory)
     int64_t adj_stats[4] = {0, 0, 0, 0};  // last lbm_adjoint: schedule, state buffers, forward steps, reverse steps
+    float2* lmu_tab = nullptr;     // local-mu model table (null: off)
     int* status_host = nullptr;    // mapped pinned word written by kernels on a wait timeout
     int* status_dev = nullptr;     // its device address
     float* stage = nullptr;  // device staging for host-pointer arguments

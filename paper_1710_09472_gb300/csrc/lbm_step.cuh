@@ -56,10 +56,28 @@ __device__ __forceinline__ V vedot(int a, const V* v) {
     return r;
 }
 
+// Local chemical-potential model (LMU): the EDF of Sec. 9.1, Eq.
+// feq-exp-2nd-order-eq, keeps its thetabar terms with the cell's own
+// thetabar(rho) instead of the weight's thetabar_w; they add
+// rho w_a K_a (thetabar - thetabar_w) with K_a a constant of the shell
+// |e_a|^2 (KParams::lmu_K), no u dependence (so neither forcing form changes)
+// and sum_a w_a K_a = 0 (the rest population's share follows from the mass
+// closure).  lmu_kd returns w s rho (thetabar - thetabar_w) from the table.
+__device__ __forceinline__ float lmu_kd(const KParams& p, float drho, float rho) {
+    float x = fmaf(drho, p.lmu_a, p.lmu_b);
+    x = fminf(fmaxf(x, 0.f), (float)(p.lmu_n - 1));  // also maps NaN to node 0
+    const int i = min((int)x, p.lmu_n - 2);
+    const float t = x - (float)i, t2 = t * t, t3 = t2 * t;
+    const float2 a = __ldg(p.lmu_tab + i), b = __ldg(p.lmu_tab + i + 1);
+    const float d = (2.f * t3 - 3.f * t2 + 1.f) * a.x + (t3 - 2.f * t2 + t) * a.y + (3.f * t2 - 2.f * t3) * b.x +
+                    (t3 - t2) * b.y;
+    return p.omega * p.scale * rho * d;
+}
+
 // The post-collision values go to emit(a, h*_a, h*_a+1) pair by pair (a odd)
 // and then to emit_rest(h*_0), so a caller can round and store each pair as
 // soon as it exists instead of holding all Q values.
-template <class L, int FORCE, class V, class Emit, class EmitRest>
+template <class L, int FORCE, bool LMU = false, class V, class Emit, class EmitRest>
 __device__ __forceinline__ void collide_emit(const V* h, const V* E, const KParams& p, Emit&& emit,
                                              EmitRest&& emit_rest) {
     constexpr int kR1 = shell_first<L>(1), kR2 = shell_first<L>(2), kR3 = shell_first<L>(3);
@@ -110,12 +128,15 @@ __device__ __forceinline__ void collide_emit(const V* h, const V* E, const KPara
         cq = srho * V(p.Cp);
     }
     const V c0 = V(p.omega * p.A) * drho;
+    V kd(0.f);
+    if constexpr (LMU) kd = lmu_kd(p, drho, rho);
     V rest = drho;
     if constexpr (kR1 > 0 && kR2 > 0 && kR3 < 0) {
         // two moving shells (D2V9, D3V19): axis and diagonal
         constexpr int kAx = kR1, kDg = kR2;
+        const V c0a = LMU ? vfma(V(p.lmu_K[1]), kd, c0) : c0, c0d = LMU ? vfma(V(p.lmu_K[2]), kd, c0) : c0;
         // per shell: the even constant, the (e.u) coefficient and the odd vector
-        const V e0a = V(p.w[kAx]) * vfma(V(p.k2[kAx]), Ku, c0), e0d = V(p.w[kDg]) * vfma(V(p.k2[kDg]), Ku, c0);
+        const V e0a = V(p.w[kAx]) * vfma(V(p.k2[kAx]), Ku, c0a), e0d = V(p.w[kDg]) * vfma(V(p.k2[kDg]), Ku, c0d);
         const V cqa = V(p.w[kAx]) * cq, cqd = V(p.w[kDg]) * cq;
         V Va[3], Vd[3];
 #pragma unroll
@@ -146,7 +167,7 @@ __device__ __forceinline__ void collide_emit(const V* h, const V* E, const KPara
         for (int sh = 1; sh <= 3; ++sh) {
             const int r = sh == 1 ? kR1 : (sh == 2 ? kR2 : kR3);
             if (r < 0) continue;
-            e0[sh] = V(p.w[r]) * vfma(V(p.k2[r]), Ku, c0);
+            e0[sh] = V(p.w[r]) * vfma(V(p.k2[r]), Ku, LMU ? vfma(V(p.lmu_K[sh]), kd, c0) : c0);
             cqs[sh] = V(p.w[r]) * cq;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -170,9 +191,9 @@ __device__ __forceinline__ void collide_emit(const V* h, const V* E, const KPara
     emit_rest(rest);
 }
 
-template <class L, int FORCE>
+template <class L, int FORCE, bool LMU = false>
 __device__ __forceinline__ void collide(const float* h, const float* E, const KParams& p, float* out) {
-    collide_emit<L, FORCE>(
+    collide_emit<L, FORCE, LMU>(
         h, E, p,
         [&](int a, float ha, float hb) {
             out[a] = ha;
@@ -202,7 +223,7 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
 // 5.9e-5 after 5000 Poiseuille steps, 7.8e-5 after 2000 Riemann steps); with
 // both compensated the errors are 6e-7 and 6e-6, within 1.1x of also
 // compensating the final sum, which costs another 28% of the step.
-template <class L, int FORCE>
+template <class L, int FORCE, bool LMU = false>
 __device__ __forceinline__ void collide_acc(const float* h, const float* E, const KParams& p, float* out) {
     constexpr int kR1 = shell_first<L>(1), kR2 = shell_first<L>(2), kR3 = shell_first<L>(3);
     float drho = h[0], drho_lo = 0.f, j[3] = {0.f, 0.f, 0.f}, jl[3] = {0.f, 0.f, 0.f};
@@ -283,12 +304,13 @@ __device__ __forceinline__ void collide_acc(const float* h, const float* E, cons
     const float c0 = om * p.A * drho_f;
     const float Ku = (FORCE == 1) ? srho * (om * u2 + 2.f * uE) : om * srho * u2;
     const float cq = (FORCE == 1) ? srho * p.Cp : om * srho * p.Cp;
-    float e0[4], cqs[4];
+    float e0[4], cqs[4], kd = 0.f;
+    if constexpr (LMU) kd = lmu_kd(p, drho_f, rho);
 #pragma unroll
     for (int sh = 1; sh <= 3; ++sh) {
         const int r = sh == 1 ? kR1 : (sh == 2 ? kR2 : kR3);
         if (r < 0) continue;
-        e0[sh] = p.w[r] * (c0 + p.k2[r] * Ku);
+        e0[sh] = p.w[r] * ((LMU ? fmaf(p.lmu_K[sh], kd, c0) : c0) + p.k2[r] * Ku);
         cqs[sh] = p.w[r] * cq;
     }
     float rest = drho;
@@ -379,12 +401,12 @@ __device__ __forceinline__ void load_E(const float* __restrict__ Ef, bool ef, co
     }
 }
 
-template <class L, class S, int FORCE>
+template <class L, class S, int FORCE, bool LMU = false>
 __device__ __forceinline__ void collide_any(const float* h, const float* E, const KParams& p, float* out) {
     if (S::kBytes == 4)
-        collide_acc<L, FORCE>(h, E, p, out);
+        collide_acc<L, FORCE, LMU>(h, E, p, out);
     else
-        collide<L, FORCE>(h, E, p, out);
+        collide<L, FORCE, LMU>(h, E, p, out);
 }
 
 // General step kernel: one thread per cell, pulls straight from global memory
@@ -407,7 +429,12 @@ __global__ void __launch_bounds__(kBlock) k_step(const typename S::T* __restrict
     float E[3];
     load_E<L>(Ef, EF, p, c.cell, E);
     float out[L::Q];
-    collide_any<L, S, FORCE>(h, E, p, out);
+    // the local-mu model is built for D2V9 and D3V19 (the host refuses others)
+    constexpr bool kLmu = L::Q == 9 || L::Q == 19;
+    if (kLmu && p.lmu_tab)
+        collide_any<L, S, FORCE, kLmu>(h, E, p, out);
+    else
+        collide_any<L, S, FORCE>(h, E, p, out);
     typename S::T t[L::Q];
     round_all<L, S, SR>(out, c.cell, p, t);
     typename S::T* Gout = reinterpret_cast<typename S::T*>(reinterpret_cast<char*>(Pout) + p.gofs);
@@ -747,7 +774,9 @@ int launch_one(const void* fin, void* fout, const uint32_t* nbr, const float* Ef
     // the compile-time strides only for the benchmarked lattices (D2V9, D3V19);
     // the others take the run-time stride (fewer instantiations to compile)
     constexpr bool kFixed = L::Q == 9 || L::Q == 19;
-    if (kFixed && p.nx == 256)
+    if (p.lmu_tab)
+        done = false;  // the local-mu model runs on the general kernel only
+    else if (kFixed && p.nx == 256)
         done = launch_rows<L, S, FORCE, EF, SR, kFixed ? 256 : 0>(tag, fin, fout, nbr, Ef, p, s);
     else if (kFixed && p.nx == 512)
         done = launch_rows<L, S, FORCE, EF, SR, kFixed ? 512 : 0>(tag, fin, fout, nbr, Ef, p, s);

@@ -172,6 +172,11 @@ class LBM:
         _lib.check(_lib.load().lbm_set_rounding_seed(self._h, int(seed) & 0xFFFFFFFF), self._h,
                    "lbm_set_rounding_seed")
 
+    def set_local_mu(self, enable: bool = True):
+        """Local chemical-potential model (lbm_set_local_mu): each cell's
+        thetabar from its own density through the FD relation rho(mu)."""
+        _lib.check(_lib.load().lbm_set_local_mu(self._h, 1 if enable else 0), self._h, "lbm_set_local_mu")
+
     def init_equilibrium(self, rho=None, u=None):
         _lib.check(_lib.load().lbm_init_equilibrium(self._h, _ptr(rho, np.float32, self.N, "rho"),
                                                     _ptr(u, np.float32, self.D * self.N, "u")), self._h,
