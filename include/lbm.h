@@ -175,9 +175,10 @@ lbm_status lbm_set_params(lbm_ctx* ctx, double tau, const double E[3], const dou
  * table over rho / rho0 in [1/4, 4] (3841 nodes, cubic Hermite; outside that
  * range the end value is used), built on the device when the model is
  * enabled (FD weight; with the MB weight thetabar does not depend on mu and
- * the model equals the default one).  The steps of this model run on the
- * general step kernel.  lbm_init_equilibrium keeps the default EDF; the
- * local thetabar enters from the first collision.
+ * the model equals the default one).  Its steps run on the row-staged
+ * kernel (an instantiation with a run-time row stride) where the rows
+ * qualify, else on the general kernel.  lbm_init_equilibrium keeps the
+ * default EDF; the local thetabar enters from the first collision.
  * Errors: INVALID_ARG (D3V27, D1V3 or the BE weight: not built), OOM, CUDA.
  * lbm_adjoint returns STATE while the model is enabled (no reverse step). */
 lbm_status lbm_set_local_mu(lbm_ctx* ctx, int enable);

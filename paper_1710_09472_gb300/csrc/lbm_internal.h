@@ -300,8 +300,9 @@ struct KParams {
     int* status;
     // Local chemical-potential model (lbm_set_local_mu; null table: off):
     // dth(r) = thetabar(r) - thetabar_w at r = rho / rho0 as a cubic Hermite
-    // table of (dth, dth' dr) pairs on lmu_n uniform nodes; the table
-    // coordinate is drho~ lmu_a + lmu_b (clamped to the table).  lmu_K[s] is
+    // table of (dth, dth' dr) pairs on lmu_n uniform nodes; drho~ lmu_a is
+    // (r - 1) / dr and lmu_b the index of the node r = 1 (the coordinate is
+    // clamped to the table).  lmu_K[s] is
     // K_s = 1/2 (c2 + D cbar2) [(c2 + D cbar2) |e|^2 / c_s^2 + D c'2] of the
     // shell |e|^2 = s: the EDF gains rho w_a K_a dth.
     const float2* lmu_tab;

@@ -64,10 +64,18 @@ __device__ __forceinline__ V vedot(int a, const V* v) {
 // and sum_a w_a K_a = 0 (the rest population's share follows from the mass
 // closure).  lmu_kd returns w s rho (thetabar - thetabar_w) from the table.
 __device__ __forceinline__ float lmu_kd(const KParams& p, float drho, float rho) {
-    float x = fmaf(drho, p.lmu_a, p.lmu_b);
-    x = fminf(fmaxf(x, 0.f), (float)(p.lmu_n - 1));  // also maps NaN to node 0
-    const int i = min((int)x, p.lmu_n - 2);
-    const float t = x - (float)i, t2 = t * t, t3 = t2 * t;
+    // (r - 1) / dr relative to the node of r = 1 (index lmu_b), so that the
+    // fraction t keeps FP32's relative precision near r = 1
+    float x = drho * p.lmu_a;
+    x = fminf(fmaxf(x, -p.lmu_b), (float)(p.lmu_n - 1) - p.lmu_b);  // also maps NaN to node 0
+    const float fl = floorf(x);
+    int i = (int)fl + (int)p.lmu_b;
+    float t = x - fl;
+    if (i > p.lmu_n - 2) {  // x at the last node
+        i = p.lmu_n - 2;
+        t = 1.f;
+    }
+    const float t2 = t * t, t3 = t2 * t;
     const float2 a = __ldg(p.lmu_tab + i), b = __ldg(p.lmu_tab + i + 1);
     const float d = (2.f * t3 - 3.f * t2 + 1.f) * a.x + (t3 - 2.f * t2 + t) * a.y + (3.f * t2 - 2.f * t3) * b.x +
                     (t3 - t2) * b.y;
@@ -544,7 +552,7 @@ __device__ __forceinline__ void stage_row(unsigned char* st, const StageLayout<L
                        bar);
 }
 
-template <class L, class S, int FORCE, bool EF, bool SR, int STAGES, int RS>
+template <class L, class S, int FORCE, bool EF, bool SR, int STAGES, int RS, bool LMU = false>
 __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restrict__ Pin,
                                                    typename S::T* __restrict__ Pout, const float* __restrict__ Ef,
                                                    int gcap, int dcap, KParams p) {
@@ -637,7 +645,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
                 if (S::kBytes == 4) {
                     // FP32 storage: compensated collision
                     float out[L::Q];
-                    collide_any<L, S, FORCE>(h, E, p, out);
+                    collide_any<L, S, FORCE, LMU>(h, E, p, out);
                     typename S::T t[L::Q];
                     round_all<L, S, SR>(out, cell, p, t);
 #pragma unroll
@@ -645,7 +653,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
                 } else {
                     // 16-bit storage: each pair is rounded and stored as soon as it exists
                     Rng rng(cell, p);
-                    collide_emit<L, FORCE>(
+                    collide_emit<L, FORCE, LMU>(
                         h, E, p,
                         [&](int a, float ha, float hb) {
                             T ta, tb;
@@ -742,7 +750,7 @@ Shape launch_shape(K kernel, int nx, size_t smem) {
     return last;
 }
 
-template <class L, class S, int FORCE, bool EF, bool SR, int RS>
+template <class L, class S, int FORCE, bool EF, bool SR, int RS, bool LMU = false>
 bool launch_rows(const S*, const void* fin, void* fout, const uint32_t* nbr, const float* Ef, const KParams& p,
                  cudaStream_t s) {
     using T = typename S::T;
@@ -754,7 +762,7 @@ bool launch_rows(const S*, const void* fin, void* fout, const uint32_t* nbr, con
     const size_t stage_bytes = (size_t)L::Q * srow + 2 * (size_t)p.lorder + gcap + dcap;
     const size_t smem = (size_t)kStages * stage_bytes + (size_t)L::Q * srow;
     if (!p.rorder || row_bytes % 16 != 0 || smem > kSmemBudget || p.nx < 32 || p.nx % 4 != 0) return false;
-    auto kern = k_step_rows<L, S, FORCE, EF, SR, kStages, RS>;
+    auto kern = k_step_rows<L, S, FORCE, EF, SR, kStages, RS, LMU>;
     const Shape sh = launch_shape(kern, p.nx, smem);
     const int threads = sh.threads, blocks = sh.blocks;
     if (blocks <= 0) return false;
@@ -774,8 +782,8 @@ int launch_one(const void* fin, void* fout, const uint32_t* nbr, const float* Ef
     // the compile-time strides only for the benchmarked lattices (D2V9, D3V19);
     // the others take the run-time stride (fewer instantiations to compile)
     constexpr bool kFixed = L::Q == 9 || L::Q == 19;
-    if (p.lmu_tab)
-        done = false;  // the local-mu model runs on the general kernel only
+    if (p.lmu_tab)  // the local-mu model (D2V9, D3V19 only): run-time row stride
+        done = kFixed && launch_rows<L, S, FORCE, EF, SR, 0, kFixed>(tag, fin, fout, nbr, Ef, p, s);
     else if (kFixed && p.nx == 256)
         done = launch_rows<L, S, FORCE, EF, SR, kFixed ? 256 : 0>(tag, fin, fout, nbr, Ef, p, s);
     else if (kFixed && p.nx == 512)
