@@ -39,12 +39,11 @@ def workload_name(n: int) -> str:
             "tau=0.8 E_x=1e-6 B_z=1e-3 force=term")
 
 # DRAM traffic per 256^3 launch of the step kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum): an ncu capture of one launch on a 256 x 128 x 128
-# box of the same recipe (the same kernel instantiation, a state larger than
-# L2), scaled to 256^3 by the fluid cells; keyed by storage, with the hash of
-# the kernel source it was taken on, and reported as null once the source
-# has changed.
-NCU_TRAFFIC = {"f16": (1218625039, "6d951315d04fdc06"), "f32": (2540311240, "e2fd3d45b1b32ed8")}
+# dram__bytes_write.sum): an ncu capture of one full-size launch of the bench
+# workload (three metrics, one pass); keyed by storage, with the hash of the
+# kernel source it was taken on, and reported as null once the source has
+# changed.
+NCU_TRAFFIC = {"f16": (1361150976, "c01fcc12b6ca0cfa"), "f32": (2681568000, "7b85c36eeab6bbaf")}
 
 FALLBACK_HBM_GBS = 6800.0
 

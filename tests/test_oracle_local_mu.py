@@ -153,3 +153,23 @@ def test_local_model_sound_speed_is_the_fermi_gas_one():
     assert abs(c_fixed / want_fixed - 1) < 2e-3
     assert abs(c_local / want_local - 1) < 2e-3
     assert c_local / c_fixed > 1.2
+
+
+@pytest.mark.parametrize("vel", ["D2V9", "D3V19"])
+def test_local_term_has_shell_constants(vel):
+    """The CUDA collision adds rho w_a K_a (thetabar - thetabar_w) with
+    K_a = 1/2 (c2 + D cbar2) [(c2 + D cbar2) xi_a^2 + D c'2], one constant per
+    shell |e_a|^2, and relies on sum_a w_a K_a = 0 (the rest population's share
+    then follows from the mass closure).  Both against the oracle's full EDF."""
+    m = oracle.Model(vel, "fd", 0.1, 1.0)
+    c = m.const
+    g = c["c2"] + m.D * c["cbar2"]
+    xi2 = np.sum(m.xi ** 2, axis=1)
+    K = 0.5 * g * (g * xi2 + m.D * c["cprime2"])
+    assert abs(np.sum(m.w * K)) < 1e-12 * np.sum(m.w * np.abs(K))
+    for _ in range(4):
+        u = 0.05 * RNG.standard_normal(m.D)
+        rho = c["I0"] * (1 + 0.1 * RNG.random())
+        d = c["thetabar"] * (RNG.random() - 0.5)
+        diff = m.equilibrium_thetabar(rho, u, c["thetabar"] + d) - m.equilibrium(rho, u)
+        np.testing.assert_allclose(diff, rho * m.w * K * d, rtol=0, atol=1e-12 * rho)
