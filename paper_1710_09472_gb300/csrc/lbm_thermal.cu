@@ -43,11 +43,14 @@ struct TParams {
     float c1, c22, c3, cb3, K30, c4, cb4, db4, dp4, a4, b4, S0, T0, c45, thw;
     float rho0, omega, tau, E, scale, inv_scale;
     uint32_t step, seed;
+    uint32_t skey;        // t_hash(step * 0x9E3779B9 + seed): the step's rounding key
+    int64_t off[kTQ];     // a nx - e_a: the pull of direction a, away from the row's ends
+    int64_t plane[kTQ];   // a nx: the store of direction a
 };
 
 // The lowbias32 integer hash (C. Wellons) and one 32-bit LCG step per pair of
 // stores (Numerical Recipes constants) give the stochastic-rounding words.
-__device__ __forceinline__ uint32_t t_hash(uint32_t x) {
+__host__ __device__ __forceinline__ uint32_t t_hash(uint32_t x) {
     x ^= x >> 16;
     x *= 0x7feb352dU;
     x ^= x >> 15;
@@ -139,9 +142,18 @@ __global__ void __launch_bounds__(kTBlock) k_thermal_step(const typename S::T* _
     constexpr bool kExact = sizeof(typename S::T) == 4;
     float h[Q], heq[Q];
     float dh = 0.f, dl = 0.f, jh = 0.f, jl = 0.f, mh = 0.f, ml = 0.f;
+    // a block whose cells are all at least 3 cells from both ends of the row
+    // pulls without the periodic wrap, at fixed offsets from its own cell
+    const bool inner = (int)blockIdx.x * kTBlock >= 3 && ((int)blockIdx.x + 1) * kTBlock + 3 <= p.nx;
+    if (inner) {
+        const typename S::T* px = Pin + x;
 #pragma unroll
-    for (int a = 0; a < Q; ++a)
-        h[a] = S::cvt(Pin[(int64_t)a * p.nx + (p.nx >= 3 ? t_src<Q>(x, a, p.nx) : wrapx(x - p.e[a], p.nx))]);
+        for (int a = 0; a < Q; ++a) h[a] = S::cvt(px[p.off[a]]);
+    } else {
+#pragma unroll
+        for (int a = 0; a < Q; ++a)
+            h[a] = S::cvt(Pin[(int64_t)a * p.nx + (p.nx >= 3 ? t_src<Q>(x, a, p.nx) : wrapx(x - p.e[a], p.nx))]);
+    }
     if (kExact) {
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
@@ -177,7 +189,8 @@ __global__ void __launch_bounds__(kTBlock) k_thermal_step(const typename S::T* _
     const float omm = 1.f - p.omega;
     float rest = dh;
     uint32_t r = 0;
-    if (SR) r = t_hash((uint32_t)x ^ t_hash(p.step * 0x9E3779B9u + p.seed));
+    if (SR) r = t_hash((uint32_t)x ^ p.skey);
+    typename S::T* py = Pout + x;
 #pragma unroll
     for (int a = 1; a < Q; a += 2) {
         const float ha = fmaf(omm, h[a], p.omega * heq[a]);
@@ -191,8 +204,8 @@ __global__ void __launch_bounds__(kTBlock) k_thermal_step(const typename S::T* _
             S::put(&ta, ha);
             S::put(&tb, hb);
         }
-        Pout[(int64_t)a * p.nx + x] = ta;
-        Pout[(int64_t)(a + 1) * p.nx + x] = tb;
+        py[p.plane[a]] = ta;
+        py[p.plane[a + 1]] = tb;
     }
     rest += dl;
     typename S::T t0, unused;
@@ -444,6 +457,11 @@ TParams tparams(const lbm_thermal* t) {
     p.inv_scale = (float)(1.0 / t->scale);
     p.step = (uint32_t)t->steps;
     p.seed = t->seed;
+    p.skey = t_hash(p.step * 0x9E3779B9u + p.seed);
+    for (int a = 0; a < t->Q; ++a) {
+        p.plane[a] = (int64_t)a * t->nx;
+        p.off[a] = p.plane[a] - t->e[a];
+    }
     return p;
 }
 

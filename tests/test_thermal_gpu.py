@@ -141,6 +141,27 @@ def test_thermal_parity_f32(lattice, weight, order, E, n, steps):
     t.close()
 
 
+@pytest.mark.parametrize("lattice,weight", [("D1V7", "mb"), ("D1V5b", "mb"), ("D1V7", "be")])
+def test_thermal_parity_long_row(lattice, weight):
+    """A row of 2309 cells (FP32, order 4, with force): the blocks away from
+    both ends pull at fixed offsets without the periodic wrap, the two end
+    blocks with it.  After 150 steps every population is within 1e-6 of the
+    largest population, and rho, j and energy within 1e-5."""
+    n, tau, E, order, steps = 2309, 0.8, 1e-4, 4, 150
+    m = oracle.Thermal(lattice, *WEIGHTS[weight], tau=tau, E=E)
+    fields = _fields(n, 51, m.I[1] / m.I[0])
+    rg, jg, eg, _, t = _gpu(lattice, weight, n, tau, E, order, "f32", steps, fields)
+    f = torch.empty(t.Q * n, device="cuda")
+    t.populations(f)
+    fg = f.cpu().numpy().astype(np.float64).reshape(t.Q, n)
+    t.close()
+    ro, jo, eo, _, _, fo = _oracle(lattice, weight, tau, E, order, steps, fields)
+    fo = fo.reshape(m.Q, n)
+    assert np.max(np.abs(fg - fo)) <= 1e-6 * np.max(np.abs(fo))
+    er, ej, ee = rel_linf(rg, ro), rel_linf(jg, jo), rel_linf(eg, eo)
+    assert er <= 1e-5 and ej <= 1e-5 and ee <= 1e-5, (er, ej, ee)
+
+
 def test_populations_elementwise():
     """Every population after 7 steps (FP32 storage, D1V7, order 4)."""
     m = oracle.Thermal("D1V7", *WEIGHTS["fd03"], tau=0.7, E=1e-4)
