@@ -179,8 +179,9 @@ lbm_status lbm_set_params(lbm_ctx* ctx, double tau, const double E[3], const dou
  * kernel (an instantiation with a run-time row stride) where the rows
  * qualify, else on the general kernel.  lbm_init_equilibrium keeps the
  * default EDF; the local thetabar enters from the first collision.
- * Errors: INVALID_ARG (D3V27, D1V3 or the BE weight: not built), OOM, CUDA.
- * lbm_adjoint returns STATE while the model is enabled (no reverse step). */
+ * lbm_adjoint differentiates the model too: its reverse step adds the
+ * density derivative of the local terms (thetabar'(rho) from the same table).
+ * Errors: INVALID_ARG (D3V27, D1V3 or the BE weight: not built), OOM, CUDA. */
 lbm_status lbm_set_local_mu(lbm_ctx* ctx, int enable);
 
 /* Start state f(x, 0) = f^eq(rho(x), u(x)) on fluid cells (Sec. 9.1 EDF, no

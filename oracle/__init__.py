@@ -12,10 +12,11 @@ Functions and the passages they follow:
   Model              Sec. 8 + Table lattices-tab (lattices), Sec. 9.1 (EDF, step)
   Model.equilibrium  Sec. 9.1, Eq. feq-reduced-applied-electrons-in-metals-eq
   Model.force_term   Sec. 7, Eq. forcing-term-integrals-eq
-  Model.equilibrium_thetabar, Model.step_local_mu
+  Model.equilibrium_thetabar, Model.step_local_mu, Model.adjoint_local_mu
                      Sec. 9.1, Eq. feq-exp-2nd-order-eq with the cell's own
                      thetabar = I_2/I_0 at its chemical potential (Sec. 5, Eq.
-                     omega-feq; the lattice stays the weight's)
+                     omega-feq; the lattice stays the weight's), and its
+                     reverse sweep
   Model.step         Sec. 9.1 discrete Boltzmann equation (collide, then stream)
   Model.adjoint      reverse sweep of Model.step (chain rule of the above)
 
@@ -92,6 +93,8 @@ def _load():
     lib.or_equilibrium_thetabar.argtypes = [vp, ctypes.c_double, dp, ctypes.c_double, dp]
     lib.or_collide_cell_thetabar.argtypes = [vp, dp, dp, ctypes.c_double, dp]
     lib.or_step_thetabar.argtypes = [vp, i64p, u8p, dp, dp, dp, dp]
+    lib.or_adjoint_thetabar.argtypes = [vp, i64p, u8p, dp, dp, dp, dp, ctypes.c_int64, ctypes.c_int64, dp, dp,
+                                        dp, dp, dp, dp, dp]
     lib.or_init_equilibrium.argtypes = [vp, i64p, u8p, dp, dp, dp]
     lib.or_step.argtypes = [vp, i64p, u8p, dp, dp, dp, ctypes.c_int64]
     lib.or_moments.argtypes = [vp, i64p, u8p, dp, dp, dp, dp]
@@ -377,6 +380,38 @@ class Model:
                 "gB": gB, "gtau": float(gtau[0])}
 
 
+    def adjoint_local_mu(self, shape, solid, states: np.ndarray, t_begin: int, t_end: int, wr=None, wj=None,
+                         Efield=None, rho_ref: float | None = None):
+        """Reverse sweep of step_local_mu over its stored trajectory: as
+        adjoint(), with every cell's thetabar and d thetabar / d rho taken
+        from its density in each state."""
+        n = self._dims(shape)
+        N = int(np.prod(n))
+        assert states.shape[0] >= t_end + 1
+        solid_a = None if solid is None else np.ascontiguousarray(solid, dtype=np.uint8).reshape(N)
+        fluid = np.ones(N, dtype=bool) if solid_a is None else solid_a == 0
+        thb = np.full((t_end + 1, N), self.const["thetabar"])
+        dthb = np.zeros((t_end + 1, N))
+        for t in range(t_end + 1):
+            rho = self.moments(shape, solid, states[t])[0].reshape(N)[fluid]
+            thb[t, fluid] = self.local_thetabar(rho, rho_ref)
+            dthb[t, fluid] = thetabar_slope_of_density(self.D, self.stat, self.theta, self.mu, rho, rho_ref)
+        E_a = None if Efield is None else np.ascontiguousarray(Efield, dtype=np.float64).reshape(self.D * N)
+        wr_a = None if wr is None else np.ascontiguousarray(wr, dtype=np.float64).reshape(N)
+        wj_a = None if wj is None else np.ascontiguousarray(wj, dtype=np.float64).reshape(self.D * N)
+        st = np.ascontiguousarray(states[: t_end + 1], dtype=np.float64)
+        lam0 = np.zeros(self.Q * N)
+        gE = np.zeros(self.D * N)
+        gB = np.zeros(3)
+        gtau = np.zeros(1)
+        loss = np.zeros(1)
+        _load().or_adjoint_thetabar(self._buf, n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _u8p(solid_a),
+                                    _dp(E_a), _dp(st), _dp(thb), _dp(dthb), int(t_begin), int(t_end), _dp(wr_a),
+                                    _dp(wj_a), _dp(lam0), _dp(gE), _dp(gB), _dp(gtau), _dp(loss))
+        return {"loss": float(loss[0]), "lam0": lam0, "gE": gE.reshape((self.D,) + tuple(shape)),
+                "gB": gB, "gtau": float(gtau[0])}
+
+
 # ---------------------------------------------------------------------------
 # Fourth-order EDF and the 1D thermal model (lbm_oracle4.c).
 # ---------------------------------------------------------------------------
@@ -565,3 +600,36 @@ def thetabar_of_density(D: int, stat: str, theta: float, mu_w: float, rho, rho_r
     for i, ri in np.ndenumerate(r):
         out[i] = thetabar_of_mu(D, theta, mu_of_density(D, theta, ri * I0w, stat), stat)
     return out
+
+
+def thetabar_slope_of_density(D: int, stat: str, theta: float, mu_w: float, rho, rho_ref: float | None = None):
+    """d thetabar / d rho of thetabar_of_density.  MB: 0.  D = 2 FD/BE in
+    closed form: with g_1 = r g_1w, d g_2 / d g_1 = g_1 (1 + z) / z (FD) or
+    g_1 (1 - z) / z (BE), since d g_nu / dz = g_{nu-1} / z; otherwise a
+    central difference of thetabar_of_density with a relative step 1e-6."""
+    rho = np.asarray(rho, dtype=np.float64)
+    if stat == "mb":
+        return np.zeros(rho.shape)
+    I0w = density_of_mu(D, theta, mu_w, stat)
+    ref = I0w if rho_ref is None else rho_ref
+    if D == 2:
+        from scipy.special import spence
+
+        eta_w = mu_w / theta
+        r = rho / ref
+        if stat == "fd":
+            g1w = np.log1p(np.exp(eta_w)) if eta_w < 30 else eta_w + np.log1p(np.exp(-eta_w))
+            g1 = r * g1w
+            z = np.expm1(g1)
+            g2 = -spence(1.0 + z)
+            dg2 = g1 * (1.0 + z) / z * g1w
+        else:
+            g1w = -np.log1p(-np.exp(eta_w))
+            g1 = r * g1w
+            z = -np.expm1(-g1)
+            g2 = spence(1.0 - z)
+            dg2 = g1 * (1.0 - z) / z * g1w
+        return 0.5 * theta * (dg2 * g1 - g2 * g1w) / g1 ** 2 / ref
+    h = 1e-6 * rho
+    return (thetabar_of_density(D, stat, theta, mu_w, rho + h, rho_ref)
+            - thetabar_of_density(D, stat, theta, mu_w, rho - h, rho_ref)) / (2 * h)

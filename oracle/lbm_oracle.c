@@ -662,17 +662,32 @@ static void or_dfeq_du(const or_model* m, int a, double rho, const double* v, do
         g[d] = rho * m->w[a] * (m->c1 * m->c1 * xi[d] + m->c2 * m->c2 * xv * xi[d] + kv * v[d]);
 }
 
+/* d f^eq_a / d thetabar of Eq. feq-exp-2nd-order-eq (its thetabar terms, term
+ * by term): rho w_a [ 1/2 c2^2 xi^2 + 1/2 c2 cbar2 D xi^2
+ *                     + 1/2 (cbar2 xi^2 + c'2) (D c2 + D^2 cbar2) ] */
+static double or_dfeq_dthetabar(const or_model* m, int a, double rho) {
+    const double* xi = &m->xi[3 * a];
+    const double D = m->D, c2 = m->c2, cb = m->cbar2, x2 = or_dot3(xi, xi);
+    return rho * m->w[a] *
+           (0.5 * c2 * c2 * x2 + 0.5 * c2 * cb * D * x2 + 0.5 * (cb * x2 + m->cprime2) * (D * c2 + D * D * cb));
+}
+
 /* Adjoint of one cell's collision.  fc = pre-collision populations, lt =
  * adjoint of the post-collision populations.  Writes lam (adjoint of fc),
- * adds this cell's contributions to gE[3], gB[3], gtau[1]. */
-void or_collide_cell_adjoint(const or_model* m, const double* fc, const double* E, const double* lt,
-                             double* lam, double* gE, double* gB, double* gtau) {
+ * adds this cell's contributions to gE[3], gB[3], gtau[1].  thb: NULL for the
+ * simulated EDF, else the cell's thetabar for Eq. feq-exp-2nd-order-eq with
+ * dthb = d thetabar / d rho (thetabar a function of the cell's density). */
+static void or_collide_cell_adjoint_th(const or_model* m, const double* fc, const double* E, const double* lt,
+                                       const double* thb, double dthb, double* lam, double* gE, double* gB,
+                                       double* gtau) {
     double rho, j[3], u[3], feq[OR_MAXQ];
     double rho_bar = 0.0, u_bar[3] = {0, 0, 0};
     double D2 = m->Delta2 * m->Delta2;
     int a, d;
     or_cell_moments(m, fc, &rho, j);
     for (d = 0; d < 3; ++d) u[d] = j[d] / rho;
+    if (thb) /* the thetabar terms of f^eq through thetabar(rho) */
+        for (a = 0; a < m->Q; ++a) rho_bar += lt[a] * or_dfeq_dthetabar(m, a, rho) * dthb / m->tau;
     if (m->force_mode == 0) {
         double uxb[3], acc[3], ue[3], ue_bar[3] = {0, 0, 0}, tmp[3];
         or_cross3(u, m->B, uxb);
@@ -680,7 +695,10 @@ void or_collide_cell_adjoint(const or_model* m, const double* fc, const double* 
             acc[d] = E[d] + uxb[d];
             ue[d] = u[d] + m->tau * acc[d];
         }
-        or_equilibrium(m, rho, ue, feq);
+        if (thb)
+            or_equilibrium_thetabar(m, rho, ue, *thb, feq);
+        else
+            or_equilibrium(m, rho, ue, feq);
         for (a = 0; a < m->Q; ++a) {
             double g[3];
             /* f*_a = (1-1/tau) f_a + f^eq_a(rho, ue)/tau */
@@ -698,7 +716,10 @@ void or_collide_cell_adjoint(const or_model* m, const double* fc, const double* 
         for (d = 0; d < 3; ++d) u_bar[d] += ue_bar[d] + m->tau * tmp[d];
     } else {
         double S[OR_MAXQ];
-        or_equilibrium(m, rho, u, feq);
+        if (thb)
+            or_equilibrium_thetabar(m, rho, u, *thb, feq);
+        else
+            or_equilibrium(m, rho, u, feq);
         or_force_term(m, rho, u, E, S);
         for (a = 0; a < m->Q; ++a) {
             const double* xi = &m->xi[3 * a];
@@ -735,14 +756,40 @@ void or_collide_cell_adjoint(const or_model* m, const double* fc, const double* 
     }
 }
 
+void or_collide_cell_adjoint(const or_model* m, const double* fc, const double* E, const double* lt,
+                             double* lam, double* gE, double* gB, double* gtau) {
+    or_collide_cell_adjoint_th(m, fc, E, lt, NULL, 0.0, lam, gE, gB, gtau);
+}
+
 /* Full adjoint over a stored trajectory.
  * states: (T+1) consecutive arrays of Q*N doubles, states[t] = f_t.
  * wr[N] (may be NULL) and wj[D*N] (may be NULL): loss weights per cell.
  * Outputs: lam0[Q*N] = dL/df_0 (may be NULL), gE[D*N] per-cell dL/dE(x)
  * (may be NULL), gB[3], gtau[1]; loss[1] = L (evaluated on the trajectory). */
+static void or_adjoint_th(const or_model* m, const int64_t* n, const uint8_t* solid, const double* Efield,
+                          const double* states, const double* thb, const double* dthb, int64_t t_begin,
+                          int64_t t_end, const double* wr, const double* wj, double* lam0, double* gE, double* gB,
+                          double* gtau, double* loss);
+
 void or_adjoint(const or_model* m, const int64_t* n, const uint8_t* solid, const double* Efield,
                 const double* states, int64_t t_begin, int64_t t_end, const double* wr, const double* wj,
                 double* lam0, double* gE, double* gB, double* gtau, double* loss) {
+    or_adjoint_th(m, n, solid, Efield, states, NULL, NULL, t_begin, t_end, wr, wj, lam0, gE, gB, gtau, loss);
+}
+
+/* The same for the local-thetabar model: thb[t * N + c] and dthb[t * N + c]
+ * are thetabar and d thetabar / d rho of cell c in state t (t = 0..t_end). */
+void or_adjoint_thetabar(const or_model* m, const int64_t* n, const uint8_t* solid, const double* Efield,
+                         const double* states, const double* thb, const double* dthb, int64_t t_begin,
+                         int64_t t_end, const double* wr, const double* wj, double* lam0, double* gE, double* gB,
+                         double* gtau, double* loss) {
+    or_adjoint_th(m, n, solid, Efield, states, thb, dthb, t_begin, t_end, wr, wj, lam0, gE, gB, gtau, loss);
+}
+
+static void or_adjoint_th(const or_model* m, const int64_t* n, const uint8_t* solid, const double* Efield,
+                          const double* states, const double* thb, const double* dthb, int64_t t_begin,
+                          int64_t t_end, const double* wr, const double* wj, double* lam0, double* gE, double* gB,
+                          double* gtau, double* loss) {
     int64_t N = n[0] * n[1] * n[2], T = t_end, t, c;
     size_t QN = (size_t)m->Q * (size_t)N;
     double* lam = (double*)calloc(QN, sizeof(double));
@@ -783,7 +830,10 @@ void or_adjoint(const or_model* m, const int64_t* n, const uint8_t* solid, const
                     ltc[a] = lt[a * N + c];
                 }
                 or_cell_E(m, Efield, N, c, E);
-                or_collide_cell_adjoint(m, fc, E, ltc, lc, ge, gB, gtau);
+                if (thb)
+                    or_collide_cell_adjoint_th(m, fc, E, ltc, &thb[t * N + c], dthb[t * N + c], lc, ge, gB, gtau);
+                else
+                    or_collide_cell_adjoint_th(m, fc, E, ltc, NULL, 0.0, lc, ge, gB, gtau);
                 for (a = 0; a < m->Q; ++a) lam[a * N + c] = lc[a];
                 if (gE)
                     for (d = 0; d < m->D; ++d) gE[d * N + c] += ge[d];

@@ -63,6 +63,32 @@ __device__ __forceinline__ void block_accumulate(double* acc, double* __restrict
     }
 }
 
+// Local chemical-potential model (KParams::lmu_*): dth = thetabar - thetabar_w
+// and d dth / d rho at the unscaled density deviation drho, from the same
+// cubic Hermite table as the forward step (node and fraction taken relative
+// to the node r = 1; outside the table the end value, slope 0).
+__device__ __forceinline__ void lmu_table(const KParams& p, float drho, float& dth, float& ddth) {
+    const float a = p.lmu_a * p.scale;  // table units per unit of unscaled deviation
+    float x = drho * a;
+    const float lo = -p.lmu_b, hi = (float)(p.lmu_n - 1) - p.lmu_b;
+    const bool inside = x > lo && x < hi;
+    x = fminf(fmaxf(x, lo), hi);  // also maps NaN to node 0
+    const float fl = floorf(x);
+    int i = (int)fl + (int)p.lmu_b;
+    float t = x - fl;
+    if (i > p.lmu_n - 2) {
+        i = p.lmu_n - 2;
+        t = 1.f;
+    }
+    const float t2 = t * t, t3 = t2 * t;
+    const float2 A = __ldg(p.lmu_tab + i), B = __ldg(p.lmu_tab + i + 1);
+    dth = (2.f * t3 - 3.f * t2 + 1.f) * A.x + (t3 - 2.f * t2 + t) * A.y + (3.f * t2 - 2.f * t3) * B.x +
+          (t3 - t2) * B.y;
+    const float dx = (6.f * t2 - 6.f * t) * A.x + (3.f * t2 - 4.f * t + 1.f) * A.y + (6.f * t - 6.f * t2) * B.x +
+                     (3.f * t2 - 2.f * t) * B.y;
+    ddth = inside ? dx * a : 0.f;
+}
+
 template <class L, bool EF>
 __device__ __forceinline__ void load_E(const float* __restrict__ Ef, const KParams& p, uint32_t cell, float* E) {
     if (EF) {
@@ -112,6 +138,7 @@ __device__ __forceinline__ void adjoint_cell(const float* h, const float* lt, co
     // forward moments of f_t
     float drho = 0.f, j[3] = {0.f, 0.f, 0.f}, lth = 0.f;
     float rho, inv_rho, u[3], M0, K0, M1[3], K1[3], Mxx, Myy, Mzz, Mxy, Mxz, Myz;
+    float KM = 0.f;  // local-mu model: sum_a lt_a w_a K_a (KParams::lmu_K, K_0 for the rest)
     if constexpr (kR1 > 0 && kR2 > 0 && kR3 < 0) {
         // two moving shells (D2V9, D3V19): axis and diagonal
         constexpr int kAx = kR1, kDg = kR2;
@@ -156,6 +183,7 @@ __device__ __forceinline__ void adjoint_cell(const float* h, const float* lt, co
         const float k1 = p.k2[kAx], k2d = p.k2[kDg];
         M0 = w0 * lt[0] + w1 * L0a + w2 * L0d;
         K0 = w0 * p.k2[0] * lt[0] + w1 * k1 * L0a + w2 * k2d * L0d;
+        if (p.lmu_tab) KM = p.lmu_K[0] * w0 * lt[0] + p.lmu_K[1] * w1 * L0a + p.lmu_K[2] * w2 * L0d;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             M1[d] = w1 * L1a[d] + w2 * L1d[d];
@@ -290,6 +318,16 @@ __device__ __forceinline__ void adjoint_cell(const float* h, const float* lt, co
             u_bar[d] = dF[d] * inv_tau + rho * (2.f * p.Cp * M2E[d] + 2.f * (K0 * E[d] + K1xB[d] * p.cs_inv));
             gEc[d] = dF[d];
             gBc[d] = 2.f * rho * p.cs_inv * uxK[d];
+        }
+    }
+    if constexpr (kR1 > 0 && kR2 > 0 && kR3 < 0) {
+        // local-mu model (D2V9, D3V19): the collision adds w rho w_a K_a dth(rho),
+        // whose rho-derivative feeds rho_bar and whose w-derivative dL/dtau
+        if (p.lmu_tab) {
+            float dth, ddth;
+            lmu_table(p, drho, dth, ddth);
+            rho_bar += inv_tau * (dth + rho * ddth) * KM;
+            gtau -= inv_tau * inv_tau * rho * dth * KM;
         }
     }
     rho_bar -= (u_bar[0] * u[0] + u_bar[1] * u[1] + u_bar[2] * u[2]) * inv_rho;

@@ -217,7 +217,7 @@ lbm::KParams lbm::make_params(const lbm_ctx* c) {
         p.lmu_a = (float)(1.0 / (c->scale * c->lat.rho0 * kLmuDr));
         p.lmu_b = (float)kLmuK1;
         const double g = c->c2 + c->D * c->cbar2;
-        for (int sh = 1; sh <= 3; ++sh)
+        for (int sh = 0; sh <= 3; ++sh)  // shell 0: the rest population (the reverse step uses it)
             p.lmu_K[sh] = (float)(0.5 * g * (g * sh / (c->cs * c->cs) + c->D * c->cprime2));
     }
     return p;
@@ -902,8 +902,6 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
     if (!c->has_state) return fail(c, LBM_ERR_STATE, "lbm_adjoint before lbm_init_equilibrium");
     if (t_end < 1 || t_begin < -1 || t_begin >= t_end)
         return fail(c, LBM_ERR_INVALID_ARG, "lbm_adjoint: need -1 <= t_begin < t_end and t_end >= 1");
-    if (c->lmu_tab)
-        return fail(c, LBM_ERR_STATE, "lbm_adjoint: no reverse step for the local-mu model (lbm_set_local_mu)");
 
     if ((dL_dE && !is_device_ptr(dL_dE)) || (dL_df0 && !is_device_ptr(dL_df0)))
         return fail(c, LBM_ERR_INVALID_ARG, "lbm_adjoint: dL_dE and dL_df0 must be device pointers");

@@ -173,3 +173,77 @@ def test_local_term_has_shell_constants(vel):
         d = c["thetabar"] * (RNG.random() - 0.5)
         diff = m.equilibrium_thetabar(rho, u, c["thetabar"] + d) - m.equilibrium(rho, u)
         np.testing.assert_allclose(diff, rho * m.w * K * d, rtol=0, atol=1e-12 * rho)
+
+
+def _local_loss(m, shape, mask, f0, Efield, T, t_begin, wr, wj):
+    f = f0.copy()
+    L = 0.0
+    for t in range(1, T + 1):
+        m.step_local_mu(shape, mask, f, 1, Efield, rho_ref=1.0)
+        if t > t_begin:
+            rho, j, _ = m.moments(shape, mask, f)
+            L += np.sum(wr * rho) + np.sum(wj * j)
+    return L
+
+
+@pytest.mark.parametrize("force", ["term", "shift"])
+def test_local_mu_adjoint_vs_finite_differences(force):
+    """The reverse sweep of the local model (Model.adjoint_local_mu) against
+    central differences of its forward run (Model.step_local_mu): per-cell
+    dL/dE, dL/dB_z, dL/dtau and dL/df_0 along a random direction (D2V9, FD
+    theta = 0.5, mu = 0, 2% density noise, an obstacle)."""
+    from paper_1710_09472_gb300 import workloads as wl
+
+    shape = (10, 12)
+    mask, _ = wl.boolean_obstacles(shape, 2.0, 0.8, seed=21)
+    N = mask.size
+    B = (0.0, 0.0, 2e-2)
+    Efield = np.zeros((2,) + shape)
+    Efield[0] = 1e-3 + 2e-4 * wl.normal(31, N).reshape(shape)
+    Efield[1] = 3e-4 * wl.normal(32, N).reshape(shape)
+    rho0 = 1.0 + 0.02 * wl.uniform01(33, N).reshape(shape)
+    u0 = 0.01 * wl.normal(34, 2 * N).reshape((2,) + shape)
+    wr = wl.normal(35, N).reshape(shape)
+    wj = wl.normal(36, 2 * N).reshape((2,) + shape)
+    tau, T, t_begin = 0.75, 10, 5
+
+    def model(tau_=tau, B_=B):
+        return oracle.Model("D2V9", "fd", 0.5, 0.0, tau=tau_, B=B_, force=force)
+
+    m = model()
+    f0 = m.init_equilibrium(shape, mask, rho0, u0)
+    states = np.empty((T + 1, f0.size))
+    states[0] = f0
+    f = f0.copy()
+    for t in range(T):
+        m.step_local_mu(shape, mask, f, 1, Efield, rho_ref=1.0)
+        states[t + 1] = f
+    res = m.adjoint_local_mu(shape, mask, states, t_begin, T, wr, wj, Efield, rho_ref=1.0)
+    L0 = _local_loss(m, shape, mask, f0, Efield, T, t_begin, wr, wj)
+    assert abs(res["loss"] - L0) < 1e-12 * max(1, abs(L0))
+    base = m.adjoint(shape, mask, states, t_begin, T, wr, wj, Efield)
+    assert abs(base["gtau"] - res["gtau"]) > 1e-3 * abs(res["gtau"])  # the local terms matter
+
+    fluid = np.argwhere(mask == 0)
+    rng = np.random.default_rng(0)
+    h = 1e-6
+    for k in rng.choice(len(fluid), 3, replace=False):
+        cell = tuple(fluid[k])
+        for d in range(2):
+            Ep, Em = Efield.copy(), Efield.copy()
+            Ep[(d,) + cell] += h
+            Em[(d,) + cell] -= h
+            fd = (_local_loss(m, shape, mask, f0, Ep, T, t_begin, wr, wj)
+                  - _local_loss(m, shape, mask, f0, Em, T, t_begin, wr, wj)) / (2 * h)
+            assert abs(res["gE"][(d,) + cell] - fd) < 1e-6 * max(abs(fd), 1e-3), (cell, d)
+    fd = (_local_loss(model(B_=(0.0, 0.0, B[2] + h)), shape, mask, f0, Efield, T, t_begin, wr, wj)
+          - _local_loss(model(B_=(0.0, 0.0, B[2] - h)), shape, mask, f0, Efield, T, t_begin, wr, wj)) / (2 * h)
+    assert abs(res["gB"][2] - fd) < 1e-6 * max(abs(fd), 1e-3), (res["gB"][2], fd)
+    fd = (_local_loss(model(tau_=tau + h), shape, mask, f0, Efield, T, t_begin, wr, wj)
+          - _local_loss(model(tau_=tau - h), shape, mask, f0, Efield, T, t_begin, wr, wj)) / (2 * h)
+    assert abs(res["gtau"] - fd) < 1e-6 * max(abs(fd), 1e-3), (res["gtau"], fd)
+    v = rng.normal(size=f0.size)
+    v.reshape(m.Q, -1)[:, mask.reshape(-1) == 1] = 0.0
+    fd = (_local_loss(m, shape, mask, f0 + h * v, Efield, T, t_begin, wr, wj)
+          - _local_loss(m, shape, mask, f0 - h * v, Efield, T, t_begin, wr, wj)) / (2 * h)
+    assert abs(float(res["lam0"] @ v) - fd) < 1e-7 * max(abs(fd), 1.0), (float(res["lam0"] @ v), fd)
