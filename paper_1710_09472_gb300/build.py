@@ -19,7 +19,8 @@ LIB = os.path.join(BUILD, "liblbm.so")
 SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_adjoint.cu", "lbm_static.cu", "lbm_step_f32.cu", "lbm_step_f16.cu",
            "lbm_step_bf16.cu", "lbm_adjoint_f32.cu", "lbm_adjoint_f16.cu", "lbm_adjoint_bf16.cu",
            "lbm_step_f32_x.cu", "lbm_step_f16_x.cu", "lbm_step_bf16_x.cu", "lbm_adjoint_f32_x.cu",
-           "lbm_adjoint_f16_x.cu", "lbm_adjoint_bf16_x.cu", "lbm_thermal.cu", "lbm_fd.cu"]
+           "lbm_adjoint_f16_x.cu", "lbm_adjoint_bf16_x.cu", "lbm_adjoint_f32_lmu.cu", "lbm_adjoint_f16_lmu.cu",
+           "lbm_adjoint_bf16_lmu.cu", "lbm_thermal.cu", "lbm_fd.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

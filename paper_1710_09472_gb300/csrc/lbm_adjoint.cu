@@ -31,6 +31,17 @@ int launch_adjoint_seed_bf16_x(int, const void*, const uint32_t*, const float*, 
 int launch_adjoint_step_bf16_x(int, int, bool, bool, const void*, const float*, float*, const uint32_t*, const float*,
                                const float*, const float*, double*, double*, const KParams&, cudaStream_t);
 
+// the local chemical-potential model, D2V9 and D3V19 (lbm_adjoint_*_lmu.cu)
+int launch_adjoint_step_f32_lmu(int, int, bool, bool, const void*, const float*, float*, const uint32_t*,
+                                const float*, const float*, const float*, double*, double*, const KParams&,
+                                cudaStream_t);
+int launch_adjoint_step_f16_lmu(int, int, bool, bool, const void*, const float*, float*, const uint32_t*,
+                                const float*, const float*, const float*, double*, double*, const KParams&,
+                                cudaStream_t);
+int launch_adjoint_step_bf16_lmu(int, int, bool, bool, const void*, const float*, float*, const uint32_t*,
+                                 const float*, const float*, const float*, double*, double*, const KParams&,
+                                 cudaStream_t);
+
 int64_t adjoint_slot_count(const KParams& p) {
     Launch l = adjk::grid_of(p);
     return (int64_t)l.grid.x * l.grid.y * adjk::kSlots;
@@ -56,6 +67,16 @@ int launch_adjoint_step(int vel, int storage, int force, bool efield, bool in_wi
                         const float* lam_in, float* lam_out, const uint32_t* nbr, const float* Ef,
                         const float* w_rho, const float* w_j, double* gE, double* slots, const KParams& p,
                         cudaStream_t s) {
+    if (p.lmu_tab && (vel == LBM_D2V9 || vel == LBM_D3V19)) {
+        if (storage == LBM_F16_DEV)
+            return launch_adjoint_step_f16_lmu(vel, force, efield, in_window, P, lam_in, lam_out, nbr, Ef, w_rho,
+                                               w_j, gE, slots, p, s);
+        if (storage == LBM_BF16_DEV)
+            return launch_adjoint_step_bf16_lmu(vel, force, efield, in_window, P, lam_in, lam_out, nbr, Ef, w_rho,
+                                                w_j, gE, slots, p, s);
+        return launch_adjoint_step_f32_lmu(vel, force, efield, in_window, P, lam_in, lam_out, nbr, Ef, w_rho, w_j,
+                                           gE, slots, p, s);
+    }
     if (vel == LBM_D3V27 || vel == LBM_D1V3) {
         if (storage == LBM_F16_DEV)
             return launch_adjoint_step_f16_x(vel, force, efield, in_window, P, lam_in, lam_out, nbr, Ef, w_rho, w_j,

@@ -131,14 +131,13 @@ __device__ __forceinline__ void load_weights(const float* __restrict__ w_rho, co
 // K1 = sum mu k2 e.  Since w_a and k2_a are constant on each shell (|e|^2 =
 // 1, 2, 3: axes, face diagonals, corners), the per-direction work is only
 // the unweighted shell moments of lt.
-template <class L, int FORCE, bool WIN>
+template <class L, int FORCE, bool WIN, bool LMU = false>
 __device__ __forceinline__ void adjoint_cell(const float* h, const float* lt, const float* E, const KParams& p,
                                              float wr, const float* wj, float* lam, float* gEc, double* acc) {
     constexpr int kR1 = shell_first<L>(1), kR2 = shell_first<L>(2), kR3 = shell_first<L>(3);
     // forward moments of f_t
     float drho = 0.f, j[3] = {0.f, 0.f, 0.f}, lth = 0.f;
     float rho, inv_rho, u[3], M0, K0, M1[3], K1[3], Mxx, Myy, Mzz, Mxy, Mxz, Myz;
-    float KM = 0.f;  // local-mu model: sum_a lt_a w_a K_a (KParams::lmu_K, K_0 for the rest)
     if constexpr (kR1 > 0 && kR2 > 0 && kR3 < 0) {
         // two moving shells (D2V9, D3V19): axis and diagonal
         constexpr int kAx = kR1, kDg = kR2;
@@ -183,7 +182,6 @@ __device__ __forceinline__ void adjoint_cell(const float* h, const float* lt, co
         const float k1 = p.k2[kAx], k2d = p.k2[kDg];
         M0 = w0 * lt[0] + w1 * L0a + w2 * L0d;
         K0 = w0 * p.k2[0] * lt[0] + w1 * k1 * L0a + w2 * k2d * L0d;
-        if (p.lmu_tab) KM = p.lmu_K[0] * w0 * lt[0] + p.lmu_K[1] * w1 * L0a + p.lmu_K[2] * w2 * L0d;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             M1[d] = w1 * L1a[d] + w2 * L1d[d];
@@ -320,10 +318,13 @@ __device__ __forceinline__ void adjoint_cell(const float* h, const float* lt, co
             gBc[d] = 2.f * rho * p.cs_inv * uxK[d];
         }
     }
-    if constexpr (kR1 > 0 && kR2 > 0 && kR3 < 0) {
+    if constexpr (LMU && kR1 > 0 && kR2 > 0 && kR3 < 0) {
         // local-mu model (D2V9, D3V19): the collision adds w rho w_a K_a dth(rho),
-        // whose rho-derivative feeds rho_bar and whose w-derivative dL/dtau
-        if (p.lmu_tab) {
+        // whose rho-derivative feeds rho_bar and whose w-derivative dL/dtau.
+        // K_a = K_0 + (K_1 - K_0) |e_a|^2 is affine in |e_a|^2, so
+        // sum_a lt_a w_a K_a = K_0 M0 + (K_1 - K_0) trace(M2).
+        {
+            const float KM = p.lmu_K[0] * M0 + (p.lmu_K[1] - p.lmu_K[0]) * (Mxx + Myy + Mzz);
             float dth, ddth;
             lmu_table(p, drho, dth, ddth);
             rho_bar += inv_tau * (dth + rho * ddth) * KM;
@@ -454,7 +455,12 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(
             float E[3], wr, wj[3], lam[L::Q], gEc[3];
             load_E<L, EF>(Ef, p, c.cell, E);
             load_weights<L, WIN>(w_rho, w_j, p, c.cell, wr, wj);
-            adjoint_cell<L, FORCE, WIN>(h, lt, E, p, wr, wj, lam, gEc, acc);
+            // the local-mu model is built for D2V9 and D3V19 (the host refuses others)
+            constexpr bool kLmu = L::Q == 9 || L::Q == 19;
+            if (kLmu && p.lmu_tab)
+                adjoint_cell<L, FORCE, WIN, kLmu>(h, lt, E, p, wr, wj, lam, gEc, acc);
+            else
+                adjoint_cell<L, FORCE, WIN>(h, lt, E, p, wr, wj, lam, gEc, acc);
 #pragma unroll
             for (int b = 0; b < L::Q; ++b) lam_out[dev::pop_at<L>(p, c, b, 0)] = lam[b];
             if (o) store_lam_links<L>(link_part(lam_out, p), o, lb, lam);
@@ -576,7 +582,7 @@ __device__ __forceinline__ void adj_stage(unsigned char* st, const AdjLayout<L, 
     }
 }
 
-template <class L, class S, int FORCE, bool EF, bool WIN, int STAGES, int RS>
+template <class L, class S, int FORCE, bool EF, bool WIN, int STAGES, int RS, bool LMU = false>
 __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __restrict__ P,
                                                          const float* __restrict__ lam_in,
                                                          float* __restrict__ lam_out,
@@ -684,7 +690,7 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
                     load_E<L, false>(Ef, p, cell, E);
                 }
                 load_weights<L, WIN>(w_rho, w_j, p, cell, wr, wj);
-                adjoint_cell<L, FORCE, WIN>(h, lt, E, p, wr, wj, lam, gEc, acc);
+                adjoint_cell<L, FORCE, WIN, LMU>(h, lt, E, p, wr, wj, lam, gEc, acc);
 #pragma unroll
                 for (int b = 0; b < L::Q; ++b) outrow[pop_slot<L>(b) * rs + x] = lam[b];
                 if (gE) {
@@ -733,7 +739,7 @@ inline Launch grid_of(const KParams& p) {
 // GROUP 0: D2V9 and D3V19; GROUP 1: D3V27 and D1V3 (separate translation units)
 template <int GROUP, class F>
 int dispatch_lattice(int vel, F&& f) {
-    if constexpr (GROUP == 0) {
+    if constexpr (GROUP == 0 || GROUP == 2) {
         if (vel == LBM_D2V9) return f(LatD2V9{});
         return f(LatD3V19{});
     } else {
@@ -752,7 +758,7 @@ constexpr int kAdjStages = 2;
 constexpr int kAdjThreads = 256;
 constexpr size_t kAdjSmemBudget = 200 * 1024;
 
-template <class L, class S, int FORCE, bool EF, bool WIN, int RS>
+template <class L, class S, int FORCE, bool EF, bool WIN, int RS, bool LMU = false>
 bool launch_rows_rs(const void* P, const float* lam_in, float* lam_out, const uint32_t* nbr, const float* Ef,
                  const float* w_rho, const float* w_j, double* gE, double* slots, int64_t slot_blocks,
                  const KParams& p, cudaStream_t s) {
@@ -775,7 +781,7 @@ bool launch_rows_rs(const void* P, const float* lam_in, float* lam_out, const ui
         (size_t)L::Q * rs * 4;
     if (smem_ref > kAdjSmemBudget) return false;
     const int threads = p.nx >= kAdjThreads ? kAdjThreads : ((p.nx + 31) / 32) * 32;
-    auto kern = k_adjoint_rows<L, S, FORCE, EF, WIN, kAdjStages, RS>;
+    auto kern = k_adjoint_rows<L, S, FORCE, EF, WIN, kAdjStages, RS, LMU>;
     // persistent grid: co-resident blocks per SM (occupancy API) x SMs,
     // cached per instantiation and shared-memory size
     static std::mutex mu;
@@ -846,10 +852,18 @@ int step_storage(int vel, int force, bool efield, bool in_window, const void* P,
     return dispatch_lattice<GROUP>(vel, [&](auto lat) {
         using L = decltype(lat);
         const auto* Pt = (const typename S::T*)P;
+// GROUP 2: the local-mu model (D2V9, D3V19), whose staged reverse kernel is
+// an instantiation of its own with the run-time row stride
 #define LBM_ADJ(F, EFV, W)                                                                                    \
     do {                                                                                                      \
-        if (!launch_rows<L, S, F, EFV, W>(P, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE, slots, slot_blocks, p, \
-                                          s))                                                                 \
+        bool staged;                                                                                          \
+        if constexpr (GROUP == 2)                                                                             \
+            staged = launch_rows_rs<L, S, F, EFV, W, 0, true>(P, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE,    \
+                                                              slots, slot_blocks, p, s);                      \
+        else                                                                                                  \
+            staged = launch_rows<L, S, F, EFV, W>(P, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE, slots,         \
+                                                  slot_blocks, p, s);                                         \
+        if (!staged)                                                                                          \
             k_adjoint_step<L, S, F, EFV, W>                                                                   \
                 <<<l.grid, l.block, 0, s>>>(Pt, lam_in, lam_out, nbr, Ef, w_rho, w_j, gE, slots, p);          \
     } while (0)
