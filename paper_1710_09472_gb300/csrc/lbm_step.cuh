@@ -552,6 +552,17 @@ __device__ __forceinline__ void stage_row(unsigned char* st, const StageLayout<L
                        bar);
 }
 
+// FP32 storage with 256-cell rows writes each row's outputs over its own
+// stage after a block barrier (one cell per thread, 256 threads) instead of
+// into separate output rows: 46 instead of 66 KB of shared memory, four
+// blocks per SM instead of three, 0.458 against 0.468 ms per 256^3 step.  The
+// stage is refilled only after the row's bulk store has read it and every
+// thread has passed its link copies (the first barrier of the next row).  For
+// FP16 the extra barrier and the 256-thread blocks cost more than the freed
+// memory gains (0.321 against 0.258 ms), so 16-bit storage keeps output rows.
+template <class S, int RS, bool LMU>
+constexpr bool kInPlaceOut = S::kBytes == 4 && RS == 256 && !LMU;
+
 template <class L, class S, int FORCE, bool EF, bool SR, int STAGES, int RS, bool LMU = false>
 __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restrict__ Pin,
                                                    typename S::T* __restrict__ Pout, const float* __restrict__ Ef,
@@ -560,6 +571,9 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int nx = p.nx;
     const int rs = RS ? RS : nx;  // shared-memory row stride (= nx): a constant for the common row lengths
+    // FP32 rows of 256 cells write their outputs over the row's own stage
+    // (no output rows: four blocks per SM instead of three); see kInPlaceOut
+    constexpr bool kInPlace = kInPlaceOut<S, RS, LMU>;
     const StageLayout<L, S> lay{nx, rs, p.lorder, gcap, dcap};
     const int sbytes = lay.bytes();
     T* outrow = reinterpret_cast<T*>(smem_raw + STAGES * sbytes);
@@ -610,6 +624,7 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
         }
         unsigned char* st = smem_raw + cs * sbytes;
         T* buf = lay.rows(st);
+        T* orow = kInPlace ? buf : outrow;  // where this row's outputs go
         const uint16_t* ord = lay.order(st);
         const uint32_t* desc = lay.descs(st);
         const uint32_t d0 = dstart[cs];
@@ -628,6 +643,38 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
         }
         const int nf = ord[0];
         const uint32_t rowbase = (uint32_t)r * (uint32_t)nx;
+        if constexpr (kInPlace) {
+            // one cell per thread (the launcher sets blockDim.x = nx): every
+            // pull first, then a barrier, then the outputs over the stage
+            const int i = threadIdx.x;
+            const int x = (int)ord[8 + i];
+            const bool fluid = i < nf;
+            const uint32_t cell = rowbase + (uint32_t)x;
+            float h[L::Q];
+            if (fluid) {
+                const int xm = x == 0 ? nx - 1 : x - 1;
+                const int xp = x == nx - 1 ? 0 : x + 1;
+#pragma unroll
+                for (int a = 0; a < L::Q; ++a) {
+                    const int ex = L::c(a, 0);
+                    h[a] = S::cvt(buf[pop_slot<L>(a) * rs + (ex > 0 ? xm : (ex < 0 ? xp : x))]);
+                }
+            }
+            __syncthreads();  // no thread overwrites a slot another has still to pull
+            if (fluid) {
+                float E[3];
+                load_E<L>(Ef, EF, p, cell, E);
+                float out[L::Q];
+                collide_any<L, S, FORCE, LMU>(h, E, p, out);
+                typename S::T t[L::Q];
+                round_all<L, S, SR>(out, cell, p, t);
+#pragma unroll
+                for (int a = 0; a < L::Q; ++a) orow[pop_slot<L>(a) * rs + x] = t[a];
+            } else {
+#pragma unroll
+                for (int a = 0; a < L::Q; ++a) S::put(orow + a * rs + x, 0.f);
+            }
+        } else
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
             const int x = (int)ord[8 + i];
             if (i < nf) {
@@ -684,13 +731,13 @@ __global__ void __launch_bounds__(256) k_step_rows(const typename S::T* __restri
         __syncthreads();           // output rows complete; the stage is free for its refill
         if (threadIdx.x == 0) {
             // the row's Q slots, one contiguous block
-            dev::bulk_store(Pout + (int64_t)rowbase * L::Q, outrow, L::Q * row_bytes);
+            dev::bulk_store(Pout + (int64_t)rowbase * L::Q, orow, L::Q * row_bytes);
             dev::bulk_commit();
         }
         // outgoing links: slot k of (x, b) takes f*_b(x)
         for (uint32_t k = g0 + threadIdx.x; k < g1; k += blockDim.x) {
             const uint32_t d = desc[k - d0];
-            Gout[k] = outrow[slot_of<L>((int)(d >> 24)) * rs + (int)(d & 0xFFFFFFu)];
+            Gout[k] = orow[slot_of<L>((int)(d >> 24)) * rs + (int)(d & 0xFFFFFFu)];
         }
     }
     dev::bulk_wait_all();
@@ -713,12 +760,13 @@ constexpr size_t kSmemBudget = 160 * 1024;
 // the larger block on a tie: more rows in flight per SM hide the per-row
 // copy latency.  256-cell FP16 rows: 192 threads (six blocks per SM) take
 // 0.258 ms per 256^3 step, against 0.268 at 160, 0.277 at 224 and 0.278 at
-// 256 threads.
+// 256 threads.  fixed_threads != 0 takes that block size (the in-place FP32
+// rows need one thread per cell).
 struct Shape {
     int threads, blocks;
 };
 template <class K>
-Shape launch_shape(K kernel, int nx, size_t smem) {
+Shape launch_shape(K kernel, int nx, size_t smem, int fixed_threads = 0) {
     static std::mutex mu;
     static const void* last_k = nullptr;
     static size_t last_smem = 0;
@@ -730,10 +778,11 @@ Shape launch_shape(K kernel, int nx, size_t smem) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const int tmax = nx >= kRowThreads ? kRowThreads : ((nx + 31) / 32) * 32;
+        const int tmax = fixed_threads ? fixed_threads : (nx >= kRowThreads ? kRowThreads : ((nx + 31) / 32) * 32);
+        const int tmin = fixed_threads ? fixed_threads : tmax / 2;
         Shape best{tmax, 0};
         int best_per_sm = -1;
-        for (int t = tmax; t >= 32 && t >= tmax / 2; t -= 32) {
+        for (int t = tmax; t >= 32 && t >= tmin; t -= 32) {
             int per_sm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, t, smem);
             if (per_sm > best_per_sm) {
@@ -760,10 +809,12 @@ bool launch_rows(const S*, const void* fin, void* fout, const uint32_t* nbr, con
     const int gcap = dev::window_cap(p.max_row_links, S::kBytes);
     const int dcap = dev::window_cap(p.max_row_links, 4);
     const size_t stage_bytes = (size_t)L::Q * srow + 2 * (size_t)p.lorder + gcap + dcap;
-    const size_t smem = (size_t)kStages * stage_bytes + (size_t)L::Q * srow;
+    constexpr bool kInPlace = kInPlaceOut<S, RS, LMU>;
+    const size_t smem = (size_t)kStages * stage_bytes + (kInPlace ? 0 : (size_t)L::Q * srow);
     if (!p.rorder || row_bytes % 16 != 0 || smem > kSmemBudget || p.nx < 32 || p.nx % 4 != 0) return false;
     auto kern = k_step_rows<L, S, FORCE, EF, SR, kStages, RS, LMU>;
-    const Shape sh = launch_shape(kern, p.nx, smem);
+    // one cell per thread in place: exactly nx (= 256) threads
+    const Shape sh = launch_shape(kern, p.nx, smem, kInPlace ? p.nx : 0);
     const int threads = sh.threads, blocks = sh.blocks;
     if (blocks <= 0) return false;
     const int rows = p.ny * p.nz;

@@ -109,13 +109,15 @@ def test_parity_row_strides(storage, shape):
 
 
 CASES_3D = [(s, f, e, shp) for s in ("f32", "f16", "bf16") for f in ("term", "shift") for e in (False, True)
-            for shp in ((9, 10, 133), (8, 12, 64))]
+            for shp in ((9, 10, 133), (8, 12, 64), (5, 6, 256))]
 
 
 @pytest.mark.parametrize("storage,force,efield,shape", CASES_3D)
 def test_parity_3d(storage, force, efield, shape):
-    """D3V19, spheres, B oblique, 40 steps; 9 x 10 x 133 (general kernel) and
-    8 x 12 x 64 (row-staged kernel)."""
+    """D3V19, spheres, B oblique, 40 steps; 9 x 10 x 133 (general kernel),
+    8 x 12 x 64 (row-staged kernel) and 5 x 6 x 256 (the row-staged kernel at
+    the compile-time 256 stride; with FP32 storage its outputs overwrite the
+    row's own stage)."""
     solid, _ = wl.boolean_obstacles(shape, 2.5, 0.75, seed=51)
     rho, u = _fields(shape, 3, 52)
     E = (1e-4, 3e-5, -2e-5)
