@@ -396,8 +396,8 @@ def other_lattices(mask, dev, stream, peak, warmup):
     box = box_dims()
     # (D1V3 boxes are at most 2^20 cells, whose state fits the 129 MB L2, so
     # they have no HBM figure)
-    # the local chemical-potential model (per-cell thetabar) runs on the
-    # general step kernel
+    # the local chemical-potential model (per-cell thetabar) runs on its own
+    # row-staged instantiation (run-time row stride)
     for vel, dims, storage, local in (("D3V27", box, "f16", False), ("D3V27", box, "f32", False),
                                       ("D3V19", box, "f16", True)):
         sim = LBM(vel, dims, WORKLOAD["tau"], E=(WORKLOAD["Ex"], 0.0, 0.0), B=(0.0, 0.0, WORKLOAD["Bz"]),

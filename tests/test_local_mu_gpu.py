@@ -104,9 +104,9 @@ def test_local_mu_parity_2d_f16():
 
 
 def test_local_mu_mb_equals_default_model():
-    """With the MB weight thetabar does not depend on mu: the local model on
-    the general kernel equals the default model (rows kernel) to FP32
-    rounding."""
+    """With the MB weight thetabar does not depend on mu: the local model (its
+    own row-staged instantiation, a zero table) equals the default model to
+    FP32 rounding."""
     solid, rho = _case(3)
     args = dict(stat="mb", theta=1.0, mu=0.0)
     r1, j1, _, s1 = _gpu("D2V9", SHAPE, solid, rho, 100, **args)
