@@ -456,7 +456,7 @@ def adjoint_512(T: int, dev, stream):
     state = sim.adjoint_stats()["state_bytes"]
     # an adjoint field: FP32 lambda plus one FP32 per link (the state holds one FP16 per link)
     lam_field = 4 * 19 * N + 2 * max(0, state - 2 * 19 * N) + 1024
-    fixed = 2 * lam_field + 2 * state + dE.numel() * 8 + wj.numel() * 4
+    fixed = 2 * lam_field + 2 * state + dE.numel() * (8 + 4) + wj.numel() * 4  # dL/dE: FP64 + FP32 partials
     budget = 180 * 10**9 - fixed - 4 * 10**9  # margin: CUDA context, library scratch, torch buffers
     sim.set_memory_budget(budget)
     torch.cuda.synchronize()

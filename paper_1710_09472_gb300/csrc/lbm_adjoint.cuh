@@ -22,7 +22,8 @@
 // pull.
 //
 // f_t is rebuilt by pulling the stored state of the forward replay.
-// Parameter gradients: dL/dE(x) is accumulated per cell in FP64; dL/dB,
+// Parameter gradients: dL/dE(x) is accumulated per cell in FP32 partials
+// that the driver folds into FP64 every few reverse steps; dL/dB,
 // dL/dtau and the loss are block-reduced into per-block FP64 slots that each
 // block owns (deterministic for a fixed launch shape).
 #pragma once
@@ -429,7 +430,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(
     const float* __restrict__ lam_in,     // lam_{t+1}
     float* __restrict__ lam_out,          // lam_t
     const uint32_t* __restrict__ nbr, const float* __restrict__ Ef, const float* __restrict__ w_rho,
-    const float* __restrict__ w_j, double* __restrict__ gE, double* __restrict__ slots, KParams p) {
+    const float* __restrict__ w_j, float* __restrict__ gE, double* __restrict__ slots, KParams p) {
     Cell c;
     double acc[kSlots] = {0.0, 0.0, 0.0, 0.0, 0.0};
     if (dev::cell_of_thread(p, c)) {
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(
             if (o) store_lam_links<L>(link_part(lam_out, p), o, lb, lam);
             if (gE) {
 #pragma unroll
-                for (int d = 0; d < L::D; ++d) gE[(int64_t)d * p.N + c.cell] += (double)gEc[d];
+                for (int d = 0; d < L::D; ++d) gE[(int64_t)d * p.N + c.cell] += gEc[d];
             }
         }
     }
@@ -476,8 +477,8 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(
 // ---------------------------------------------------------------------------
 // Row-staged reverse step (persistent; block b takes rows b, b + G, ...).
 // One stage holds, for the row (y, z):
-//   - with dL/dE, the row's D rows of it (FP64, accumulated in place and
-//     stored back after the row); with a per-cell field, its D rows of E;
+//   - with dL/dE, the row's D rows of its FP32 partials (accumulated in place
+//     and stored back after the row); with a per-cell field, its D rows of E;
 //   - the Q pull rows of the forward state P_t in slot order: direction a
 //     from row (y - e_ay, z - e_az), read at x - e_ax (one copy per
 //     neighbouring row: its block of consecutive slots);
@@ -504,7 +505,7 @@ template <class L, class S>
 struct AdjLayout {
     int nx, rs, lorder, gcapP, gcapL;  // row length, shared-memory row stride (elements), order entries;
                                        // gcapL also bounds the descriptor window (4-byte elements)
-    int gerow, efrow;                  // bytes of the staged dL/dE rows (FP64) and E rows (FP32), 0 when absent
+    int gerow, efrow;                  // bytes of the staged dL/dE rows and E rows (FP32), 0 when absent
     __device__ __host__ int prow() const { return L::Q * rs * S::kBytes; }
     __device__ __host__ int lrow() const { return L::Q * rs * 4; }
     __device__ __host__ int bytes() const {
@@ -528,7 +529,7 @@ struct AdjLayout {
 // back after the row); with Ef, its E.
 template <class L, class S>
 __device__ __forceinline__ void adj_stage(unsigned char* st, const AdjLayout<L, S>& lay, uint64_t* bar,
-                                          const typename S::T* P, const float* lam, const double* gE, const float* Ef,
+                                          const typename S::T* P, const float* lam, const float* gE, const float* Ef,
                                           int row, uint32_t g0, uint32_t g1, uint32_t* ws, const KParams& p) {
     const uint32_t prb = (uint32_t)p.nx * S::kBytes, lrb = (uint32_t)p.nx * 4u;
     const int rs = lay.rs;
@@ -538,7 +539,7 @@ __device__ __forceinline__ void adj_stage(unsigned char* st, const AdjLayout<L, 
     ws[0] = (uint32_t)(pb0 / S::kBytes);
     ws[1] = (uint32_t)(lb0 / 4);
     dev::mbar_expect_tx(bar, L::Q * (prb + lrb) + 2u * (uint32_t)lay.lorder + (uint32_t)(pb1 - pb0) +
-                                 2u * (uint32_t)(lb1 - lb0) + (lay.gerow ? L::D * (uint32_t)p.nx * 8u : 0u) +
+                                 2u * (uint32_t)(lb1 - lb0) + (lay.gerow ? L::D * (uint32_t)p.nx * 4u : 0u) +
                                  (lay.efrow ? L::D * (uint32_t)p.nx * 4u : 0u));
     const int y = row % p.ny, z = row / p.ny;
     const int yp = y == p.ny - 1 ? 0 : y + 1, ym = y == 0 ? p.ny - 1 : y - 1;
@@ -571,8 +572,8 @@ __device__ __forceinline__ void adj_stage(unsigned char* st, const AdjLayout<L, 
     if (lay.gerow) {
 #pragma unroll
         for (int d = 0; d < L::D; ++d)
-            dev::bulk_load(lay.gerows(st) + d * rs * 8, gE + (int64_t)d * p.N + (int64_t)row * p.nx,
-                           (uint32_t)p.nx * 8u, bar);
+            dev::bulk_load(lay.gerows(st) + d * rs * 4, gE + (int64_t)d * p.N + (int64_t)row * p.nx,
+                           (uint32_t)p.nx * 4u, bar);
     }
     if (lay.efrow) {
 #pragma unroll
@@ -588,13 +589,13 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
                                                          float* __restrict__ lam_out,
                                                          const float* __restrict__ Ef,
                                                          const float* __restrict__ w_rho,
-                                                         const float* __restrict__ w_j, double* __restrict__ gE,
+                                                         const float* __restrict__ w_j, float* __restrict__ gE,
                                                          double* __restrict__ slots, int gcapP, int gcapL, KParams p) {
     using T = typename S::T;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int nx = p.nx;
     const int rs = RS ? RS : nx;  // shared-memory row stride (= nx): a constant for the common row lengths
-    const AdjLayout<L, S> lay{nx, rs, p.lorder, gcapP, gcapL, gE ? L::D * rs * 8 : 0, EF ? L::D * rs * 4 : 0};
+    const AdjLayout<L, S> lay{nx, rs, p.lorder, gcapP, gcapL, gE ? L::D * rs * 4 : 0, EF ? L::D * rs * 4 : 0};
     const int sbytes = lay.bytes();
     float* outrow = reinterpret_cast<float*>(smem_raw + STAGES * sbytes);
     __shared__ __align__(8) uint64_t bar[STAGES];
@@ -645,7 +646,7 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
         }
         unsigned char* st = smem_raw + cs * sbytes;
         T* prow = reinterpret_cast<T*>(lay.prows(st));
-        double* ge_s = reinterpret_cast<double*>(lay.gerows(st));
+        float* ge_s = reinterpret_cast<float*>(lay.gerows(st));
         const float* ef_s = reinterpret_cast<const float*>(lay.efrows(st));
         float* lrow = reinterpret_cast<float*>(lay.lrows(st));
         const uint16_t* ord = reinterpret_cast<const uint16_t*>(lay.order(st));
@@ -695,7 +696,7 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
                 for (int b = 0; b < L::Q; ++b) outrow[pop_slot<L>(b) * rs + x] = lam[b];
                 if (gE) {
 #pragma unroll
-                    for (int d = 0; d < L::D; ++d) ge_s[d * rs + x] += (double)gEc[d];
+                    for (int d = 0; d < L::D; ++d) ge_s[d * rs + x] += gEc[d];
                 }
             } else {
 #pragma unroll
@@ -714,7 +715,7 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_rows(const typename S::T* __
                 dev::bulk_commit();
             } else if (gE && k <= L::D) {
                 const int d = k - 1;
-                dev::bulk_store(gE + (int64_t)d * p.N + rowbase, ge_s + d * rs, (uint32_t)nx * 8u);
+                dev::bulk_store(gE + (int64_t)d * p.N + rowbase, ge_s + d * rs, (uint32_t)nx * 4u);
                 dev::bulk_commit();
             }
         }
@@ -760,7 +761,7 @@ constexpr size_t kAdjSmemBudget = 200 * 1024;
 
 template <class L, class S, int FORCE, bool EF, bool WIN, int RS, bool LMU = false>
 bool launch_rows_rs(const void* P, const float* lam_in, float* lam_out, const uint32_t* nbr, const float* Ef,
-                 const float* w_rho, const float* w_j, double* gE, double* slots, int64_t slot_blocks,
+                 const float* w_rho, const float* w_j, float* gE, double* slots, int64_t slot_blocks,
                  const KParams& p, cudaStream_t s) {
     if (!p.rorder || (p.nx * S::kBytes) % 16 != 0 || p.nx % 4 != 0 || p.nx < 32) return false;
     if (reinterpret_cast<uintptr_t>(gE) % 16 != 0) return false;  // dL/dE rows move by bulk copies
@@ -769,7 +770,7 @@ bool launch_rows_rs(const void* P, const float* lam_in, float* lam_out, const ui
     if (RS && RS != p.nx) return false;  // the stage rows are exactly nx long
     const int rs = p.nx;
     const size_t stage =
-        (size_t)AdjLayout<L, S>{p.nx, rs, p.lorder, gcapP, gcapL, gE ? L::D * rs * 8 : 0, EF ? L::D * rs * 4 : 0}
+        (size_t)AdjLayout<L, S>{p.nx, rs, p.lorder, gcapP, gcapL, gE ? L::D * rs * 4 : 0, EF ? L::D * rs * 4 : 0}
             .bytes();
     const size_t smem = kAdjStages * stage + (size_t)L::Q * rs * 4;
     // the kernel choice and the persistent grid are taken for the layout with
@@ -777,7 +778,7 @@ bool launch_rows_rs(const void* P, const float* lam_in, float* lam_out, const ui
     // with them the order of the FP64 gradient sums) are the same either way
     const size_t smem_ref =
         kAdjStages *
-            (size_t)AdjLayout<L, S>{p.nx, rs, p.lorder, gcapP, gcapL, L::D * rs * 8, EF ? L::D * rs * 4 : 0}.bytes() +
+            (size_t)AdjLayout<L, S>{p.nx, rs, p.lorder, gcapP, gcapL, L::D * rs * 4, EF ? L::D * rs * 4 : 0}.bytes() +
         (size_t)L::Q * rs * 4;
     if (smem_ref > kAdjSmemBudget) return false;
     const int threads = p.nx >= kAdjThreads ? kAdjThreads : ((p.nx + 31) / 32) * 32;
@@ -815,7 +816,7 @@ bool launch_rows_rs(const void* P, const float* lam_in, float* lam_out, const ui
 // for rows of 256 or 512 cells (as in the step kernel).
 template <class L, class S, int FORCE, bool EF, bool WIN>
 bool launch_rows(const void* P, const float* lam_in, float* lam_out, const uint32_t* nbr, const float* Ef,
-                 const float* w_rho, const float* w_j, double* gE, double* slots, int64_t slot_blocks,
+                 const float* w_rho, const float* w_j, float* gE, double* slots, int64_t slot_blocks,
                  const KParams& p, cudaStream_t s) {
     // the compile-time strides only for the benchmarked lattices (D2V9, D3V19)
     constexpr bool kFixed = L::Q == 9 || L::Q == 19;
@@ -846,7 +847,7 @@ int seed_storage(int vel, const void* P, const uint32_t* nbr, const float* w_rho
 template <class S, int GROUP>
 int step_storage(int vel, int force, bool efield, bool in_window, const void* P, const float* lam_in,
                  float* lam_out, const uint32_t* nbr, const float* Ef, const float* w_rho, const float* w_j,
-                 double* gE, double* slots, const KParams& p, cudaStream_t s) {
+                 float* gE, double* slots, const KParams& p, cudaStream_t s) {
     Launch l = grid_of(p);
     const int64_t slot_blocks = (int64_t)l.grid.x * l.grid.y;
     return dispatch_lattice<GROUP>(vel, [&](auto lat) {

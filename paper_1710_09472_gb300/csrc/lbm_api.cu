@@ -274,7 +274,7 @@ struct StateHeader {
 // Frees the adjoint workspace (after the stream has drained).
 void ws_release(lbm_ctx* c) {
     AdjWorkspace& w = c->ws;
-    if (w.states.empty() && !w.lam[0] && !w.lam[1] && !w.slots && !w.red && !w.wstage) return;
+    if (w.states.empty() && !w.lam[0] && !w.lam[1] && !w.slots && !w.red && !w.wstage && !w.gpart) return;
     cudaStreamSynchronize(c->stream);
     for (void* q : w.states) cudaFree(q);
     w.states.clear();
@@ -283,6 +283,7 @@ void ws_release(lbm_ctx* c) {
     cudaFree(w.slots);
     cudaFree(w.red);
     cudaFree(w.wstage);
+    cudaFree(w.gpart);
     w = AdjWorkspace();
 }
 
@@ -936,7 +937,9 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     free_b += ws.held();
-    const size_t fixed = 2 * lam_alloc + sizeof(double) * (nslot + 8) + sizeof(float) * (size_t)c->N * (1 + c->D);
+    const size_t gpart_bytes = dL_dE ? sizeof(float) * (size_t)c->D * (size_t)c->N : 0;
+    const size_t fixed =
+        2 * lam_alloc + sizeof(double) * (nslot + 8) + sizeof(float) * (size_t)c->N * (1 + c->D) + gpart_bytes;
     // bytes for the kept forward states: the budget, or 95% of what the fixed part leaves free
     const size_t avail = free_b > fixed ? free_b - fixed : 0;
     const size_t budget = c->mem_budget ? std::min(c->mem_budget, avail) : avail - avail / 20;
@@ -992,6 +995,13 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
         ws.nslot = nslot;
     }
     if (!ws.red) ADJ_CHECK(cudaMalloc((void**)&ws.red, sizeof(double) * 8));
+    if (gpart_bytes && ws.gpart_bytes != gpart_bytes) {
+        cudaFree(ws.gpart);
+        ws.gpart = nullptr;
+        ws.gpart_bytes = 0;
+        ADJ_CHECK(cudaMalloc((void**)&ws.gpart, gpart_bytes));
+        ws.gpart_bytes = gpart_bytes;
+    }
     // the schedule's views of the state buffers
     std::vector<void*> ckpt, seg, snaps;
     void* base = nullptr;   // binomial: the state at t = 0
@@ -1032,7 +1042,16 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
             wj_d = wstage + c->N;
         }
     }
-    if (dL_dE) ADJ_CHECK(cudaMemsetAsync(dL_dE, 0, sizeof(double) * (size_t)c->D * c->N, c->stream));
+    if (dL_dE) {
+        ADJ_CHECK(cudaMemsetAsync(dL_dE, 0, sizeof(double) * (size_t)c->D * c->N, c->stream));
+        ADJ_CHECK(cudaMemsetAsync(ws.gpart, 0, gpart_bytes, c->stream));
+    }
+    // dL/dE: each reverse step adds into FP32 partials, folded into the FP64
+    // gradient every kFoldEvery reverse steps (counted from t_end, so every
+    // schedule folds after the same steps) and at the end
+    constexpr int64_t kFoldEvery = 32;
+    float* gpart = dL_dE ? ws.gpart : nullptr;
+    int64_t rsteps = 0;
 
     const int vel = c->lat.vel, sto = c->storage, force = c->lat.force;
     const bool ef = c->use_Efield, sr = c->stochastic;
@@ -1049,8 +1068,10 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
     auto rstep = [&](int64_t t, const void* state) {
         const bool win = t > t_begin && t <= t_end;
         c->launches += lbm::launch_adjoint_step(vel, sto, force, ef, win, state, lam[li], lam[li ^ 1], c->nbr,
-                                                c->Efield, wr_d, wj_d, dL_dE, slots, p, c->stream);
+                                                c->Efield, wr_d, wj_d, gpart, slots, p, c->stream);
         li ^= 1;
+        if (gpart && ++rsteps % kFoldEvery == 0)
+            c->launches += lbm::launch_fold_partials(gpart, dL_dE, (int64_t)c->D * c->N, c->stream);
     };
     auto seed = [&](const void* state_T) {
         c->launches += lbm::launch_adjoint_seed(vel, sto, state_T, c->nbr, wr_d, wj_d, lam[li], slots,
@@ -1161,6 +1182,8 @@ lbm_status lbm_adjoint(lbm_ctx* c, const float* w_rho, const float* w_j, int64_t
         ADJ_CHECK(cudaGetLastError());
         c->cur ^= 1;  // the context's current state is the state at T
     }
+    if (gpart && rsteps % kFoldEvery != 0)  // the last partials
+        c->launches += lbm::launch_fold_partials(gpart, dL_dE, (int64_t)c->D * c->N, c->stream);
     c->adj_stats[0] = store_all ? 2 : (binomial ? 1 : 0);
     c->adj_stats[1] = store_all ? T + 1 : (binomial ? 2 + nsnap : nseg + K - 1);
     c->adj_stats[2] = fwd_steps;

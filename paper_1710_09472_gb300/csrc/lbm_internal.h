@@ -362,9 +362,12 @@ int launch_adjoint_seed(int vel, int storage, const void* P, const uint32_t* nbr
                         cudaStream_t s);
 int launch_adjoint_step(int vel, int storage, int force, bool efield, bool in_window, const void* P,
                         const float* lam_in, float* lam_out, const uint32_t* nbr, const float* Ef,
-                        const float* w_rho, const float* w_j, double* gE, double* slots, const KParams& p,
+                        const float* w_rho, const float* w_j, float* gE, double* slots, const KParams& p,
                         cudaStream_t s);
 int launch_reduce_slots(const double* slots, int64_t n_blocks, int n_slots, double* out, cudaStream_t s);
+// acc[i] += part[i] (FP64) and part[i] = 0 for i < n: folds the reverse
+// steps' FP32 dL/dE partials into the caller's FP64 gradient.
+int launch_fold_partials(float* part, double* acc, int64_t n, cudaStream_t s);
 int launch_accumulate_totals(const double* partials, int64_t n_partials, double* acc4, cudaStream_t s);
 
 // Local chemical-potential table (lbm_fd.cu): for the FD weight of dimension D
@@ -395,8 +398,11 @@ struct AdjWorkspace {
     double* red = nullptr;
     float* wstage = nullptr;  // loss weights staged from the host
     size_t wstage_bytes = 0;
+    float* gpart = nullptr;   // FP32 dL/dE partials of the latest reverse steps (D N)
+    size_t gpart_bytes = 0;
     size_t held() const {
-        return states.size() * state_bytes + 2 * lam_bytes + sizeof(double) * (size_t)nslot + wstage_bytes;
+        return states.size() * state_bytes + 2 * lam_bytes + sizeof(double) * (size_t)nslot + wstage_bytes +
+               gpart_bytes;
     }
 };
 
