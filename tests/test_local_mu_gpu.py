@@ -116,16 +116,18 @@ def test_local_mu_mb_equals_default_model():
     assert rel_linf(r1, r2) < 1e-6 and rel_linf(j1, j2) < 1e-5
 
 
-def test_local_mu_3d_sampled_step():
+@pytest.mark.parametrize("dims", [(24, 20, 16), (64, 12, 10)])
+def test_local_mu_3d_sampled_step(dims):
     """D3V19 at the paper's copper values (theta = 1/270, mu = 1: the
-    Sommerfeld branch of the device table) on a porous box: after 20 GPU
-    steps of the local model, one more GPU step against the oracle's
-    collision with thetabar from the cell-by-cell FD route (mu_of_density,
-    then I_2/I_0), at sampled fluid cells and every direction."""
+    Sommerfeld branch of the device table) on a porous box (nx = 24: the
+    general kernel; nx = 64: the row-staged kernel's local-mu instantiation):
+    after 20 GPU steps of the local model, one more GPU step against the
+    oracle's collision with thetabar from the cell-by-cell FD route
+    (mu_of_density, then I_2/I_0), at sampled fluid cells and every
+    direction."""
     from paper_1710_09472_gb300.lbm import LBM
 
     theta, mu = 1.0 / 270.0, 1.0
-    dims = (24, 20, 16)
     nx, ny, nz = dims
     mask, _ = wl.boolean_obstacles((nz, ny, nx), 3.0, 0.8, 9)
     solid_flat = mask.reshape(-1).astype(np.uint8)
