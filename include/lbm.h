@@ -277,11 +277,13 @@ lbm_status lbm_selftest_wait_timeout(lbm_ctx* ctx, int64_t clocks);
  *             lbm_get_populations), or NULL.
  * Device memory: the schedule's states (populations + bounce-back link
  * buffer each) plus two FP32 adjoint fields (Q N values + one per bounce-back
- * link each).  The context keeps these buffers after the call and reuses
- * them in the next one (buffers it already holds count as free memory when
- * the schedule is chosen); lbm_release_workspace, lbm_set_geometry and
- * lbm_destroy free them.
- * Gradients accumulate in FP64; the sweep is deterministic.
+ * link each), and with dL_dE an FP32 partial of it (D N values).  The
+ * context keeps these buffers after the call and reuses them in the next one
+ * (buffers it already holds count as free memory when the schedule is
+ * chosen); lbm_release_workspace, lbm_set_geometry and lbm_destroy free them.
+ * dL/dB, dL/dtau and the loss accumulate in FP64; dL/dE(x) accumulates in the
+ * FP32 partial for at most 32 reverse steps at a time, each batch then added
+ * into the FP64 dL_dE.  The sweep is deterministic.
  * Synchronises.  Errors: INVALID_ARG, STATE, OOM (with the size needed), CUDA,
  * NONFINITE. */
 lbm_status lbm_adjoint(lbm_ctx* ctx, const float* w_rho, const float* w_j, int64_t t_begin, int64_t t_end,
